@@ -1,0 +1,313 @@
+"""Plain FP64 CPU oracle for the R-matrix outer-region energy sweep.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+baseline leg of the benchmark may import this module.  The product path (the
+CUDA library and its binding) never imports, links or executes it, and this
+module imports nothing from the product path.
+
+What it computes, for one partial wave and one energy E (Rydberg units, radius
+in bohr, k^2 = E - e_i):
+
+1. R-matrix pole sum (Eq. 1, written as a matrix product in Eq. 2):
+   R_ij(E) = (1/2a) sum_k w_ik w_jk / (E_k - E).
+   Eq. 1 prints sum_k W_ik W_kj / (E - E_k) with no 1/(2a); this oracle takes
+   the Rydberg-units form with surface amplitudes w_ik = sqrt(2) psi_ik(a), whose
+   sign makes dR/dE positive semidefinite (Wigner causality).
+2. Open/closed split: channel i is open when E > e_i; thresholds are sorted, so
+   the open channels are a prefix of length n_o.
+3. Zero-potential asymptotic functions at r = a (the paper does not give them;
+   standard reading): open channels s_i = k^-1/2 jhat_l(kr),
+   c_i = -k^-1/2 nhat_l(kr) (Riccati-Bessel, nhat_l = x y_l(x) ~ -cos(x - l pi/2)),
+   so that every open channel has Wronskian s c' - s' c = -1; closed channels
+   decay as khat_l(kappa r), kappa = sqrt(e_i - E).
+4. Matching with Bloch constant b = 0, F(a) = a R F'(a), F_ij ~ s_i d_ij + c_i K_ij
+   (open i), F_ij ~ e_i(r) x_ij (closed i).  Column j of the matching matrix is
+   divided by c_j (open) or e_j (closed); the system becomes
+   (I - a R Lambda) Y = -B, Lambda_j = c'_j/c_j or e'_j/e_j,
+   B[:, m] = s_m delta_m - a R[:, m] s'_m, and K_jm = Y_jm / c_j.
+   Solved by LU with partial pivoting (LAPACK getrf/getrs).
+5. S = (I + iK)(I - iK)^-1, T = S - I, sigma_{i->j} = (pi / k_i^2) |T_ji|^2
+   (statistical weight (2J+1)/g_i taken as 1), eigenphase sum
+   eta = sum_m arctan(lambda_m(K)).
+
+Energies closer than 1e-9 Ry to a pole or a threshold are moved up by 1e-6 Ry,
+once, and flagged.
+
+The paper prints no worked example for this path; the tests pin every step to
+closed forms and invariants instead (Breit-Wigner single pole, hard sphere,
+uncoupled channels, Bloch-operator resolvent, symmetry, unitarity, detailed
+balance, Wigner monotonicity, resonance causality).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg
+from scipy.special import spherical_jn, spherical_yn
+
+FLAG_NUDGED = 1
+FLAG_ILLCOND = 2
+FLAG_NO_OPEN = 4
+FLAG_SINGULAR = 8
+
+NUDGE_TOL = 1e-9
+NUDGE_SHIFT = 1e-6
+ILLCOND_RATIO = 1e-12
+
+
+# ----------------------------------------------------------------------------
+# energy mesh preparation
+# ----------------------------------------------------------------------------
+def nudge_energies(energies, poles, thresh):
+    """Move every energy within 1e-9 Ry of a pole or a threshold up by 1e-6 Ry.
+
+    Applied once per energy (no re-check after the move).  Returns the new mesh
+    and a uint8 flag array with FLAG_NUDGED set where a move happened.
+    """
+    E = np.array(energies, dtype=np.float64, copy=True)
+    flags = np.zeros(E.shape, dtype=np.uint8)
+    for e in range(E.shape[0]):
+        near = False
+        if poles.size:
+            near |= bool(np.min(np.abs(poles - E[e])) < NUDGE_TOL)
+        if thresh.size:
+            near |= bool(np.min(np.abs(thresh - E[e])) < NUDGE_TOL)
+        if near:
+            E[e] = E[e] + NUDGE_SHIFT
+            flags[e] |= FLAG_NUDGED
+    return E, flags
+
+
+def n_open(thresh, E):
+    """Number of open channels at energy E: #{i : e_i < E}."""
+    return int(np.count_nonzero(thresh < E))
+
+
+# ----------------------------------------------------------------------------
+# pole sum (Eq. 1 / Eq. 2)
+# ----------------------------------------------------------------------------
+def rmatrix(W, poles, E, a, delta=None, part="all"):
+    """R_ij(E) = (1/2a) sum_k w_ik w_jk / (E_k - E), Eq. 1 as the product of Eq. 2.
+
+    X_ik = w_ik / (E_k - E) and Y = W^T, so R = X Y / (2a), one GEMM per energy.
+    ``part`` restricts the sum to the near-pole window |E_k - E| < delta
+    ("near") or to its complement ("far"); "all" is the full sum.
+    """
+    d = 1.0 / (poles - E)
+    if part != "all":
+        inside = np.abs(poles - E) < delta
+        if part == "far":
+            d = np.where(inside, 0.0, d)
+        elif part == "near":
+            d = np.where(inside, d, 0.0)
+        else:
+            raise ValueError(part)
+    return (W * d[None, :]) @ W.T / (2.0 * a)
+
+
+def rmatrix_loops(W, poles, E, a):
+    """The same pole sum as three plain loops (tiny sizes only)."""
+    n, N = W.shape
+    R = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            s = 0.0
+            for k in range(N):
+                s += W[i, k] * W[j, k] / (poles[k] - E)
+            R[i, j] = s / (2.0 * a)
+    return R
+
+
+def pair_index(n, i, j):
+    """Packed upper-triangle index p(i, j) = i n - i(i-1)/2 + (j - i), i <= j."""
+    return i * n - (i * (i - 1)) // 2 + (j - i)
+
+
+def pack_upper(R):
+    """Pack the upper triangle of a symmetric n x n matrix, row by row."""
+    n = R.shape[0]
+    iu = np.triu_indices(n)
+    return R[iu]
+
+
+def unpack_upper(Rp, n):
+    R = np.zeros((n, n))
+    iu = np.triu_indices(n)
+    R[iu] = Rp
+    R.T[iu] = Rp
+    return R
+
+
+# ----------------------------------------------------------------------------
+# asymptotic functions at r = a
+# ----------------------------------------------------------------------------
+def riccati_jn(l, x):
+    """jhat_l(x) = x j_l(x) and its x-derivative (SciPy spherical Bessel)."""
+    j = spherical_jn(l, x)
+    jp = spherical_jn(l, x, derivative=True)
+    return x * j, j + x * jp
+
+
+def riccati_yn(l, x):
+    """nhat_l(x) = x y_l(x) (~ -cos(x - l pi/2)) and its x-derivative."""
+    y = spherical_yn(l, x)
+    yp = spherical_yn(l, x, derivative=True)
+    return x * y, y + x * yp
+
+
+def khat_logderiv(l, x):
+    """x-log-derivative of the decaying Riccati function khat_l(x).
+
+    khat_l(x) = exp(-x) p_l(x), p_l(x) = sum_{m=0}^{l} (l+m)!/(m!(l-m)!) (2x)^-m,
+    so khat_l'/khat_l = p_l'/p_l - 1.
+    """
+    p = 0.0
+    dp = 0.0
+    for m in range(l + 1):
+        c = math.factorial(l + m) / (math.factorial(m) * math.factorial(l - m)) / (2.0 ** m)
+        p += c * x ** (-m)
+        dp += -m * c * x ** (-m - 1)
+    return dp / p - 1.0
+
+
+def channel_functions(l, thresh, E, a):
+    """Per-channel matching data at energy E.
+
+    Returns dict with n_o, k2 (E - e_i), and for open channels s, s', c, c'
+    (r-derivatives); for every channel the scaled log-derivative Lambda used as
+    column scale of the matching matrix.
+    """
+    n = l.shape[0]
+    k2 = E - thresh
+    no = n_open(thresh, E)
+    s = np.zeros(n); sp = np.zeros(n); c = np.zeros(n); cp = np.zeros(n)
+    lam = np.zeros(n)
+    for i in range(n):
+        if k2[i] > 0.0:
+            k = math.sqrt(k2[i])
+            x = k * a
+            jh, jhp = riccati_jn(int(l[i]), x)
+            nh, nhp = riccati_yn(int(l[i]), x)
+            s[i] = jh / math.sqrt(k)
+            sp[i] = jhp * math.sqrt(k)
+            c[i] = -nh / math.sqrt(k)
+            cp[i] = -nhp * math.sqrt(k)
+            lam[i] = cp[i] / c[i]
+        else:
+            kap = math.sqrt(-k2[i])
+            lam[i] = kap * khat_logderiv(int(l[i]), kap * a)
+    return {"n_o": no, "k2": k2, "s": s, "sp": sp, "c": c, "cp": cp, "lam": lam}
+
+
+# ----------------------------------------------------------------------------
+# matching -> K, then S, eigenphase sum, cross sections
+# ----------------------------------------------------------------------------
+def kmatrix(R, l, thresh, E, a):
+    """Open-open K-matrix from the R-matrix at energy E (b = 0 matching).
+
+    Solves (I - a R Lambda) Y = -B by LU with partial pivoting; K = Y[:n_o]/c.
+    Returns (K (n_o x n_o), n_o, flags, pivot ratio min|u_jj| / max|u_jj|).
+    """
+    n = l.shape[0]
+    f = channel_functions(l, thresh, E, a)
+    no = f["n_o"]
+    flags = 0
+    if no == 0:
+        return np.zeros((0, 0)), 0, FLAG_NO_OPEN, 1.0
+    Mt = np.eye(n) - a * R * f["lam"][None, :]
+    B = -a * R[:, :no] * f["sp"][None, :no]
+    B[np.arange(no), np.arange(no)] += f["s"][:no]
+    lu, piv = scipy.linalg.lu_factor(Mt, check_finite=False)
+    d = np.abs(np.diag(lu))
+    if d.min() == 0.0:
+        return np.full((no, no), np.nan), no, FLAG_SINGULAR, 0.0
+    ratio = d.min() / d.max()
+    if ratio < ILLCOND_RATIO:
+        flags |= FLAG_ILLCOND
+    Y = scipy.linalg.lu_solve((lu, piv), -B, check_finite=False)
+    K = Y[:no, :] / f["c"][:no, None]
+    return K, no, flags, ratio
+
+
+def smatrix(K):
+    """S = (I + iK)(I - iK)^-1 (= (I - iK)^-1 (I + iK) for symmetric K) and T = S - I."""
+    no = K.shape[0]
+    I = np.eye(no)
+    S = np.linalg.solve(I - 1j * K, I + 1j * K)
+    return S, S - I
+
+
+def xsec(T, k2):
+    """sigma[i, j] = sigma_{i->j} = (pi / k_i^2) |T_ji|^2 for open i, j (bohr^2)."""
+    no = T.shape[0]
+    return (math.pi / k2[:no])[:, None] * np.abs(T.T) ** 2
+
+
+def eigenphase_sum(K):
+    """eta = sum_m arctan(lambda_m(K)), in (-n_o pi/2, n_o pi/2)."""
+    if K.shape[0] == 0:
+        return 0.0
+    return float(np.sum(np.arctan(np.linalg.eigvalsh(0.5 * (K + K.T)))))
+
+
+# ----------------------------------------------------------------------------
+# whole sweep
+# ----------------------------------------------------------------------------
+def sweep(wave, energies, sel=(0,), delta=0.05, part="all", keep_R=True, keep_K=True,
+          energy_idx=None):
+    """Run the full per-energy path for one wave.
+
+    ``energy_idx`` restricts the work to a subset of mesh indices (the mesh is
+    still nudged as a whole).  Returned arrays follow the library's layouts:
+    R (m, n_p) packed upper, K (m, n, n) with the open block valid and zeros
+    elsewhere, eta (m,), sig_tot (m, n_sel), sig_sel (m, n_sel, n), n_open (m,),
+    flags (m,) uint8, piv_ratio (m,).
+    """
+    l, thr, poles, W, a = wave.l, wave.thresh, wave.poles, wave.W, wave.a
+    n = l.shape[0]
+    E_all, nflags = nudge_energies(energies, poles, thr)
+    idx = np.arange(E_all.shape[0]) if energy_idx is None else np.asarray(energy_idx)
+    m = idx.shape[0]
+    n_sel = len(sel)
+    out = {
+        "E": E_all[idx].copy(),
+        "eta": np.zeros(m),
+        "sig_tot": np.zeros((m, n_sel)),
+        "sig_sel": np.zeros((m, n_sel, n)),
+        "n_open": np.zeros(m, dtype=np.int32),
+        "flags": np.zeros(m, dtype=np.uint8),
+        "piv_ratio": np.zeros(m),
+    }
+    if keep_R:
+        out["R"] = np.zeros((m, n * (n + 1) // 2))
+    if keep_K:
+        out["K"] = np.zeros((m, n, n))
+    for t, e in enumerate(idx):
+        E = E_all[e]
+        R = rmatrix(W, poles, E, a, delta=delta, part=part)
+        K, no, fl, ratio = kmatrix(R, l, thr, E, a)
+        fl |= int(nflags[e])
+        out["flags"][t] = fl
+        out["n_open"][t] = no
+        out["piv_ratio"][t] = ratio
+        if keep_R:
+            out["R"][t] = pack_upper(R)
+        if no == 0 or (fl & FLAG_SINGULAR):
+            continue
+        if keep_K:
+            out["K"][t, :no, :no] = K
+        S, T = smatrix(K)
+        sig = xsec(T, E - thr)
+        out["eta"][t] = eigenphase_sum(K)
+        for q, i in enumerate(sel):
+            if i < no:
+                out["sig_sel"][t, q, :no] = sig[i, :]
+                out["sig_tot"][t, q] = float(np.sum(sig[i, :]))
+    return out
+
+
+def wrap_angle(x):
+    """Wrap to (-pi, pi]."""
+    y = np.mod(np.asarray(x) + np.pi, 2.0 * np.pi) - np.pi
+    return np.where(y == -np.pi, np.pi, y)
