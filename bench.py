@@ -1,0 +1,368 @@
+"""Benchmark of the R-matrix outer-region sweep (energies/s, R + K + sigma).
+
+One step = one pass of the whole per-energy path (pole sum, asymptotic
+functions, matching LU -> K, S-step -> eigenphase sum and cross sections) over
+the energy batch of the workload, with every input resident in HBM.  Prints
+one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+
+Multi-GPU: the sweep has no exchange step; each rank runs an independent
+replica of the workload (weak scaling) and the value is the total number of
+(wave, energy) units over the max time across ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1403_5524_gb300 import synth  # noqa: E402
+
+METRIC = "energies/sec (R+K+σ) split-precision vs FP64 GPU at n_ch=256; max rel err"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=3)
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "split_bf16"])
+    ap.add_argument("--stride", type=int, default=0,
+                    help="use every stride-th energy of the mesh (0 = automatic)")
+    ap.add_argument("--sel", type=int, default=1, help="number of selected initial channels")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    wl = synth.config(args.config)
+    stride = args.stride
+    if stride == 0:
+        stride = 25 if args.prec == "fp64" and args.config in (3, 5) else 1
+    if stride > 1:
+        wl = synth.Workload(wl.name, wl.waves, wl.energies[::stride].copy(), wl.delta, wl.meta)
+    return wl, stride
+
+
+def algorithmic_flops(wl, n_open_by_wave, n_sel):
+    """Per-step FLOP counts of the method (not counting slice products).
+
+    pole sum 2 n_p N per energy; matching LU (2/3) n^3 + 2 n^2 n_o;
+    S-step (8/3) n_o^3 + 8 n_o^2 r (real flops of the complex LU and solve).
+    """
+    pole = 0.0
+    solve = 0.0
+    for w, no in zip(wl.waves, n_open_by_wave):
+        n = w.n
+        npair = n * (n + 1) / 2
+        pole += 2.0 * npair * w.N * wl.n_e
+        no = no.astype(np.float64)
+        solve += float(np.sum((2.0 / 3.0) * n ** 3 + 2.0 * n * n * no + (8.0 / 3.0) * no ** 3
+                              + 8.0 * no * no * n_sel))
+    return pole, solve
+
+
+class Clocks:
+    """Sample nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(wl, sel, budget_s=15.0, max_e=64, keep=False):
+    """Time the FP64 CPU oracle on a bounded, evenly spaced sample of the mesh.
+
+    Returns (energies done, seconds, indices, oracle outputs or None)."""
+    from oracle import rmatrix as orc
+    w = wl.waves[0]
+    idx = np.linspace(0, wl.n_e - 1, max_e).astype(int)
+    t0 = time.perf_counter()
+    done = 0
+    parts = []
+    for k in range(0, idx.size, 4):
+        part = idx[k:k + 4]
+        parts.append(orc.sweep(w, wl.energies, sel=sel, keep_R=keep, keep_K=keep, energy_idx=part))
+        done += part.size
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    out = None
+    if keep:
+        out = {k: np.concatenate([p_[k] for p_ in parts]) for k in parts[0]}
+    return done, dt, idx[:done], out
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl, stride = workload(args)
+    sel = tuple(range(args.sel))
+    total_e, total_t = 0, 0.0
+    per = max(2, min(16, 64 // max(1, args.steps)))
+    for s in range(args.warmup + args.steps):
+        n, dt, _, _ = oracle_sample(wl, sel, budget_s=20.0, max_e=per)
+        if s >= args.warmup:
+            total_e += n
+            total_t += dt
+    val = total_e / total_t
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "energies/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": wl.name, "mesh_stride": stride,
+                       "sample": f"{per} evenly spaced energies of the mesh per step"},
+            "cpu_baseline": {"value": val, "unit": "energies/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{total_e} energies over {args.steps} steps"},
+            "e2e": {"value": val, "unit": "energies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_1403_5524_gb300 import rm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl, stride = workload(args)
+    sel = tuple(range(args.sel))
+    stream = torch.cuda.current_stream(dev)
+    # inputs resident in HBM
+    dwaves = [synth.Wave(l=torch.from_numpy(w.l).to(dev), thresh=torch.from_numpy(w.thresh).to(dev),
+                         poles=torch.from_numpy(w.poles).to(dev), W=torch.from_numpy(w.W).to(dev), a=w.a)
+              for w in wl.waves]
+    dE = torch.from_numpy(wl.energies).to(dev)
+    plan = rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        plan.run()
+    barrier()
+    plan.profile(True)
+    plan.profile_read()
+    l0 = plan.launches()
+    clk = Clocks(local)
+    clk.start()
+    step_ms = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)  # L2 flush between timed steps, outside the events
+        ev[s][0].record(stream)
+        plan.run()
+        ev[s][1].record(stream)
+    barrier()
+    clocks = clk.stop()
+    launches = plan.launches() - l0
+    prof = plan.profile_read()
+    plan.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = world * len(wl.waves) * wl.n_e * args.steps
+    value = units / (total_ms / 1000.0)
+
+    # open-channel counts for the FLOP model
+    n_open = []
+    for g, w in enumerate(wl.waves):
+        no = np.zeros(wl.n_e, np.int32)
+        plan.results(g, 0, wl.n_e, n_open=no)
+        n_open.append(no)
+    pole_flops, solve_flops = algorithmic_flops(wl, n_open, len(sel))
+    kern = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
+    dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    flops_per_step = {"polesum_fp64": pole_flops, "solve": solve_flops}
+    roof = None
+    if dom in flops_per_step:
+        total_fl = flops_per_step[dom] * args.steps
+        n_l = kern[dom]["launches"]
+        avg_ms = kern[dom]["ms_total"] / n_l
+        achieved = (total_fl / n_l) / (avg_ms / 1000.0) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "flops_per_launch": total_fl / n_l, "avg_launch_ms": avg_ms}
+    for k in kern:
+        if k in flops_per_step:
+            kern[k]["tflops"] = flops_per_step[k] * args.steps / (kern[k]["ms_total"] / 1000.0) / 1e12
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        hwaves = [synth.Wave(l=pin(w.l), thresh=pin(w.thresh), poles=pin(w.poles), W=pin(w.W), a=w.a)
+                  for w in wl.waves]
+        hE = pin(wl.energies)
+        outs = [{k: torch.from_numpy(v).pin_memory().numpy() for k, v in
+                 rm.host_outputs(wl.n_e, w.n, len(sel)).items()} for w in wl.waves]
+        h2d = sum(w.l.nbytes + w.thresh.nbytes + w.poles.nbytes + w.W.nbytes for w in wl.waves) + hE.nbytes
+        d2h = sum(sum(v.nbytes for v in o.values()) for o in outs)
+        e2e_steps = max(1, min(args.steps, 3))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.load(hwaves, hE)
+            plan.run()
+            for g in range(len(wl.waves)):
+                plan.results(g, 0, wl.n_e, **outs[g])
+        barrier()
+        dt = (time.perf_counter() - t0) / e2e_steps
+        if world > 1:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * len(wl.waves) * wl.n_e / dt, "unit": "energies/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
+
+    # CPU baseline leg: the oracle timed on a bounded sample of the same mesh;
+    # its outputs for those energies also give the accuracy report.
+    cpu = None
+    errors = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        n, dt, idx, ref = oracle_sample(wl, sel, budget_s=15.0, max_e=24, keep=not args.no_check)
+        cpu = {"value": n / dt, "unit": "energies/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} evenly spaced energies of the same mesh, FP64 NumPy/SciPy (incl. R and K)"}
+        if ref is not None:
+            errors = accuracy(plan, wl, sel, idx, ref)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.prec == "fp64" else "bf16-split+f64",
+                "data": "synthetic (seeded, workload distributions of the paper's problem class)",
+                "config": {"workload": wl.name, "prec": args.prec, "mesh_stride": stride,
+                           "energies_per_step": wl.n_e, "waves": len(wl.waves),
+                           "n_ch": [w.n for w in wl.waves][:4], "n_poles": [w.N for w in wl.waves][:4],
+                           "n_sel": len(sel), "l2": "flushed (512 MB write) between timed steps",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "kernels": kern, "gpu_launches": int(launches),
+                "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "errors": errors}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def accuracy(plan, wl, sel, idx, ref):
+    """Max normwise errors of the GPU path against oracle outputs on energies idx."""
+    FL_SKIP = 2 | 4 | 8  # ILLCOND | NO_OPEN | SINGULAR
+    w = wl.waves[0]
+    n = w.n
+    eR = eK = eS = eE = 0.0
+    R = np.zeros((1, n * (n + 1) // 2))
+    K = np.zeros((1, n, n))
+    for t, e in enumerate(idx):
+        e = int(e)
+        plan.rmatrix(0, e, e + 1, R)
+        Ro = ref["R"][t]
+        eR = max(eR, float(np.abs(R[0] - Ro).max() / np.abs(Ro).max()))
+        if ref["flags"][t] & FL_SKIP:
+            continue
+        plan.kmatrix(0, e, e + 1, K=K)
+        no = ref["n_open"][t]
+        Ko = ref["K"][t, :no, :no]
+        eK = max(eK, float(np.abs(K[0, :no, :no] - Ko).max() / np.abs(Ko).max()))
+        out = {"eigsum": np.zeros(1), "sig_tot": np.zeros((1, len(sel))), "sig_sel": np.zeros((1, len(sel), n))}
+        plan.xsec(0, e, e + 1, **out)
+        for q in range(len(sel)):
+            st = ref["sig_tot"][t, q]
+            if st > 0:
+                eS = max(eS, float(np.abs(out["sig_sel"][0, q] - ref["sig_sel"][t, q]).max() / st))
+        d = out["eigsum"][0] - ref["eta"][t]
+        eE = max(eE, float(abs(np.mod(d + np.pi, 2 * np.pi) - np.pi)))
+    return {"energies_checked": int(len(idx)), "R": eR, "K": eK, "sigma": eS, "eigsum_abs": eE,
+            "norm": "max|x - x*| / max|x*| per energy (sigma: / sigma_tot of the initial channel)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * rm.h - C ABI of the GB300 R-matrix outer-region energy sweep.
+ *
+ * For every energy E on a mesh and every partial wave the library computes
+ *   R_ij(E) = (1/2a) sum_k w_ik w_jk / (E_k - E)          (Eq. 1, as the
+ *             matrix product of Eq. 2; sign and 1/2a: Rydberg form with
+ *             surface amplitudes w_ik, dR/dE positive semidefinite),
+ * matches it at r = a (Bloch constant b = 0) to zero-potential asymptotic
+ * functions (Riccati-Bessel for open channels, decaying khat_l for closed
+ * ones; the paper states the problem but not these formulae), solves for the
+ * open-open K-matrix by LU with partial pivoting, and reduces K to
+ * S = (I + iK)(I - iK)^-1, the eigenphase sum and partial cross sections
+ * sigma_{i->j} = (pi / k_i^2) |T_ji|^2, T = S - I (weights (2J+1)/g_i = 1).
+ * Units: Rydberg energies, bohr lengths, k^2 = E - e_i, sigma in bohr^2.
+ *
+ * Threading and streams.  A plan belongs to one CUDA device and one stream
+ * (given at creation; NULL = the legacy default stream).  Every call
+ * enqueues work on that stream.  Calls whose output memory is RM_MEM_HOST
+ * return after the results are in host memory; calls with RM_MEM_DEVICE
+ * outputs return as soon as the work is enqueued.  A plan must not be used
+ * from two host threads at once.
+ *
+ * Errors.  Every call returns an rm_status_t; nothing aborts and no C++
+ * exception crosses this boundary.  rm_last_error() gives a one-line
+ * description of the most recent failure in the calling thread.  Numerical
+ * trouble at a single energy is not an error: it is reported in the per-energy
+ * flags (RM_FLAG_*).
+ *
+ * Layouts (all row-major, 0-based):
+ *   W          n_ch x n_poles, w_ik at W[i*n_poles + k]
+ *   R_packed   per energy, the upper triangle row by row:
+ *              p(i,j) = i*n - i(i-1)/2 + (j-i), i <= j, n_p = n(n+1)/2;
+ *              energy e of the range at R_packed[(e-e0)*n_p + p]
+ *   K          per energy a dense n x n block at K[(e-e0)*n*n + i*n + j];
+ *              the open-open n_o x n_o block is valid, the rest is zero
+ *   sig_sel    per energy n_sel x n: sig_sel[((e-e0)*n_sel + q)*n + j]
+ *              = sigma_{sel[q] -> j}; zero where either channel is closed
+ *   sig_tot    per energy n_sel: sum over j of sig_sel
+ *   eigsum     per energy: -arg det(I - iK) wrapped to (-pi, pi]; equal to
+ *              sum_m arctan(lambda_m(K)) modulo 2 pi
+ */
+#ifndef RM_H
+#define RM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RM_OK = 0,
+  RM_ERR_ARG = 1,      /* null pointer, bad size, bad option, l out of range, NaN input */
+  RM_ERR_ORDER = 2,    /* poles or thresholds (or the energy mesh) not sorted ascending */
+  RM_ERR_NOMEM = 3,    /* device or host allocation failed */
+  RM_ERR_CUDA = 4,     /* CUDA runtime error, or no usable sm_103 device */
+  RM_ERR_TIMEOUT = 5,  /* a bounded device-side wait ran out */
+  RM_ERR_STATE = 6     /* call not valid in the plan's current state */
+} rm_status_t;
+
+typedef enum { RM_MEM_HOST = 0, RM_MEM_DEVICE = 1 } rm_mem_t;
+
+typedef enum {
+  RM_PREC_FP64 = 0,        /* pole sum over all poles in FP64 (baseline form) */
+  RM_PREC_SPLIT_BF16 = 1   /* far poles: sliced BF16 tcgen05 GEMM, FP32 TMEM
+                              accumulation; |E_k - E| < delta in FP64 */
+} rm_precision_t;
+
+/* per-energy flag bits */
+#define RM_FLAG_NUDGED 1u    /* energy was within 1e-9 Ry of a pole or threshold; moved up 1e-6 Ry */
+#define RM_FLAG_ILLCOND 2u   /* min|pivot| / max|pivot| of the matching LU below 1e-12 */
+#define RM_FLAG_NO_OPEN 4u   /* no open channel (E below every threshold); outputs are zero */
+#define RM_FLAG_SINGULAR 8u  /* exact zero pivot; outputs are NaN */
+
+#define RM_LMAX 32           /* largest supported channel angular momentum */
+#define RM_MAX_SEL 64        /* largest number of selected initial channels */
+
+typedef struct rm_plan_s* rm_plan_t;
+
+/* One partial wave (J-pi symmetry).  Pointer memory space: rm_options.mem. */
+typedef struct {
+  int32_t n_ch;          /* channels n, 1 <= n <= 640 */
+  int32_t n_poles;       /* poles N, 1 <= N */
+  double a;              /* R-matrix radius (bohr), > 0 */
+  const int32_t* l;      /* [n] channel angular momenta, 0 <= l <= RM_LMAX */
+  const double* thresh;  /* [n] channel thresholds e_i (Ry), sorted ascending */
+  const double* pole_E;  /* [N] poles E_k (Ry), sorted ascending */
+  const double* W;       /* [n*N] surface amplitudes w_ik, row-major */
+} rm_wave;
+
+typedef struct {
+  int32_t prec;            /* rm_precision_t */
+  double delta;            /* near-pole window half width (Ry) for split modes; > 0 */
+  int32_t slices;          /* split slices per operand (0 = default) */
+  const int32_t* sel_init; /* host array of selected initial channels; NULL = {0} */
+  int32_t n_sel;           /* entries in sel_init (ignored when sel_init is NULL) */
+  int32_t mem;             /* rm_mem_t of every input pointer (waves and energies) */
+  int32_t chunk;           /* energies per internal chunk; 0 = automatic */
+} rm_options;
+
+/* Fill *opt with defaults: FP64, delta 0.05, sel {0}, host inputs, auto chunk. */
+void rm_options_default(rm_options* opt);
+
+/*
+ * Create a plan: validate and copy the inputs to the device (the caller may
+ * free them when this returns), nudge the energy mesh per wave (energies
+ * within 1e-9 Ry of a pole or threshold move up by 1e-6 Ry, once), count the
+ * open channels per energy and size the workspace.  energies[n_e] must be
+ * sorted ascending.  cuda_stream is a cudaStream_t (NULL = default stream).
+ * On failure *out is NULL.
+ */
+rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves,
+                           const double* energies, int64_t n_e, const rm_options* opt,
+                           void* cuda_stream);
+
+/* Replace the inputs of an existing plan by new ones of the same shapes
+   (n_ch, n_poles, n_waves, n_e); pointers are in memory space `mem`. */
+rm_status_t rm_plan_load(rm_plan_t plan, const rm_wave* waves, const double* energies,
+                         int32_t mem);
+
+/* Packed R-matrices of one wave for energies [e0, e1) (the pole sum of
+   Eq. 1, in the plan's precision), R_packed[(e1-e0) * n_p]. */
+rm_status_t rm_rmatrix(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, double* R_packed,
+                       int32_t mem);
+
+/* K-matrices, open-channel counts and flags of one wave for [e0, e1).
+   K[(e1-e0)*n*n], n_open[(e1-e0)], flags[(e1-e0)]; any may be NULL. */
+rm_status_t rm_kmatrix(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, double* K,
+                       int32_t* n_open, uint8_t* flags, int32_t mem);
+
+/* Eigenphase sums and cross sections of one wave for [e0, e1).
+   eigsum[(e1-e0)], sig_tot[(e1-e0)*n_sel], sig_sel[(e1-e0)*n_sel*n]; any may be NULL. */
+rm_status_t rm_xsec(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, double* eigsum,
+                    double* sig_tot, double* sig_sel, int32_t mem);
+
+/* The whole sweep: every wave, every energy, R -> K -> S, eigenphase sum and
+   cross sections into plan-owned device buffers (read them with
+   rm_results).  This is the call the benchmark times. */
+rm_status_t rm_run(rm_plan_t plan);
+
+/* Copy results of the last rm_run for one wave and energies [e0, e1).
+   Any output pointer may be NULL. */
+rm_status_t rm_results(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, double* eigsum,
+                       double* sig_tot, double* sig_sel, int32_t* n_open, uint8_t* flags,
+                       int32_t mem);
+
+/* Wait for the plan's stream; reports device-side error words. */
+rm_status_t rm_sync(rm_plan_t plan);
+
+/* Sizes: n_ch, n_poles of a wave; the plan's n_e, n_sel, chunk and device
+   workspace bytes.  Any output may be NULL. */
+rm_status_t rm_plan_info(rm_plan_t plan, int32_t wave, int32_t* n_ch, int32_t* n_poles,
+                         int64_t* n_e, int32_t* n_sel, int32_t* chunk, int64_t* workspace_bytes);
+
+/* Number of kernel launches this plan has issued since creation. */
+int64_t rm_plan_launches(rm_plan_t plan);
+
+/* Kernel identifiers for per-kernel device timing. */
+#define RM_KERNEL_POLESUM_FP64 0   /* FP64 pole sum (all poles) */
+#define RM_KERNEL_POLESUM_SPLIT 1  /* sliced BF16 tcgen05 pole sum (far poles) */
+#define RM_KERNEL_NEAR 2           /* FP64 near-pole window */
+#define RM_KERNEL_ASYM 3           /* asymptotic functions */
+#define RM_KERNEL_SOLVE 4          /* matching LU + S-step */
+#define RM_KERNEL_COUNT 5
+
+/* Per-kernel device timing.  While enabled, every kernel launch of the plan
+   is bracketed by CUDA events on the plan's stream.  rm_profile_read waits
+   for the stream and returns, for one kernel id, the summed event time (ms)
+   and the number of launches since the last read, then resets them. */
+rm_status_t rm_profile_enable(rm_plan_t plan, int32_t on);
+rm_status_t rm_profile_read(rm_plan_t plan, int32_t kernel, double* total_ms, int64_t* launches);
+
+rm_status_t rm_plan_destroy(rm_plan_t plan);
+
+const char* rm_status_str(rm_status_t s);
+const char* rm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RM_H */

@@ -1,0 +1,439 @@
+// Per-energy matching solve and S-matrix step, FP64, one CTA per energy.
+//
+// Matching (Bloch constant b = 0; the paper states the problem but not the
+// matching, so this is the standard zero-potential form): with the column of
+// channel j divided by c_j (open) or e_j (closed),
+//   [ I - a R Lambda | -B ],  B[:, m] = s_m delta_m - a R[:, m] s'_m  (m open),
+// is reduced by LU with partial pivoting (row interchanges chosen on the
+// first n columns, applied to all columns) followed by back substitution,
+// which leaves Y = (I - a R Lambda)^-1 (-B) in the right-hand columns;
+// K_jm = Y_jm / c_j for open j, m.
+//
+// S-step: A = I - iK (n_o x n_o complex) with right-hand sides K[:, sel_q];
+// the same LU gives X = A^-1 K[:, sel], T[:, sel_q] = 2i X[:, q] (T = S - I =
+// 2iK(I - iK)^-1), sigma_{sel_q -> j} = (pi / k^2) |T_{j,sel_q}|^2, and the
+// eigenphase sum -arg det(I - iK) from the pivots and the interchange count.
+//
+// The blocked LU keeps a 16-column panel in shared memory, factors it with
+// partial pivoting, and updates the columns to its right in 64-column tiles
+// (row interchanges, triangular solve with the unit-lower panel block, then
+// the rank-16 update).  Each matrix lives in a per-CTA global workspace slot
+// that stays in L2 while the CTA works on it.  GB300 retires about two FP64
+// FMAs per clock per SM, so one 256-thread CTA per SM saturates the FP64 pipe.
+#include "rm_internal.cuh"
+
+namespace rm {
+
+namespace {
+
+constexpr int NB = 16;   // panel width
+constexpr int TC = 64;   // column tile of the trailing update
+constexpr int NT = 256;  // threads per CTA
+constexpr int NWARP = NT / 32;
+
+template <typename T>
+struct Ops;
+
+template <>
+struct Ops<double> {
+  __device__ static double zero() { return 0.0; }
+  __device__ static double one() { return 1.0; }
+  __device__ static double mag(double x) { return fabs(x); }
+  __device__ static double inv(double x) { return 1.0 / x; }
+  __device__ static double mul(double a, double b) { return a * b; }
+  __device__ static double fms(double acc, double a, double b) { return fma(-a, b, acc); }
+};
+
+template <>
+struct Ops<cplx> {
+  __device__ static cplx zero() { return cplx{0.0, 0.0}; }
+  __device__ static cplx one() { return cplx{1.0, 0.0}; }
+  __device__ static double mag(cplx x) { return fabs(x.re) + fabs(x.im); }  // LAPACK cabs1
+  __device__ static cplx inv(cplx x) {
+    // Smith's division 1 / (re + i im)
+    if (fabs(x.re) >= fabs(x.im)) {
+      const double r = x.im / x.re, d = x.re + x.im * r;
+      return cplx{1.0 / d, -r / d};
+    }
+    const double r = x.re / x.im, d = x.im + x.re * r;
+    return cplx{r / d, -1.0 / d};
+  }
+  __device__ static cplx mul(cplx a, cplx b) { return a * b; }
+  __device__ static cplx fms(cplx acc, cplx a, cplx b) {
+    return cplx{fma(-a.re, b.re, fma(a.im, b.im, acc.re)), fma(-a.re, b.im, fma(-a.im, b.re, acc.im))};
+  }
+};
+
+struct LUStat {
+  double pmin, pmax;
+  int swaps;
+  bool singular;
+};
+
+struct Red {
+  double v[NWARP];
+  int i[NWARP];
+  int piv;
+};
+
+// Block-wide argmax of Ops::mag over panel column j, rows [j, rows); ties -> smallest row.
+template <typename T>
+__device__ int panel_argmax(const T* panel, int rows, int j, Red* red) {
+  double best = -1.0;
+  int bidx = rows;
+  for (int r = j + threadIdx.x; r < rows; r += NT) {
+    const double v = Ops<T>::mag(panel[r * NB + j]);
+    if (v > best) { best = v; bidx = r; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+    if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red->v[w] = best; red->i[w] = bidx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = red->v[0];
+    int bi = red->i[0];
+    for (int q = 1; q < NWARP; ++q)
+      if (red->v[q] > b || (red->v[q] == b && red->i[q] < bi)) { b = red->v[q]; bi = red->i[q]; }
+    red->piv = bi;
+  }
+  __syncthreads();
+  return red->piv;
+}
+
+// LU with partial pivoting of the leading n x n block of A (row-major, ld),
+// row operations applied to all m columns, then back substitution on
+// columns [n, m).  smem: panel[n_max*NB], tile[NB*TC], ipiv[n_max].
+template <typename T>
+__device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* tile, int* ipiv,
+                         Red* red, LUStat& st) {
+  using O = Ops<T>;
+  const int t = threadIdx.x;
+  st.pmin = INFINITY;
+  st.pmax = 0.0;
+  st.swaps = 0;
+  st.singular = false;
+  // ------------------------------------------------------------ factorisation
+  for (int kb = 0; kb < n; kb += NB) {
+    const int nb = min(NB, n - kb);
+    const int rows = n - kb;
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      panel[idx] = (c < nb) ? A[(int64_t)(kb + r) * ld + kb + c] : O::zero();
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      const int p = panel_argmax(panel, rows, j, red);
+      if (t < NB && p != j) {
+        const T tmp = panel[j * NB + t];
+        panel[j * NB + t] = panel[p * NB + t];
+        panel[p * NB + t] = tmp;
+      }
+      if (t == 0) {
+        ipiv[kb + j] = kb + p;
+        if (p != j) st.swaps++;
+      }
+      __syncthreads();
+      const T piv = panel[j * NB + j];
+      const double pm = O::mag(piv);
+      if (t == 0) {
+        st.pmin = fmin(st.pmin, pm);
+        st.pmax = fmax(st.pmax, pm);
+        if (pm == 0.0) st.singular = true;
+      }
+      const T pinv = (pm == 0.0) ? O::zero() : O::inv(piv);
+      for (int r = j + 1 + t; r < rows; r += NT) {
+        const T lr = O::mul(panel[r * NB + j], pinv);
+        panel[r * NB + j] = lr;
+        for (int c = j + 1; c < nb; ++c) panel[r * NB + c] = O::fms(panel[r * NB + c], lr, panel[j * NB + c]);
+      }
+      __syncthreads();
+    }
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      if (c < nb) A[(int64_t)(kb + r) * ld + kb + c] = panel[idx];
+    }
+    // columns right of the panel, in tiles of TC
+    for (int c0 = kb + nb; c0 < m; c0 += TC) {
+      const int tc = t % TC, tr = t / TC;
+      const int col = c0 + tc;
+      if (t < TC && col < m) {
+        T u[NB];
+        for (int j = 0; j < nb; ++j) {
+          const int r1 = kb + j, r2 = ipiv[kb + j];
+          if (r1 != r2) {
+            const T a1 = A[(int64_t)r1 * ld + col];
+            A[(int64_t)r1 * ld + col] = A[(int64_t)r2 * ld + col];
+            A[(int64_t)r2 * ld + col] = a1;
+          }
+        }
+        for (int j = 0; j < nb; ++j) {
+          T v = A[(int64_t)(kb + j) * ld + col];
+          for (int i = 0; i < j; ++i) v = O::fms(v, panel[j * NB + i], u[i]);
+          u[j] = v;
+        }
+        for (int j = 0; j < nb; ++j) {
+          A[(int64_t)(kb + j) * ld + col] = u[j];
+          tile[j * TC + t] = u[j];
+        }
+      }
+      __syncthreads();
+      if (col < m) {
+        for (int r = kb + nb + tr; r < n; r += NT / TC) {
+          T v = A[(int64_t)r * ld + col];
+          const T* lrow = panel + (r - kb) * NB;
+#pragma unroll 4
+          for (int j = 0; j < nb; ++j) v = O::fms(v, lrow[j], tile[j * TC + tc]);
+          A[(int64_t)r * ld + col] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ------------------------------------------------------- back substitution
+  const int kb_last = ((n - 1) / NB) * NB;
+  for (int kb = kb_last; kb >= 0; kb -= NB) {
+    const int nb = min(NB, n - kb);
+    const int rows = kb + nb;  // U[0 .. kb+nb)[kb .. kb+nb)
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      panel[idx] = (c < nb) ? A[(int64_t)r * ld + kb + c] : O::zero();
+    }
+    __syncthreads();
+    for (int c0 = n; c0 < m; c0 += TC) {
+      const int tc = t % TC, tr = t / TC;
+      const int col = c0 + tc;
+      if (t < TC && col < m) {
+        T y[NB];
+        for (int j = nb - 1; j >= 0; --j) {
+          T v = A[(int64_t)(kb + j) * ld + col];
+          for (int i = j + 1; i < nb; ++i) v = O::fms(v, panel[(kb + j) * NB + i], y[i]);
+          const T d = panel[(kb + j) * NB + j];
+          y[j] = (O::mag(d) == 0.0) ? O::zero() : O::mul(v, O::inv(d));
+        }
+        for (int j = 0; j < nb; ++j) {
+          A[(int64_t)(kb + j) * ld + col] = y[j];
+          tile[j * TC + t] = y[j];
+        }
+      }
+      __syncthreads();
+      if (col < m) {
+        for (int r = tr; r < kb; r += NT / TC) {
+          T v = A[(int64_t)r * ld + col];
+          const T* urow = panel + r * NB;
+#pragma unroll 4
+          for (int j = 0; j < nb; ++j) v = O::fms(v, urow[j], tile[j * TC + tc]);
+          A[(int64_t)r * ld + col] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+struct SolveArgs {
+  int n, n_sel;
+  double a;
+  const double* R;  // [ne * np]
+  const double* asym;
+  int64_t ld_asym;  // stride between lam, s, sp, c blocks
+  const double* E;  // [ne]
+  const double* thr;
+  const int32_t* n_open_in;
+  const uint8_t* flags_in;
+  const int32_t* sel;
+  int ne;
+  double* slot;
+  int64_t slot_doubles;
+  int ldR;  // leading dimension of the real augmented matrix
+  int ldC;  // leading dimension (complex elements) of the S-step matrix
+  SolveOut out;
+};
+
+__global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Red red;
+  __shared__ double s_acc;
+  const int n = g.n;
+  cplx* panel_c = reinterpret_cast<cplx*>(smem_raw);
+  cplx* tile_c = panel_c + (size_t)n * NB;
+  int* ipiv = reinterpret_cast<int*>(tile_c + NB * TC);
+  double* panel_d = reinterpret_cast<double*>(panel_c);
+  double* tile_d = reinterpret_cast<double*>(tile_c);
+
+  double* A = g.slot + (int64_t)blockIdx.x * g.slot_doubles;
+  cplx* C = reinterpret_cast<cplx*>(A + (int64_t)n * g.ldR);
+  const int64_t np = (int64_t)n * (n + 1) / 2;
+  const int t = threadIdx.x;
+
+  for (int e = blockIdx.x; e < g.ne; e += gridDim.x) {
+    const int no = g.n_open_in[e];
+    uint8_t fl = g.flags_in[e];
+    const double* Re = g.R + (int64_t)e * np;
+    const double* lam = g.asym + 0 * g.ld_asym + (int64_t)e * n;
+    const double* s = g.asym + 1 * g.ld_asym + (int64_t)e * n;
+    const double* sp = g.asym + 2 * g.ld_asym + (int64_t)e * n;
+    const double* c = g.asym + 3 * g.ld_asym + (int64_t)e * n;
+    if (g.out.K) {
+      for (int64_t idx = t; idx < (int64_t)n * n; idx += NT) g.out.K[(int64_t)e * n * n + idx] = 0.0;
+    }
+    if (no == 0) {
+      fl |= RM_FLAG_NO_OPEN;
+      if (t == 0) {
+        if (g.out.flags) g.out.flags[e] = fl;
+        if (g.out.n_open) g.out.n_open[e] = 0;
+        if (g.out.eta) g.out.eta[e] = 0.0;
+      }
+      if (g.out.sig_tot)
+        for (int q = t; q < g.n_sel; q += NT) g.out.sig_tot[(int64_t)e * g.n_sel + q] = 0.0;
+      if (g.out.sig_sel)
+        for (int64_t idx = t; idx < (int64_t)g.n_sel * n; idx += NT)
+          g.out.sig_sel[(int64_t)e * g.n_sel * n + idx] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    // ---------------------------------------------------------------- build
+    const int m = n + no;
+    for (int64_t idx = t; idx < (int64_t)n * m; idx += NT) {
+      const int i = (int)(idx / m), j = (int)(idx % m);
+      double v;
+      if (j < n) {
+        const double rij = Re[pair_index(n, min(i, j), max(i, j))];
+        v = ((i == j) ? 1.0 : 0.0) - g.a * rij * lam[j];
+      } else {
+        const int mo = j - n;
+        const double rim = Re[pair_index(n, min(i, mo), max(i, mo))];
+        v = -(((i == mo) ? s[mo] : 0.0) - g.a * rim * sp[mo]);
+      }
+      A[(int64_t)i * g.ldR + j] = v;
+    }
+    __syncthreads();
+    LUStat st;
+    lu_solve<double>(A, n, m, g.ldR, panel_d, tile_d, ipiv, &red, st);
+    __shared__ int s_singular;
+    __shared__ double s_ratio;
+    if (t == 0) {
+      s_singular = st.singular ? 1 : 0;
+      s_ratio = (st.pmax > 0.0) ? st.pmin / st.pmax : 0.0;
+    }
+    __syncthreads();
+    if (s_singular) fl |= RM_FLAG_SINGULAR;
+    else if (s_ratio < 1e-12) fl |= RM_FLAG_ILLCOND;
+    // K_jm = Y_jm / c_j
+    if (g.out.K) {
+      for (int64_t idx = t; idx < (int64_t)no * no; idx += NT) {
+        const int j = (int)(idx / no), mo = (int)(idx % no);
+        g.out.K[(int64_t)e * n * n + (int64_t)j * n + mo] = A[(int64_t)j * g.ldR + n + mo] / c[j];
+      }
+    }
+    if (t == 0) {
+      if (g.out.flags) g.out.flags[e] = fl;
+      if (g.out.n_open) g.out.n_open[e] = no;
+    }
+    if (!g.out.do_xsec) {
+      __syncthreads();
+      continue;
+    }
+    // --------------------------------------------------------------- S-step
+    const int r = g.n_sel;
+    const int mc = no + r;
+    for (int64_t idx = t; idx < (int64_t)no * mc; idx += NT) {
+      const int i = (int)(idx / mc), j = (int)(idx % mc);
+      cplx v;
+      if (j < no) {
+        const double kij = A[(int64_t)i * g.ldR + n + j] / c[i];
+        v = cplx{(i == j) ? 1.0 : 0.0, -kij};
+      } else {
+        const int sq = g.sel[j - no];
+        v = cplx{(sq < no) ? A[(int64_t)i * g.ldR + n + sq] / c[i] : 0.0, 0.0};
+      }
+      C[(int64_t)i * g.ldC + j] = v;
+    }
+    __syncthreads();
+    lu_solve<cplx>(C, no, mc, g.ldC, panel_c, tile_c, ipiv, &red, st);
+    if (t == 0 && g.out.eta) {
+      double ph = 0.0;
+      for (int j = 0; j < no; ++j) {
+        const cplx d = C[(int64_t)j * g.ldC + j];
+        ph += atan2(d.im, d.re);
+      }
+      ph += M_PI * (double)(st.swaps & 1);
+      double eta = -ph;
+      eta = eta - 2.0 * M_PI * floor((eta + M_PI) / (2.0 * M_PI));  // [-pi, pi)
+      if (eta == -M_PI) eta = M_PI;
+      g.out.eta[e] = s_singular ? NAN : eta;
+    }
+    for (int q = 0; q < r; ++q) {
+      const int sq = g.sel[q];
+      const bool open_i = sq < no;
+      const double k2 = g.E[e] - g.thr[min(sq, n - 1)];
+      double part = 0.0;
+      for (int j = t; j < n; j += NT) {
+        double sig = 0.0;
+        if (open_i && j < no) {
+          const cplx x = C[(int64_t)j * g.ldC + no + q];
+          sig = 4.0 * M_PI / k2 * (x.re * x.re + x.im * x.im);
+        }
+        if (s_singular) sig = NAN;
+        if (g.out.sig_sel) g.out.sig_sel[((int64_t)e * r + q) * n + j] = sig;
+        part += sig;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+      if (t == 0) s_acc = 0.0;
+      __syncthreads();
+      if ((t & 31) == 0) atomicAdd(&s_acc, part);
+      __syncthreads();
+      if (t == 0 && g.out.sig_tot) g.out.sig_tot[(int64_t)e * r + q] = s_acc;
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace
+
+size_t solve_smem_bytes(int n_max) {
+  return (size_t)n_max * NB * sizeof(cplx) + (size_t)NB * TC * sizeof(cplx) + (size_t)n_max * sizeof(int) + 16;
+}
+
+int64_t solve_slot_doubles(int n_max, int n_sel) {
+  const int64_t ldR = 2 * (int64_t)n_max;
+  const int64_t ldC = (int64_t)n_max + n_sel;
+  int64_t d = (int64_t)n_max * ldR + 2 * (int64_t)n_max * ldC;
+  return (d + 31) / 32 * 32;
+}
+
+cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, const double* R,
+                         const double* asym, int ld_chunk, const SolveOut& out, cudaStream_t s) {
+  if (ne <= 0) return cudaSuccess;
+  SolveArgs g;
+  g.n = w.n;
+  g.n_sel = p.n_sel;
+  g.a = w.a;
+  g.R = R;
+  g.asym = asym;
+  g.ld_asym = ld_chunk;
+  g.E = w.E + e0;
+  g.thr = w.thr;
+  g.n_open_in = w.n_open + e0;
+  g.flags_in = w.flags0 + e0;
+  g.sel = p.sel_dev;
+  g.ne = ne;
+  g.slot = p.slot;
+  g.slot_doubles = p.slot_doubles;
+  g.ldR = 2 * p.n_max;
+  g.ldC = p.n_max + p.n_sel;
+  g.out = out;
+  const size_t smem = solve_smem_bytes(p.n_max);
+  cudaError_t err = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int grid = min(ne, p.solve_slots);
+  solve_kernel<<<grid, NT, smem, s>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace rm

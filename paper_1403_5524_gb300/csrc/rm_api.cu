@@ -1,0 +1,626 @@
+// C ABI of the R-matrix outer-region sweep: plan management and the chunked
+// per-energy pipeline (pole sum -> asymptotic data -> matching LU -> S-step).
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "rm_internal.cuh"
+
+using namespace rm;
+
+namespace {
+
+thread_local std::string g_err;
+
+rm_status_t fail(rm_status_t s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+rm_status_t cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? RM_ERR_NOMEM : RM_ERR_CUDA;
+}
+
+#define RM_CUDA(call, where)                     \
+  do {                                           \
+    cudaError_t e__ = (call);                    \
+    if (e__ != cudaSuccess) return cuda_fail(e__, where); \
+  } while (0)
+
+template <typename T>
+rm_status_t dalloc(Plan* p, T** ptr, int64_t count) {
+  *ptr = nullptr;
+  if (count <= 0) return RM_OK;
+  const size_t bytes = (size_t)count * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(RM_ERR_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  p->workspace_bytes += (int64_t)bytes;
+  return RM_OK;
+}
+
+void dfree(void* ptr) {
+  if (ptr) cudaFree(ptr);
+}
+
+void free_plan(Plan* p) {
+  if (!p) return;
+  for (auto& w : p->waves) {
+    dfree(w.l); dfree(w.thr); dfree(w.poles); dfree(w.W); dfree(w.E); dfree(w.flags0);
+    dfree(w.n_open); dfree(w.eta); dfree(w.sig_tot); dfree(w.sig_sel); dfree(w.flags);
+  }
+  dfree(p->energies); dfree(p->sel_dev); dfree(p->Rbuf); dfree(p->asym); dfree(p->slot);
+  dfree(p->err_word);
+  for (int k = 0; k < RM_KERNEL_COUNT; ++k)
+    for (auto& pr : p->ev_live[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (auto e : p->ev_pool) cudaEventDestroy(e);
+  delete p;
+}
+
+bool valid_mem(int32_t m) { return m == RM_MEM_HOST || m == RM_MEM_DEVICE; }
+
+cudaMemcpyKind kind_in(int32_t mem) {
+  return mem == RM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+}
+cudaMemcpyKind kind_out(int32_t mem) {
+  return mem == RM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+}
+
+rm_status_t check_wave_args(const rm_wave& w, int idx) {
+  const std::string tag = "wave " + std::to_string(idx) + ": ";
+  if (w.n_ch < 1 || w.n_ch > 640) return fail(RM_ERR_ARG, tag + "n_ch must be in [1, 640]");
+  if (w.n_poles < 1) return fail(RM_ERR_ARG, tag + "n_poles must be >= 1");
+  if (!(w.a > 0.0) || !(w.a < 1e300)) return fail(RM_ERR_ARG, tag + "radius a must be finite and > 0");
+  if (!w.l || !w.thresh || !w.pole_E || !w.W) return fail(RM_ERR_ARG, tag + "null input pointer");
+  return RM_OK;
+}
+
+// Copy one wave's inputs into the plan's padded device buffers and validate.
+rm_status_t upload_wave(Plan* p, WaveDev& d, const rm_wave& w, int32_t mem) {
+  const cudaMemcpyKind k = kind_in(mem);
+  cudaStream_t s = p->stream;
+  RM_CUDA(cudaMemcpyAsync(d.l, w.l, sizeof(int32_t) * d.n, k, s), "copy l");
+  RM_CUDA(cudaMemcpyAsync(d.thr, w.thresh, sizeof(double) * d.n, k, s), "copy thresholds");
+  RM_CUDA(cudaMemcpyAsync(d.poles, w.pole_E, sizeof(double) * d.N, k, s), "copy poles");
+  RM_CUDA(cudaMemsetAsync(d.W, 0, sizeof(double) * (size_t)d.n * d.Npad, s), "clear W");
+  RM_CUDA(cudaMemcpy2DAsync(d.W, sizeof(double) * d.Npad, w.W, sizeof(double) * d.N,
+                            sizeof(double) * d.N, d.n, k, s), "copy W");
+  if (mem == RM_MEM_HOST) {
+    int32_t lmax = 0;
+    for (int i = 0; i < d.n; ++i) lmax = w.l[i] > lmax ? w.l[i] : lmax;
+    d.lmax = lmax;
+  }
+  return RM_OK;
+}
+
+rm_status_t prepare(Plan* p, const rm_wave* waves, const double* energies, int32_t mem) {
+  cudaStream_t s = p->stream;
+  if (p->n_e > 0)
+    RM_CUDA(cudaMemcpyAsync(p->energies, energies, sizeof(double) * p->n_e, kind_in(mem), s),
+            "copy energies");
+  RM_CUDA(cudaMemsetAsync(p->err_word, 0, sizeof(int32_t), s), "clear error word");
+  for (int g = 0; g < p->n_waves; ++g) {
+    WaveDev& d = p->waves[g];
+    rm_status_t st = upload_wave(p, d, waves[g], mem);
+    if (st != RM_OK) return st;
+    // pad poles past N with a far value (D -> 0 there; W is zero there too)
+    if (d.Npad > d.N) {
+      std::vector<double> far(d.Npad - d.N, 1e300);
+      RM_CUDA(cudaMemcpyAsync(d.poles + d.N, far.data(), sizeof(double) * far.size(),
+                              cudaMemcpyHostToDevice, s), "pad poles");
+      RM_CUDA(cudaStreamSynchronize(s), "pad poles");
+    }
+    RM_CUDA(launch_validate(d, d.N, p->energies, p->n_e, p->err_word, s), "validate kernel");
+    p->launches++;
+  }
+  int32_t err = 0;
+  RM_CUDA(cudaMemcpyAsync(&err, p->err_word, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read error word");
+  RM_CUDA(cudaStreamSynchronize(s), "validate");
+  if (err == RM_ERR_ORDER) return fail(RM_ERR_ORDER, "poles, thresholds or energies are not sorted ascending");
+  if (err != 0) return fail(RM_ERR_ARG, "input contains NaN/Inf or an angular momentum outside [0, RM_LMAX]");
+  for (int g = 0; g < p->n_waves; ++g) {
+    WaveDev& d = p->waves[g];
+    if (p->n_e > 0) {
+      RM_CUDA(launch_prep(d, p->energies, p->n_e, s), "prep kernel");
+      p->launches++;
+    }
+    if (p->n_e > 0) RM_CUDA(cudaMemsetAsync(d.flags, 0, p->n_e, s), "clear flags");
+  }
+  RM_CUDA(cudaStreamSynchronize(s), "prepare");
+  for (int g = 0; g < p->n_waves; ++g)
+    for (int q = 0; q < p->n_sel; ++q)
+      if (p->sel[q] >= p->waves[g].n && p->n_waves == 1)
+        return fail(RM_ERR_ARG, "selected initial channel out of range");
+  p->ran = false;
+  return RM_OK;
+}
+
+Plan* as_plan(rm_plan_t h) { return reinterpret_cast<Plan*>(h); }
+
+cudaEvent_t pool_event(Plan* p) {
+  if (!p->ev_pool.empty()) {
+    cudaEvent_t e = p->ev_pool.back();
+    p->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// Bracket one kernel launch with events when profiling is on.
+struct Prof {
+  Plan* p;
+  int k;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Prof(Plan* p_, int k_) : p(p_), k(k_) {
+    p->launches++;
+    if (!p->prof) return;
+    a = pool_event(p);
+    b = pool_event(p);
+    if (a) cudaEventRecord(a, p->stream);
+  }
+  ~Prof() {
+    if (!a || !b) return;
+    cudaEventRecord(b, p->stream);
+    p->ev_live[k].push_back({a, b});
+  }
+};
+
+void prof_collect(Plan* p) {
+  for (int k = 0; k < RM_KERNEL_COUNT; ++k) {
+    for (auto& pr : p->ev_live[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+        p->prof_ms[k] += ms;
+        p->prof_n[k] += 1;
+      } else {
+        cudaGetLastError();
+      }
+      p->ev_pool.push_back(pr.first);
+      p->ev_pool.push_back(pr.second);
+    }
+    p->ev_live[k].clear();
+  }
+}
+
+rm_status_t check_range(Plan* p, int32_t wave, int64_t e0, int64_t e1) {
+  if (!p) return fail(RM_ERR_ARG, "null plan");
+  if (wave < 0 || wave >= p->n_waves) return fail(RM_ERR_ARG, "wave index out of range");
+  if (e0 < 0 || e1 < e0 || e1 > p->n_e) return fail(RM_ERR_ARG, "energy range out of bounds");
+  if (cudaSetDevice(p->device) != cudaSuccess) return fail(RM_ERR_CUDA, "cudaSetDevice failed");
+  return RM_OK;
+}
+
+// Pole sum for one chunk into R (device, [ne * np]).
+rm_status_t polesum_chunk(Plan* p, const WaveDev& w, int64_t c0, int ne, double* R) {
+  if (p->prec == RM_PREC_FP64) {
+    Prof pr(p, RM_KERNEL_POLESUM_FP64);
+    RM_CUDA(launch_polesum_fp64(w, c0, ne, R, p->stream), "FP64 pole-sum kernel");
+    return RM_OK;
+  }
+  return fail(RM_ERR_ARG, "precision mode not available in this build");
+}
+
+// Pipeline over [e0, e1) for one wave.  Any output may be null; device outputs
+// are written directly, index 0 = energy e0.
+struct RangeOut {
+  double* R = nullptr;  // [ne * np]
+  SolveOut so;          // K, eta, sig_tot, sig_sel, flags, n_open (offset by e0)
+  bool need_solve = false;
+};
+
+rm_status_t run_range(Plan* p, int32_t wave, int64_t e0, int64_t e1, const RangeOut& o) {
+  const WaveDev& w = p->waves[wave];
+  const int64_t np = (int64_t)w.n * (w.n + 1) / 2;
+  for (int64_t c0 = e0; c0 < e1; c0 += p->chunk) {
+    const int ne = (int)((e1 - c0) < p->chunk ? (e1 - c0) : p->chunk);
+    const int64_t off = c0 - e0;
+    double* R = o.R ? o.R + off * np : p->Rbuf;
+    rm_status_t st = polesum_chunk(p, w, c0, ne, R);
+    if (st != RM_OK) return st;
+    if (!o.need_solve) continue;
+    const int ld = p->chunk * p->n_max;
+    {
+      Prof pr(p, RM_KERNEL_ASYM);
+      RM_CUDA(launch_asym(w, c0, ne, p->asym, ld, p->stream), "asymptotic-function kernel");
+    }
+    SolveOut so = o.so;
+    if (so.K) so.K += off * w.n * w.n;
+    if (so.eta) so.eta += off;
+    if (so.sig_tot) so.sig_tot += off * p->n_sel;
+    if (so.sig_sel) so.sig_sel += off * p->n_sel * w.n;
+    if (so.flags) so.flags += off;
+    if (so.n_open) so.n_open += off;
+    {
+      Prof pr(p, RM_KERNEL_SOLVE);
+      RM_CUDA(launch_solve(*p, w, c0, ne, R, p->asym, ld, so, p->stream), "solve kernel");
+    }
+  }
+  return RM_OK;
+}
+
+// device scratch for host-memory outputs of the per-range calls
+struct Scratch {
+  void* ptr = nullptr;
+  ~Scratch() { if (ptr) cudaFree(ptr); }
+};
+
+template <typename T>
+rm_status_t out_buf(Plan* p, T* user, int64_t count, int32_t mem, Scratch& sc, T** dev) {
+  *dev = nullptr;
+  if (!user || count <= 0) return RM_OK;
+  if (mem == RM_MEM_DEVICE) { *dev = user; return RM_OK; }
+  cudaError_t e = cudaMalloc(&sc.ptr, sizeof(T) * (size_t)count);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(RM_ERR_NOMEM, "scratch allocation failed"); }
+  *dev = reinterpret_cast<T*>(sc.ptr);
+  return RM_OK;
+}
+
+template <typename T>
+rm_status_t copy_back(Plan* p, T* user, T* dev, int64_t count, int32_t mem) {
+  if (!user || mem != RM_MEM_HOST || count <= 0) return RM_OK;
+  RM_CUDA(cudaMemcpyAsync(user, dev, sizeof(T) * (size_t)count, cudaMemcpyDeviceToHost, p->stream), "copy out");
+  return RM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rm_options_default(rm_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->prec = RM_PREC_FP64;
+  opt->delta = 0.05;
+  opt->slices = 0;
+  opt->sel_init = nullptr;
+  opt->n_sel = 0;
+  opt->mem = RM_MEM_HOST;
+  opt->chunk = 0;
+}
+
+const char* rm_status_str(rm_status_t s) {
+  switch (s) {
+    case RM_OK: return "ok";
+    case RM_ERR_ARG: return "invalid argument";
+    case RM_ERR_ORDER: return "input not sorted ascending";
+    case RM_ERR_NOMEM: return "out of memory";
+    case RM_ERR_CUDA: return "CUDA error";
+    case RM_ERR_TIMEOUT: return "device wait timed out";
+    case RM_ERR_STATE: return "invalid plan state";
+  }
+  return "unknown status";
+}
+
+const char* rm_last_error(void) { return g_err.c_str(); }
+
+rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves,
+                           const double* energies, int64_t n_e, const rm_options* opt,
+                           void* cuda_stream) {
+  try {
+    if (!out) return fail(RM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!waves || n_waves < 1) return fail(RM_ERR_ARG, "need at least one wave");
+    if (n_e < 0 || (n_e > 0 && !energies)) return fail(RM_ERR_ARG, "bad energy mesh");
+    rm_options o;
+    if (opt) o = *opt; else rm_options_default(&o);
+    if (!valid_mem(o.mem)) return fail(RM_ERR_ARG, "bad memory space");
+    if (o.prec != RM_PREC_FP64 && o.prec != RM_PREC_SPLIT_BF16) return fail(RM_ERR_ARG, "bad precision mode");
+    if (o.prec != RM_PREC_FP64 && !(o.delta > 0.0)) return fail(RM_ERR_ARG, "delta must be > 0");
+    if (o.chunk < 0) return fail(RM_ERR_ARG, "chunk must be >= 0");
+    int n_sel = 1;
+    int32_t sel[RM_MAX_SEL] = {0};
+    if (o.sel_init) {
+      if (o.n_sel < 1 || o.n_sel > RM_MAX_SEL) return fail(RM_ERR_ARG, "n_sel out of range");
+      n_sel = o.n_sel;
+      for (int q = 0; q < n_sel; ++q) {
+        if (o.sel_init[q] < 0) return fail(RM_ERR_ARG, "negative selected channel");
+        sel[q] = o.sel_init[q];
+      }
+    }
+    for (int g = 0; g < n_waves; ++g) {
+      rm_status_t st = check_wave_args(waves[g], g);
+      if (st != RM_OK) return st;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(RM_ERR_CUDA, "no CUDA device"); }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) { cudaGetLastError(); return fail(RM_ERR_CUDA, "cannot query device"); }
+    if (prop.major != 10 || prop.minor != 3)
+      return fail(RM_ERR_CUDA, std::string("needs an sm_103 (GB300) device, found ") + prop.name);
+
+    Plan* p = new (std::nothrow) Plan();
+    if (!p) return fail(RM_ERR_NOMEM, "host allocation failed");
+    p->device = dev;
+    p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    p->n_waves = n_waves;
+    p->n_e = n_e;
+    p->prec = o.prec;
+    p->delta = o.delta;
+    p->slices = o.slices;
+    p->n_sel = n_sel;
+    std::memcpy(p->sel, sel, sizeof(sel));
+    p->sm_count = prop.multiProcessorCount;
+    p->waves.resize(n_waves);
+    int n_max = 0;
+    int64_t np_max = 0;
+    rm_status_t st = RM_OK;
+    for (int g = 0; g < n_waves && st == RM_OK; ++g) {
+      WaveDev& d = p->waves[g];
+      d.n = waves[g].n_ch;
+      d.N = waves[g].n_poles;
+      d.Npad = (d.N + 63) / 64 * 64;
+      d.a = waves[g].a;
+      n_max = d.n > n_max ? d.n : n_max;
+      const int64_t np = (int64_t)d.n * (d.n + 1) / 2;
+      np_max = np > np_max ? np : np_max;
+      if ((st = dalloc(p, &d.l, d.n)) != RM_OK) break;
+      if ((st = dalloc(p, &d.thr, d.n)) != RM_OK) break;
+      if ((st = dalloc(p, &d.poles, d.Npad)) != RM_OK) break;
+      if ((st = dalloc(p, &d.W, (int64_t)d.n * d.Npad)) != RM_OK) break;
+      if ((st = dalloc(p, &d.E, n_e)) != RM_OK) break;
+      if ((st = dalloc(p, &d.flags0, n_e)) != RM_OK) break;
+      if ((st = dalloc(p, &d.n_open, n_e)) != RM_OK) break;
+      if ((st = dalloc(p, &d.eta, n_e)) != RM_OK) break;
+      if ((st = dalloc(p, &d.sig_tot, n_e * n_sel)) != RM_OK) break;
+      if ((st = dalloc(p, &d.sig_sel, n_e * n_sel * d.n)) != RM_OK) break;
+      if ((st = dalloc(p, &d.flags, n_e)) != RM_OK) break;
+    }
+    p->n_max = n_max;
+    if (st == RM_OK) {
+      int chunk = o.chunk;
+      if (chunk == 0) {
+        const int64_t budget = 96ll << 20;
+        int64_t c = budget / (np_max * 8) / 128 * 128;
+        c = c < 128 ? 128 : (c > 8192 ? 8192 : c);
+        chunk = (int)c;
+      }
+      if (n_e > 0 && chunk > n_e) chunk = (int)n_e;
+      if (chunk < 1) chunk = 1;
+      p->chunk = chunk;
+      p->solve_slots = p->sm_count;
+      p->slot_doubles = solve_slot_doubles(n_max, n_sel);
+      if (st == RM_OK) st = dalloc(p, &p->energies, n_e);
+      if (st == RM_OK) st = dalloc(p, &p->sel_dev, n_sel);
+      if (st == RM_OK) st = dalloc(p, &p->Rbuf, (int64_t)chunk * np_max);
+      if (st == RM_OK) st = dalloc(p, &p->asym, 4ll * chunk * n_max);
+      if (st == RM_OK) st = dalloc(p, &p->slot, (int64_t)p->solve_slots * p->slot_doubles);
+      if (st == RM_OK) st = dalloc(p, &p->err_word, 1);
+    }
+    if (st == RM_OK) {
+      if (cudaMemcpy(p->sel_dev, p->sel, sizeof(int32_t) * n_sel, cudaMemcpyHostToDevice) != cudaSuccess)
+        st = fail(RM_ERR_CUDA, "copy selected channels");
+    }
+    if (st == RM_OK && solve_smem_bytes(n_max) > (size_t)prop.sharedMemPerBlockOptin)
+      st = fail(RM_ERR_ARG, "n_ch too large for the solve kernel's shared memory");
+    if (st == RM_OK) st = prepare(p, waves, energies, o.mem);
+    if (st != RM_OK) {
+      free_plan(p);
+      return st;
+    }
+    *out = reinterpret_cast<rm_plan_t>(p);
+    return RM_OK;
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
+rm_status_t rm_plan_load(rm_plan_t h, const rm_wave* waves, const double* energies, int32_t mem) {
+  try {
+    Plan* p = as_plan(h);
+    if (!p) return fail(RM_ERR_ARG, "null plan");
+    if (!waves || (p->n_e > 0 && !energies) || !valid_mem(mem)) return fail(RM_ERR_ARG, "bad arguments");
+    for (int g = 0; g < p->n_waves; ++g) {
+      rm_status_t st = check_wave_args(waves[g], g);
+      if (st != RM_OK) return st;
+      if (waves[g].n_ch != p->waves[g].n || waves[g].n_poles != p->waves[g].N)
+        return fail(RM_ERR_ARG, "wave shape differs from the plan's");
+      if (waves[g].a != p->waves[g].a) p->waves[g].a = waves[g].a;
+    }
+    if (cudaSetDevice(p->device) != cudaSuccess) return fail(RM_ERR_CUDA, "cudaSetDevice failed");
+    return prepare(p, waves, energies, mem);
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
+rm_status_t rm_rmatrix(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* R_packed, int32_t mem) {
+  try {
+    Plan* p = as_plan(h);
+    rm_status_t st = check_range(p, wave, e0, e1);
+    if (st != RM_OK) return st;
+    if (!R_packed || !valid_mem(mem)) return fail(RM_ERR_ARG, "bad output");
+    const WaveDev& w = p->waves[wave];
+    const int64_t np = (int64_t)w.n * (w.n + 1) / 2;
+    if (mem == RM_MEM_DEVICE) {
+      RangeOut o;
+      o.R = R_packed;
+      return run_range(p, wave, e0, e1, o);
+    }
+    for (int64_t c0 = e0; c0 < e1; c0 += p->chunk) {
+      const int64_t c1 = (e1 - c0) < p->chunk ? e1 : c0 + p->chunk;
+      RangeOut o;  // into Rbuf
+      st = run_range(p, wave, c0, c1, o);
+      if (st != RM_OK) return st;
+      RM_CUDA(cudaMemcpyAsync(R_packed + (c0 - e0) * np, p->Rbuf, sizeof(double) * (size_t)((c1 - c0) * np),
+                              cudaMemcpyDeviceToHost, p->stream), "copy R");
+      RM_CUDA(cudaStreamSynchronize(p->stream), "rm_rmatrix");
+    }
+    return RM_OK;
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
+rm_status_t rm_kmatrix(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* K, int32_t* n_open,
+                       uint8_t* flags, int32_t mem) {
+  try {
+    Plan* p = as_plan(h);
+    rm_status_t st = check_range(p, wave, e0, e1);
+    if (st != RM_OK) return st;
+    if (!valid_mem(mem)) return fail(RM_ERR_ARG, "bad memory space");
+    const WaveDev& w = p->waves[wave];
+    const int64_t ne = e1 - e0;
+    Scratch sK, sN, sF;
+    RangeOut o;
+    o.need_solve = true;
+    o.so.do_xsec = false;
+    if ((st = out_buf(p, K, ne * w.n * w.n, mem, sK, &o.so.K)) != RM_OK) return st;
+    if ((st = out_buf(p, n_open, ne, mem, sN, &o.so.n_open)) != RM_OK) return st;
+    if ((st = out_buf(p, flags, ne, mem, sF, &o.so.flags)) != RM_OK) return st;
+    if ((st = run_range(p, wave, e0, e1, o)) != RM_OK) return st;
+    if ((st = copy_back(p, K, o.so.K, ne * w.n * w.n, mem)) != RM_OK) return st;
+    if ((st = copy_back(p, n_open, o.so.n_open, ne, mem)) != RM_OK) return st;
+    if ((st = copy_back(p, flags, o.so.flags, ne, mem)) != RM_OK) return st;
+    if (mem == RM_MEM_HOST) RM_CUDA(cudaStreamSynchronize(p->stream), "rm_kmatrix");
+    return RM_OK;
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
+rm_status_t rm_xsec(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* eigsum, double* sig_tot,
+                    double* sig_sel, int32_t mem) {
+  try {
+    Plan* p = as_plan(h);
+    rm_status_t st = check_range(p, wave, e0, e1);
+    if (st != RM_OK) return st;
+    if (!valid_mem(mem)) return fail(RM_ERR_ARG, "bad memory space");
+    const WaveDev& w = p->waves[wave];
+    const int64_t ne = e1 - e0;
+    Scratch s1, s2, s3;
+    RangeOut o;
+    o.need_solve = true;
+    o.so.do_xsec = true;
+    if ((st = out_buf(p, eigsum, ne, mem, s1, &o.so.eta)) != RM_OK) return st;
+    if ((st = out_buf(p, sig_tot, ne * p->n_sel, mem, s2, &o.so.sig_tot)) != RM_OK) return st;
+    if ((st = out_buf(p, sig_sel, ne * p->n_sel * w.n, mem, s3, &o.so.sig_sel)) != RM_OK) return st;
+    if ((st = run_range(p, wave, e0, e1, o)) != RM_OK) return st;
+    if ((st = copy_back(p, eigsum, o.so.eta, ne, mem)) != RM_OK) return st;
+    if ((st = copy_back(p, sig_tot, o.so.sig_tot, ne * p->n_sel, mem)) != RM_OK) return st;
+    if ((st = copy_back(p, sig_sel, o.so.sig_sel, ne * p->n_sel * w.n, mem)) != RM_OK) return st;
+    if (mem == RM_MEM_HOST) RM_CUDA(cudaStreamSynchronize(p->stream), "rm_xsec");
+    return RM_OK;
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
+rm_status_t rm_run(rm_plan_t h) {
+  try {
+    Plan* p = as_plan(h);
+    if (!p) return fail(RM_ERR_ARG, "null plan");
+    if (cudaSetDevice(p->device) != cudaSuccess) return fail(RM_ERR_CUDA, "cudaSetDevice failed");
+    for (int g = 0; g < p->n_waves; ++g) {
+      WaveDev& w = p->waves[g];
+      RangeOut o;
+      o.need_solve = true;
+      o.so.do_xsec = true;
+      o.so.eta = w.eta;
+      o.so.sig_tot = w.sig_tot;
+      o.so.sig_sel = w.sig_sel;
+      o.so.flags = w.flags;
+      rm_status_t st = run_range(p, g, 0, p->n_e, o);
+      if (st != RM_OK) return st;
+    }
+    p->ran = true;
+    return RM_OK;
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
+rm_status_t rm_results(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* eigsum, double* sig_tot,
+                       double* sig_sel, int32_t* n_open, uint8_t* flags, int32_t mem) {
+  try {
+    Plan* p = as_plan(h);
+    rm_status_t st = check_range(p, wave, e0, e1);
+    if (st != RM_OK) return st;
+    if (!valid_mem(mem)) return fail(RM_ERR_ARG, "bad memory space");
+    if (!p->ran) return fail(RM_ERR_STATE, "rm_results before rm_run");
+    const WaveDev& w = p->waves[wave];
+    const int64_t ne = e1 - e0;
+    const cudaMemcpyKind k = kind_out(mem);
+    cudaStream_t s = p->stream;
+    if (ne > 0) {
+      if (eigsum) RM_CUDA(cudaMemcpyAsync(eigsum, w.eta + e0, sizeof(double) * ne, k, s), "copy eta");
+      if (sig_tot)
+        RM_CUDA(cudaMemcpyAsync(sig_tot, w.sig_tot + e0 * p->n_sel, sizeof(double) * ne * p->n_sel, k, s), "copy sig_tot");
+      if (sig_sel)
+        RM_CUDA(cudaMemcpyAsync(sig_sel, w.sig_sel + e0 * p->n_sel * w.n, sizeof(double) * ne * p->n_sel * w.n, k, s),
+                "copy sig_sel");
+      if (n_open) RM_CUDA(cudaMemcpyAsync(n_open, w.n_open + e0, sizeof(int32_t) * ne, k, s), "copy n_open");
+      if (flags) RM_CUDA(cudaMemcpyAsync(flags, w.flags + e0, ne, k, s), "copy flags");
+    }
+    if (mem == RM_MEM_HOST) RM_CUDA(cudaStreamSynchronize(s), "rm_results");
+    return RM_OK;
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
+rm_status_t rm_sync(rm_plan_t h) {
+  Plan* p = as_plan(h);
+  if (!p) return fail(RM_ERR_ARG, "null plan");
+  RM_CUDA(cudaStreamSynchronize(p->stream), "rm_sync");
+  int32_t err = 0;
+  RM_CUDA(cudaMemcpy(&err, p->err_word, sizeof(int32_t), cudaMemcpyDeviceToHost), "read error word");
+  if (err == RM_ERR_TIMEOUT) return fail(RM_ERR_TIMEOUT, "a device-side wait ran out");
+  return RM_OK;
+}
+
+rm_status_t rm_plan_info(rm_plan_t h, int32_t wave, int32_t* n_ch, int32_t* n_poles, int64_t* n_e,
+                         int32_t* n_sel, int32_t* chunk, int64_t* workspace_bytes) {
+  Plan* p = as_plan(h);
+  if (!p) return fail(RM_ERR_ARG, "null plan");
+  if (wave < 0 || wave >= p->n_waves) return fail(RM_ERR_ARG, "wave index out of range");
+  if (n_ch) *n_ch = p->waves[wave].n;
+  if (n_poles) *n_poles = p->waves[wave].N;
+  if (n_e) *n_e = p->n_e;
+  if (n_sel) *n_sel = p->n_sel;
+  if (chunk) *chunk = p->chunk;
+  if (workspace_bytes) *workspace_bytes = p->workspace_bytes;
+  return RM_OK;
+}
+
+int64_t rm_plan_launches(rm_plan_t h) {
+  Plan* p = as_plan(h);
+  return p ? p->launches : -1;
+}
+
+rm_status_t rm_profile_enable(rm_plan_t h, int32_t on) {
+  Plan* p = as_plan(h);
+  if (!p) return fail(RM_ERR_ARG, "null plan");
+  p->prof = on != 0;
+  return RM_OK;
+}
+
+rm_status_t rm_profile_read(rm_plan_t h, int32_t kernel, double* total_ms, int64_t* launches) {
+  Plan* p = as_plan(h);
+  if (!p) return fail(RM_ERR_ARG, "null plan");
+  if (kernel < 0 || kernel >= RM_KERNEL_COUNT) return fail(RM_ERR_ARG, "bad kernel id");
+  RM_CUDA(cudaStreamSynchronize(p->stream), "rm_profile_read");
+  prof_collect(p);
+  if (total_ms) *total_ms = p->prof_ms[kernel];
+  if (launches) *launches = p->prof_n[kernel];
+  p->prof_ms[kernel] = 0.0;
+  p->prof_n[kernel] = 0;
+  return RM_OK;
+}
+
+rm_status_t rm_plan_destroy(rm_plan_t h) {
+  Plan* p = as_plan(h);
+  if (!p) return RM_OK;
+  cudaSetDevice(p->device);
+  cudaStreamSynchronize(p->stream);
+  free_plan(p);
+  return RM_OK;
+}
+
+}  // extern "C"

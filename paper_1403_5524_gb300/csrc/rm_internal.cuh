@@ -1,0 +1,117 @@
+// Internal declarations shared by the translation units of the R-matrix library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rm.h"
+
+namespace rm {
+
+// ---------------------------------------------------------------------------
+// device-side helpers
+// ---------------------------------------------------------------------------
+struct cplx {
+  double re, im;
+};
+__host__ __device__ inline cplx make_c(double r, double i) { return cplx{r, i}; }
+__host__ __device__ inline cplx operator+(cplx a, cplx b) { return cplx{a.re + b.re, a.im + b.im}; }
+__host__ __device__ inline cplx operator-(cplx a, cplx b) { return cplx{a.re - b.re, a.im - b.im}; }
+__host__ __device__ inline cplx operator*(cplx a, cplx b) {
+  return cplx{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+
+// Packed upper-triangle index p(i,j), i <= j.
+__host__ __device__ inline int64_t pair_index(int n, int i, int j) {
+  return (int64_t)i * n - ((int64_t)i * (i - 1)) / 2 + (j - i);
+}
+
+// ---------------------------------------------------------------------------
+// per-wave device data
+// ---------------------------------------------------------------------------
+struct WaveDev {
+  int n = 0;         // channels
+  int N = 0;         // poles
+  int Npad = 0;      // poles rounded up for aligned tiles
+  double a = 0.0;
+  int lmax = 0;
+  int32_t* l = nullptr;     // [n]
+  double* thr = nullptr;    // [n]
+  double* poles = nullptr;  // [Npad], padding = +huge
+  double* W = nullptr;      // [n * Npad], padding = 0
+  double* E = nullptr;      // [n_e] nudged energies for this wave
+  uint8_t* flags0 = nullptr;  // [n_e] flags from the nudge
+  int32_t* n_open = nullptr;  // [n_e]
+  // results of rm_run
+  double* eta = nullptr;      // [n_e]
+  double* sig_tot = nullptr;  // [n_e * n_sel]
+  double* sig_sel = nullptr;  // [n_e * n_sel * n]
+  uint8_t* flags = nullptr;   // [n_e]
+};
+
+struct Plan {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_waves = 0;
+  int64_t n_e = 0;
+  int prec = RM_PREC_FP64;
+  double delta = 0.05;
+  int slices = 0;
+  int n_sel = 1;
+  int32_t sel[RM_MAX_SEL] = {0};
+  int32_t* sel_dev = nullptr;
+  int chunk = 0;
+  int n_max = 0;
+  int sm_count = 0;
+  double* energies = nullptr;  // [n_e] raw mesh (device)
+  std::vector<WaveDev> waves;
+  // workspace
+  double* Rbuf = nullptr;  // [chunk * n_p_max]
+  double* asym = nullptr;  // [4 * chunk * n_max]: lam, s, sp, c
+  double* slot = nullptr;  // solve workspace, solve_slots * slot_doubles
+  int solve_slots = 0;
+  int64_t slot_doubles = 0;
+  int32_t* err_word = nullptr;  // device error word (0 = ok)
+  int64_t workspace_bytes = 0;
+  int64_t launches = 0;
+  bool ran = false;
+  // per-kernel event timing (rm_profile_enable)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_live[RM_KERNEL_COUNT];
+  double prof_ms[RM_KERNEL_COUNT] = {0};
+  int64_t prof_n[RM_KERNEL_COUNT] = {0};
+};
+
+// ---------------------------------------------------------------------------
+// kernels (host launchers); each returns cudaGetLastError() of its launch
+// ---------------------------------------------------------------------------
+// Validation of one wave's inputs on the device: sortedness, l range, NaN.
+cudaError_t launch_validate(const WaveDev& w, int N_real, const double* energies, int64_t n_e,
+                            int32_t* err_word, cudaStream_t s);
+// Nudge the mesh for one wave and count open channels.
+cudaError_t launch_prep(const WaveDev& w, const double* energies, int64_t n_e, cudaStream_t s);
+// R[e][p] = (1/2a) sum_k w_ik w_jk / (E_k - E_e) for e in [e0, e0+ne), FP64.
+cudaError_t launch_polesum_fp64(const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s);
+// Asymptotic data (lam, s, s', c) per (energy, channel) for e in [e0, e0+ne).
+cudaError_t launch_asym(const WaveDev& w, int64_t e0, int ne, double* asym, int ld_chunk,
+                        cudaStream_t s);
+// Matching LU -> K; complex LU of I - iK -> eigenphase sum, sigma.
+struct SolveOut {
+  double* K = nullptr;        // optional [ne * n * n]
+  double* eta = nullptr;      // optional [ne]
+  double* sig_tot = nullptr;  // optional [ne * n_sel]
+  double* sig_sel = nullptr;  // optional [ne * n_sel * n]
+  uint8_t* flags = nullptr;   // optional [ne]
+  int32_t* n_open = nullptr;  // optional [ne]
+  bool do_xsec = true;
+};
+cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, const double* R,
+                         const double* asym, int ld_chunk, const SolveOut& out, cudaStream_t s);
+size_t solve_smem_bytes(int n_max);
+int64_t solve_slot_doubles(int n_max, int n_sel);
+
+}  // namespace rm

@@ -1,0 +1,103 @@
+"""Host-only checks of the C ABI: the library loads, exports every function
+include/rm.h declares, and rejects bad arguments without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1403_5524_gb300 import rm, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "rm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rm_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return rm.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(rm.EXPORTS) <= set(names)
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert lib.rm_status_str(code)
+    assert lib.rm_status_str(99) == b"unknown status"
+
+
+def test_options_default(lib):
+    o = rm.rm_options()
+    lib.rm_options_default(C.byref(o))
+    assert o.prec == rm.RM_PREC_FP64 and abs(o.delta - 0.05) < 1e-15 and o.mem == rm.RM_MEM_HOST
+    assert o.chunk == 0 and o.n_sel == 0
+
+
+def _create(lib, waves, energies, opt=None, n_waves=None):
+    h = C.c_void_p()
+    warr = (rm.rm_wave * max(1, len(waves)))()
+    keep = []
+    for g, w in enumerate(waves):
+        keep += [w.l, w.thresh, w.poles, w.W]
+        warr[g].n_ch, warr[g].n_poles, warr[g].a = w.l.shape[0], w.poles.shape[0], w.a
+        warr[g].l, warr[g].thresh = w.l.ctypes.data, w.thresh.ctypes.data
+        warr[g].pole_E, warr[g].W = w.poles.ctypes.data, w.W.ctypes.data
+    code = lib.rm_plan_create(C.byref(h), warr, len(waves) if n_waves is None else n_waves,
+                              energies.ctypes.data if energies is not None else None,
+                              0 if energies is None else energies.shape[0],
+                              C.byref(opt) if opt is not None else None, None)
+    return code, h
+
+
+def test_bad_arguments_rejected_before_device(lib):
+    wl = synth.small(1, 4, 20, 5)
+    w = wl.waves[0]
+    assert lib.rm_plan_create(None, None, 0, None, 0, None, None) == rm.RM_ERR_ARG
+    code, h = _create(lib, [w], wl.energies, n_waves=0)
+    assert code == rm.RM_ERR_ARG and not h.value
+    bad = synth.Wave(l=w.l, thresh=w.thresh, poles=w.poles, W=w.W, a=-1.0)
+    assert _create(lib, [bad], wl.energies)[0] == rm.RM_ERR_ARG
+    o = rm.rm_options()
+    lib.rm_options_default(C.byref(o))
+    o.prec = 7
+    assert _create(lib, [w], wl.energies, o)[0] == rm.RM_ERR_ARG
+    o.prec = rm.RM_PREC_FP64
+    o.mem = 5
+    assert _create(lib, [w], wl.energies, o)[0] == rm.RM_ERR_ARG
+    o.mem = rm.RM_MEM_HOST
+    sel = np.array([0, -1], np.int32)
+    o.sel_init, o.n_sel = sel.ctypes.data, 2
+    assert _create(lib, [w], wl.energies, o)[0] == rm.RM_ERR_ARG
+    big = synth.Wave(l=np.zeros(700, np.int32), thresh=np.zeros(700), poles=w.poles,
+                     W=np.zeros((700, w.N)), a=1.0)
+    assert _create(lib, [big], wl.energies)[0] == rm.RM_ERR_ARG
+    assert lib.rm_last_error()
+
+
+def test_no_gpu_is_an_error_not_a_crash(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    wl = synth.small(1, 4, 20, 5)
+    code, h = _create(lib, wl.waves, wl.energies)
+    assert code == rm.RM_ERR_CUDA and not h.value
+    with pytest.raises(rm.RMError):
+        rm.Plan(wl.waves, wl.energies)
+
+
+def test_null_plan_calls(lib):
+    assert lib.rm_run(None) == rm.RM_ERR_ARG
+    assert lib.rm_sync(None) == rm.RM_ERR_ARG
+    assert lib.rm_plan_destroy(None) == rm.RM_OK
+    assert lib.rm_plan_launches(None) == -1
