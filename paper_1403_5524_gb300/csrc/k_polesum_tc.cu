@@ -1,0 +1,665 @@
+// Split-precision pole sum on the tcgen05 tensor cores (far poles) and the
+// FP64 near-pole window.
+//
+// The pole sum of Eq. 1 is the product of Eq. 2 in the packed form
+//   R(p, e) = (1/2a) sum_k P_pk D_ke,  P_pk = w_ik w_jk (p = (i <= j)),
+//   D_ke = 1 / (E_k - E_e),
+// a GEMM with M = pairs, K = poles, N = energies.  Neither operand exists in
+// global memory: each CTA forms its tile of P from TMA-staged rows of W and
+// its tile of D from the pole and energy values, in shared memory.
+//
+// Precision: both operands are scaled by powers of two to [-256, 256] (P per
+// pair, D per energy), formed in double-float (FP32 hi + lo, about 46 bits),
+// and cut into four slices: the nearest integer, the next 8 bits (multiples
+// of 2^-8), the next 8 bits (multiples of 2^-16) and the rest rounded to BF16.
+// The first three are exact in BF16; the last leaves an error below 2^-34 of
+// the scale.  Thirteen slice products are accumulated on the tensor cores:
+// all ten with u + v <= 3 and the three order-4 products (1,3), (2,2), (3,1)
+// that the four slices provide.  They go to four FP32 TMEM accumulators, one
+// per order (order 4 shares the order-3 one); orders 0-2 hold values on a
+// fixed grid, so their FP32 sums are exact while below 2^24 of that grid, and
+// the accumulators are drained into exact 64-bit fixed-point sums (unit
+// 2^-32) every 2048 poles.
+//
+// Poles with |E_k - E_e| < delta are excluded from the GEMM by per-energy pole
+// index ranges [klo, khi) and summed in FP64 by the near-window kernel, so the
+// two parts partition the pole set exactly.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "rm_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace rm {
+
+namespace {
+
+constexpr int BM = 128;                 // pairs per tile: 8 i-channels x 16 j-channels
+constexpr int BN = 128;                 // energies per tile
+constexpr int KS = 32;                  // poles per k-step (64-byte BF16 rows)
+constexpr int STAGES = 3;
+constexpr int NWORK = 16;               // producer / drain warps
+constexpr int NTHREADS = (NWORK + 1) * 32;
+constexpr int DRAIN_KSTEPS = 64;        // drain every 2048 poles
+constexpr int SLICE_BYTES = BM * KS * 2;          // 8 KB: 128 rows x 64 B
+constexpr int A_BYTES = 4 * SLICE_BYTES;          // 4 slices of P
+constexpr int B_BYTES = 4 * SLICE_BYTES;          // 4 slices of D
+constexpr int WI_FLOATS = 16 * KS;   // 8 channels x (hi, lo) rows
+constexpr int WJ_FLOATS = 32 * KS;   // 16 channels x (hi, lo) rows
+constexpr int PO_FLOATS = 2 * KS;    // poles hi row, lo row
+constexpr int TX_BYTES = (WI_FLOATS + WJ_FLOATS + PO_FLOATS) * 4;  // 6400
+constexpr int STAGE_STRIDE = ((A_BYTES + B_BYTES + TX_BYTES + 1023) / 1024) * 1024;
+constexpr int NBARS = 3 * STAGES + 3;
+constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_STRIDE + 1024 + NBARS * 8 + 16;
+constexpr long long WAIT_BUDGET = 4000000000LL;   // clock cycles (~2 s)
+
+static_assert(BM == 128 && BN == 128, "TMEM layout assumes 128 x 128 tiles");
+
+// byte offset of element (row r, k) in a K-major, 64-byte-swizzled slice
+__device__ __forceinline__ uint32_t swz(int r, int k) {
+  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((k >> 3) ^ ((r >> 1) & 3))) << 4) + ((k & 7) << 1));
+}
+
+// x = xh + xl (double-float, |x| <= 256) -> four slices: nearest integer,
+// then multiples of 2^-8 and of 2^-16, then the rest.  s0..s2 are exact in
+// BF16; s3 (|s3| <= 2^-17) is rounded to BF16 when packed.
+__device__ __forceinline__ void slice4(float xh, float xl, float (&s)[4]) {
+  const float h0 = __fsub_rn(__fadd_rn(xh, 12582912.0f), 12582912.0f);  // nearest integer
+  const float h1 = __fsub_rn(__fadd_rn(xh, 49152.0f), 49152.0f);        // nearest multiple of 2^-8
+  s[0] = h0;
+  s[1] = __fsub_rn(h1, h0);
+  const float r = __fadd_rn(__fsub_rn(xh, h1), xl);
+  s[2] = __fsub_rn(__fadd_rn(r, 192.0f), 192.0f);                       // nearest multiple of 2^-16
+  s[3] = __fsub_rn(r, s[2]);
+}
+
+// (ah + al)(bh + bl) -> (ph, pl), double-float product (error ~2^-46 relative)
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+  ph = __fmul_rn(ah, bh);
+  const float e = __fmaf_rn(ah, bh, -ph);
+  pl = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+}
+
+// 1 / ((kh + kl) - (eh + el)) as a double-float
+__device__ __forceinline__ void df_recip_diff(float kh, float kl, float eh, float el, float& rh, float& rl) {
+  // two-difference of the high parts, then add the low parts
+  const float s = __fsub_rn(kh, eh);
+  const float bb = __fsub_rn(s, kh);
+  const float err = __fsub_rn(__fsub_rn(kh, __fsub_rn(s, bb)), __fadd_rn(eh, bb));
+  const float dl0 = __fadd_rn(err, __fsub_rn(kl, el));
+  const float dh = __fadd_rn(s, dl0);
+  const float dl = __fsub_rn(dl0, __fsub_rn(dh, s));
+  rh = __frcp_rn(dh);
+  float c = __fmaf_rn(-dh, rh, 1.0f);  // exact residual of the rounded reciprocal
+  c = __fmaf_rn(-dl, rh, c);
+  rl = __fmul_rn(rh, c);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+struct TCArgs {
+  const float* mult_p;
+  const double* f_p;
+  const int32_t* klo;
+  const int32_t* khi;
+  const double* tau;
+  const float* mult_e;
+  const float* Eh;
+  const float* El;
+  const int2* tiles;
+  int n, N, nK;
+  int64_t e_begin;  // absolute index of the chunk's first energy
+  int ne;           // energies in the chunk
+  double* R;        // [ne * np]
+  int32_t* err;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    polesum_tc_kernel(const __grid_constant__ CUtensorMap map_omega, const __grid_constant__ CUtensorMap map_pol,
+                      TCArgs g) {
+  using namespace ptx;
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_STRIDE);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* wfull = bars + 2 * STAGES;
+  uint64_t* acc_full = bars + 3 * STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* done = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBARS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int2 tile = g.tiles[blockIdx.x];
+  const int I0 = tile.x * 8, J0 = tile.y * 16;
+  const int n0 = blockIdx.y * BN;
+  const int nK = g.nK;
+  const int n = g.n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + s, NWORK);
+      mbar_init(empty + s, 1);
+      mbar_init(wfull + s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, NWORK);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == NWORK) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == NWORK) {
+    // ------------------------------------------------ TMA + MMA issue (1 thread)
+    if (lane == 0) {
+      int tma_last[STAGES];
+      for (int s = 0; s < STAGES; ++s) tma_last[s] = -1;
+      auto issue_tma = [&](int s, int j) {
+        uint8_t* st = smem + s * STAGE_STRIDE;
+        float* WI = reinterpret_cast<float*>(st + A_BYTES + B_BYTES);
+        float* WJ = WI + WI_FLOATS;
+        float* PO = WJ + WJ_FLOATS;
+        mbar_arrive_expect_tx(wfull + s, TX_BYTES);
+        const int x = j * KS;
+        tma_load_2d(WI, &map_omega, wfull + s, x, 2 * I0);
+        tma_load_2d(WJ, &map_omega, wfull + s, x, 2 * J0);
+        tma_load_2d(WJ + 16 * KS, &map_omega, wfull + s, x, 2 * J0 + 16);
+        tma_load_2d(PO, &map_pol, wfull + s, x, 0);
+        tma_last[s] = j;
+      };
+      for (int s = 0; s < STAGES && s < nK; ++s) issue_tma(s, s);
+      const uint32_t idN256 = idesc_bf16_f32(128, 256);
+      const uint32_t idN128 = idesc_bf16_f32(128, 128);
+      bool ok = true;
+      bool issued = false;
+      for (int j = 0; j < nK; ++j) {
+        const int s = j % STAGES;
+        if (!mbar_wait(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) { ok = false; break; }
+        if (j + STAGES < nK) issue_tma(s, j + STAGES);
+        const int d = j / DRAIN_KSTEPS;
+        const bool first = (j % DRAIN_KSTEPS) == 0;
+        if (first && d > 0) {
+          if (!mbar_wait(acc_empty, (uint32_t)((d - 1) & 1), abort_flag, WAIT_BUDGET)) { ok = false; break; }
+        }
+        tc_fence_after();
+        const uint32_t a = smem_u32(smem + s * STAGE_STRIDE);
+        const uint32_t b = a + A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint32_t ko = kk * 32;
+          const uint32_t f = (first && kk == 0) ? 0u : 1u;
+          // columns: order 0 [0,128), 1 [128,256), 2 [256,384), 3 [384,512)
+          mma_bf16_ss(tmem + 0, desc_kmajor_sw64(a + 0 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 0 * SLICE_BYTES + ko), idN256, f);
+          mma_bf16_ss(tmem + 256, desc_kmajor_sw64(a + 0 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 2 * SLICE_BYTES + ko), idN256, f);
+          mma_bf16_ss(tmem + 128, desc_kmajor_sw64(a + 1 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 0 * SLICE_BYTES + ko), idN256, 1u);
+          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 1 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 2 * SLICE_BYTES + ko), idN128, 1u);
+          mma_bf16_ss(tmem + 256, desc_kmajor_sw64(a + 2 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 0 * SLICE_BYTES + ko), idN256, 1u);
+          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 3 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 0 * SLICE_BYTES + ko), idN128, 1u);
+          // order-4 products (1,3), (2,2), (3,1) into the order-3 accumulator
+          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 1 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 3 * SLICE_BYTES + ko), idN128, 1u);
+          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 2 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 2 * SLICE_BYTES + ko), idN128, 1u);
+          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 3 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 1 * SLICE_BYTES + ko), idN128, 1u);
+        }
+        issued = true;
+        mma_commit(empty + s);
+        if ((j + 1) % DRAIN_KSTEPS == 0 || j == nK - 1) mma_commit(acc_full);
+      }
+      if (!ok) {
+        // abort path: let in-flight TMA loads and MMAs finish before the CTA exits
+        const long long cleanup = 400000000LL;
+        for (int s = 0; s < STAGES; ++s) {
+          if (tma_last[s] < 0) continue;
+          const long long t0 = clock64();
+          while (!mbar_try_wait(wfull + s, (uint32_t)((tma_last[s] / STAGES) & 1)) && clock64() - t0 < cleanup) {
+          }
+        }
+        if (issued) {
+          mma_commit(done);
+          const long long t0 = clock64();
+          while (!mbar_try_wait(done, 0u) && clock64() - t0 < cleanup) {
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------- producers and drains
+    const int w = warp;
+    // A role: pair row rA = ai*16 + jj, k-pairs kpa + 2t
+    const int ai = w >> 1, jj = lane & 15, kpa = (w & 1) * 8 + (lane >> 4);
+    const int rA = ai * 16 + jj;
+    const int gi = I0 + ai, gj = J0 + jj;
+    float mp = 0.0f;
+    if (gi < n && gj < n && gi <= gj) mp = g.mult_p[pair_index(n, gi, gj)];
+    // B role: energy row rb, k-pairs kpb + 4t
+    const int rb = w * 8 + (lane & 7), kpb = lane >> 3;
+    const int eloc = n0 + rb;
+    float eh = 0.0f, el = 0.0f, me = 0.0f;
+    int klo = 0, khi = 0;
+    if (eloc < g.ne) {
+      const int64_t ge = g.e_begin + eloc;
+      eh = g.Eh[ge];
+      el = g.El[ge];
+      me = g.mult_e[ge];
+      klo = g.klo[ge];
+      khi = g.khi[ge];
+    }
+    const uint32_t trow = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(32 * (w >> 2));
+    long long V[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) V[c] = 0;
+    bool ok = true;
+    for (int j = 0; j < nK && ok; ++j) {
+      const int s = j % STAGES;
+      if (j >= STAGES && !mbar_wait(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, WAIT_BUDGET)) {
+        ok = false;
+        break;
+      }
+      if (!mbar_wait(wfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) {
+        ok = false;
+        break;
+      }
+      uint8_t* st = smem + s * STAGE_STRIDE;
+      const float* WI = reinterpret_cast<const float*>(st + A_BYTES + B_BYTES);
+      const float* WJ = WI + WI_FLOATS;
+      const float* PO = WJ + WJ_FLOATS;
+      uint8_t* Ab = st;
+      uint8_t* Bb = st + A_BYTES;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int k = 2 * (kpa + 2 * t);
+        const float2 wih = *reinterpret_cast<const float2*>(WI + (2 * ai) * KS + k);
+        const float2 wil = *reinterpret_cast<const float2*>(WI + (2 * ai + 1) * KS + k);
+        const float2 wjh = *reinterpret_cast<const float2*>(WJ + (2 * jj) * KS + k);
+        const float2 wjl = *reinterpret_cast<const float2*>(WJ + (2 * jj + 1) * KS + k);
+        float ph0, pl0, ph1, pl1;
+        df_mul(wih.x, wil.x, wjh.x, wjl.x, ph0, pl0);
+        df_mul(wih.y, wil.y, wjh.y, wjl.y, ph1, pl1);
+        float s0[4], s1[4];
+        slice4(__fmul_rn(ph0, mp), __fmul_rn(pl0, mp), s0);
+        slice4(__fmul_rn(ph1, mp), __fmul_rn(pl1, mp), s1);
+        const uint32_t off = swz(rA, k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + off) = pack_bf16x2(s0[u], s1[u]);
+      }
+      const int k0 = j * KS;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int k = 2 * (kpb + 4 * t);
+        const int kg = k0 + k;
+        const float2 ph = *reinterpret_cast<const float2*>(PO + k);
+        const float2 pl = *reinterpret_cast<const float2*>(PO + KS + k);
+        float rh0, rl0, rh1, rl1;
+        df_recip_diff(ph.x, pl.x, eh, el, rh0, rl0);
+        df_recip_diff(ph.y, pl.y, eh, el, rh1, rl1);
+        const bool far0 = (kg < klo || kg >= khi) && kg < g.N;
+        const bool far1 = (kg + 1 < klo || kg + 1 >= khi) && kg + 1 < g.N;
+        const float m0 = far0 ? me : 0.0f, m1 = far1 ? me : 0.0f;
+        float s0[4], s1[4];
+        slice4(__fmul_rn(rh0, m0), __fmul_rn(rl0, m0), s0);
+        slice4(__fmul_rn(rh1, m1), __fmul_rn(rl1, m1), s1);
+        const uint32_t off = swz(rb, k);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + off) = pack_bf16x2(s0[v], s1[v]);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full + s);
+      if ((j + 1) % DRAIN_KSTEPS == 0 || j == nK - 1) {
+        const int d = j / DRAIN_KSTEPS;
+        if (!mbar_wait(acc_full, (uint32_t)(d & 1), abort_flag, WAIT_BUDGET)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // fixed point with unit 2^-32 (of the product of the two [-256, 256] scales)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[16];
+            tmem_ld16(trow + (uint32_t)(o * 128 + h * 16), r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+              V[h * 16 + c] += (long long)__float2ll_rn(__fmul_rn(__uint_as_float(r[c]), 4294967296.0f));
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
+      }
+    }
+    // ------------------------------------------------------------- epilogue
+    if (ok) {
+      const int row = 32 * (w & 3) + lane;
+      const int pi = I0 + row / 16, pj = J0 + row % 16;
+      if (pi < n && pj < n && pi <= pj) {
+        const int64_t np = (int64_t)n * (n + 1) / 2;
+        const int64_t p = pair_index(n, pi, pj);
+        const double fp = g.f_p[p];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int e = n0 + 32 * (w >> 2) + c;
+          if (e < g.ne) g.R[(int64_t)e * np + p] = (double)V[c] * fp * g.tau[g.e_begin + e];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == NWORK) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicMax(g.err, (int)RM_ERR_TIMEOUT);
+}
+
+// ------------------------------------------------------------ preparation
+// sigma_i = 2^ceil(log2 max_k |w_ik|); w_ik / sigma_i as FP32 hi (row 2i) + lo (row 2i+1)
+__global__ void prep_omega_kernel(const double* __restrict__ W, int n, int N, int Npad, double* __restrict__ sigma,
+                                  float* __restrict__ omega) {
+  const int i = blockIdx.x;
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) m = fmax(m, fabs(W[(int64_t)i * Npad + k]));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) mm = fmax(mm, red[q]);
+    int ex = 0;
+    double sg = 1.0;
+    if (mm > 0.0) {
+      frexp(mm, &ex);  // mm = f 2^ex, f in [0.5, 1)
+      sg = ldexp(1.0, ex);
+    }
+    red[0] = sg;
+    sigma[i] = sg;
+  }
+  __syncthreads();
+  const double inv = 1.0 / red[0];  // power of two: exact
+  for (int k = threadIdx.x; k < Npad; k += blockDim.x) {
+    float h = 0.0f, l = 0.0f;
+    if (k < N) {
+      const double v = W[(int64_t)i * Npad + k] * inv;
+      h = (float)v;
+      l = (float)(v - (double)h);
+    }
+    omega[(int64_t)(2 * i) * Npad + k] = h;
+    omega[(int64_t)(2 * i + 1) * Npad + k] = l;
+  }
+}
+
+__global__ void prep_pol_kernel(const double* __restrict__ poles, int N, int Npad, float* __restrict__ pol) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Npad) return;
+  float h = 0.0f, l = 0.0f;
+  if (k < N) {
+    h = (float)poles[k];
+    l = (float)(poles[k] - (double)h);
+  }
+  pol[k] = h;
+  pol[Npad + k] = l;
+}
+
+// per pair: 2^e_p with max_k |fl(omega_i omega_j)| 2^e_p <= 1; mult_p = 2^(e_p+8),
+// f_p = sigma_i sigma_j 2^-e_p 2^-48 / (2a)  (2^-16 for the two 2^8 scales,
+// 2^-32 for the fixed-point unit of the drained sums)
+__global__ void prep_pairs_kernel(const float* __restrict__ omega, const double* __restrict__ sigma, int n, int N,
+                                  int Npad, double inv2a, float* __restrict__ mult_p, double* __restrict__ f_p) {
+  const int64_t np = (int64_t)n * (n + 1) / 2;
+  const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= np) return;
+  const int lane = threadIdx.x & 31;
+  // unpack p -> (i, j)
+  const double b = 2.0 * n + 1.0;
+  int i = (int)floor((b - sqrt(b * b - 8.0 * (double)p)) * 0.5);
+  if (i < 0) i = 0;
+  while (i > 0 && pair_index(n, i, i) > p) --i;
+  while (i + 1 < n && pair_index(n, i + 1, i + 1) <= p) ++i;
+  const int j = i + (int)(p - pair_index(n, i, i));
+  const float* wi = omega + (int64_t)(2 * i) * Npad;
+  const float* wj = omega + (int64_t)(2 * j) * Npad;
+  float m = 0.0f;
+  for (int k = lane; k < N; k += 32) m = fmaxf(m, fabsf(__fmul_rn(wi[k], wj[k])));
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, off));
+  if (lane == 0) {
+    if (m == 0.0f) {
+      mult_p[p] = 0.0f;
+      f_p[p] = 0.0;
+    } else {
+      int ex = 0;
+      frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1)
+      int ep = -ex;
+      if (ep > 110) ep = 110;
+      mult_p[p] = ldexpf(1.0f, ep + 8);
+      f_p[p] = ldexp(sigma[i] * sigma[j], -ep - 48) * inv2a;
+    }
+  }
+}
+
+__device__ inline int lower_bound_d(const double* v, int m, double x) {
+  int lo = 0, hi = m;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ inline int upper_bound_d(const double* v, int m, double x) {
+  int lo = 0, hi = m;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// per energy: near window [klo, khi) = {k : |E_k - E| < delta}, the power-of-two
+// scale tau >= max over far poles of |1/(E_k - E)|, and E split into FP32 hi + lo
+__global__ void prep_energy_split_kernel(const double* __restrict__ E, int64_t n_e, const double* __restrict__ poles,
+                                         int N, double delta, int32_t* __restrict__ klo, int32_t* __restrict__ khi,
+                                         double* __restrict__ tau, float* __restrict__ mult_e, float* __restrict__ Eh,
+                                         float* __restrict__ El) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_e) return;
+  const double x = E[e];
+  const int lo = upper_bound_d(poles, N, x - delta);  // first E_k > x - delta
+  const int hi = lower_bound_d(poles, N, x + delta);  // first E_k >= x + delta
+  double dmin = INFINITY;
+  if (lo > 0) dmin = fmin(dmin, x - poles[lo - 1]);
+  if (hi < N) dmin = fmin(dmin, poles[hi] - x);
+  double t = 1.0;
+  if (dmin < INFINITY && dmin > 0.0) {
+    int ex = 0;
+    frexp(1.001 / dmin, &ex);
+    t = ldexp(1.0, ex);
+  }
+  klo[e] = lo;
+  khi[e] = hi;
+  tau[e] = t;
+  mult_e[e] = (float)(256.0 / t);
+  const float h = (float)x;
+  Eh[e] = h;
+  El[e] = (float)(x - (double)h);
+}
+
+// ------------------------------------------------------- near-pole window
+constexpr int NEB = 8;    // energies per CTA
+constexpr int NKP = 32;   // poles per staged piece
+constexpr int NNT = 256;  // threads
+
+__global__ void __launch_bounds__(NNT) near_kernel(const double* __restrict__ W, int n, int Npad,
+                                                   const double* __restrict__ poles, const double* __restrict__ E,
+                                                   const int32_t* __restrict__ klo, const int32_t* __restrict__ khi,
+                                                   int ne, double inv2a, int splits, double* __restrict__ R) {
+  extern __shared__ double nsm[];
+  double* Ws = nsm;                       // [n][NKP + 1]
+  double* Dm = Ws + (size_t)n * (NKP + 1);  // [NEB][NKP]
+  const int e0 = blockIdx.x * NEB;
+  const int e1 = min(ne, e0 + NEB);
+  if (e0 >= ne) return;
+  const int64_t np = (int64_t)n * (n + 1) / 2;
+  const int64_t pb = np * blockIdx.y / splits, pe = np * (blockIdx.y + 1) / splits;
+  const int Klo = klo[e0], Khi = khi[e1 - 1];
+  const int t = threadIdx.x;
+  for (int Ks = Klo; Ks < Khi; Ks += NKP) {
+    for (int idx = t; idx < n * NKP; idx += NNT) {
+      const int i = idx / NKP, kk = idx % NKP;
+      Ws[i * (NKP + 1) + kk] = (Ks + kk < Khi) ? W[(int64_t)i * Npad + Ks + kk] : 0.0;
+    }
+    for (int idx = t; idx < NEB * NKP; idx += NNT) {
+      const int e = idx / NKP, kk = idx % NKP;
+      const int k = Ks + kk;
+      double v = 0.0;
+      if (e0 + e < e1 && k >= klo[e0 + e] && k < khi[e0 + e]) v = inv2a / (poles[k] - E[e0 + e]);
+      Dm[idx] = v;
+    }
+    __syncthreads();
+    // this thread's first pair
+    int64_t p = pb + t;
+    if (p < pe) {
+      const double b = 2.0 * n + 1.0;
+      int i = (int)floor((b - sqrt(b * b - 8.0 * (double)p)) * 0.5);
+      if (i < 0) i = 0;
+      while (i > 0 && pair_index(n, i, i) > p) --i;
+      while (i + 1 < n && pair_index(n, i + 1, i + 1) <= p) ++i;
+      int j = i + (int)(p - pair_index(n, i, i));
+      for (; p < pe; p += NNT) {
+        double P[NKP];
+#pragma unroll
+        for (int kk = 0; kk < NKP; ++kk) P[kk] = Ws[i * (NKP + 1) + kk] * Ws[j * (NKP + 1) + kk];
+        for (int e = 0; e < e1 - e0; ++e) {
+          double acc = 0.0;
+#pragma unroll
+          for (int kk = 0; kk < NKP; ++kk) acc = fma(P[kk], Dm[e * NKP + kk], acc);
+          R[(int64_t)(e0 + e) * np + p] += acc;
+        }
+        j += NNT;
+        while (j >= n && i < n - 1) {
+          ++i;
+          j = j - n + i;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* ptr = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+bool encode_2d_f32(CUtensorMap* map, const float* base, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                   uint32_t box_rows) {
+  auto enc = get_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * sizeof(float)};
+  cuuint32_t box[2] = {box_cols, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t polesum_tc_smem_bytes() { return TC_SMEM; }
+
+std::vector<int2> split_tiles(int n) {
+  std::vector<int2> t;
+  const int nbi = (n + 7) / 8, nbj = (n + 15) / 16;
+  for (int I = 0; I < nbi; ++I)
+    for (int J = 0; J < nbj; ++J)
+      if (16 * J + 15 >= 8 * I) t.push_back(make_int2(I, J));
+  return t;
+}
+
+cudaError_t split_prepare(const Plan& p, WaveDev& w, cudaStream_t s) {
+  SplitDev& sd = w.split;
+  prep_omega_kernel<<<w.n, 256, 0, s>>>(w.W, w.n, w.N, w.Npad, sd.sigma, sd.omega);
+  prep_pol_kernel<<<(w.Npad + 255) / 256, 256, 0, s>>>(w.poles, w.N, w.Npad, sd.pol);
+  const int64_t np = (int64_t)w.n * (w.n + 1) / 2;
+  prep_pairs_kernel<<<(unsigned)((np + 7) / 8), 256, 0, s>>>(sd.omega, sd.sigma, w.n, w.N, w.Npad, 1.0 / (2.0 * w.a),
+                                                             sd.mult_p, sd.f_p);
+  if (p.n_e > 0)
+    prep_energy_split_kernel<<<(unsigned)((p.n_e + 255) / 256), 256, 0, s>>>(
+        w.E, p.n_e, w.poles, w.N, p.delta, sd.klo, sd.khi, sd.tau, sd.mult_e, sd.Eh, sd.El);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (!encode_2d_f32(&sd.map_omega, sd.omega, (uint64_t)w.Npad, (uint64_t)(2 * w.n), KS, 16))
+    return cudaErrorInvalidValue;
+  if (!encode_2d_f32(&sd.map_pol, sd.pol, (uint64_t)w.Npad, 2, KS, 2)) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+cudaError_t launch_polesum_split(const Plan& p, const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s) {
+  if (ne <= 0) return cudaSuccess;
+  const SplitDev& sd = w.split;
+  TCArgs g;
+  g.mult_p = sd.mult_p;
+  g.f_p = sd.f_p;
+  g.klo = sd.klo;
+  g.khi = sd.khi;
+  g.tau = sd.tau;
+  g.mult_e = sd.mult_e;
+  g.Eh = sd.Eh;
+  g.El = sd.El;
+  g.tiles = sd.tiles;
+  g.n = w.n;
+  g.N = w.N;
+  g.nK = w.Npad / KS;
+  g.e_begin = e0;
+  g.ne = ne;
+  g.R = R;
+  g.err = p.err_word;
+  cudaError_t err = cudaFuncSetAttribute(polesum_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  if (err != cudaSuccess) return err;
+  dim3 grid(sd.n_tiles, (ne + BN - 1) / BN);
+  polesum_tc_kernel<<<grid, NTHREADS, TC_SMEM, s>>>(sd.map_omega, sd.map_pol, g);
+  return cudaGetLastError();
+}
+
+size_t near_smem_bytes(int n) { return ((size_t)n * (NKP + 1) + NEB * NKP) * sizeof(double); }
+
+cudaError_t launch_near(const Plan& p, const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s) {
+  if (ne <= 0) return cudaSuccess;
+  const size_t smem = near_smem_bytes(w.n);
+  cudaError_t err = cudaFuncSetAttribute(near_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int blocks = (ne + NEB - 1) / NEB;
+  int splits = (2 * p.sm_count + blocks - 1) / blocks;
+  if (splits < 1) splits = 1;
+  if (splits > 64) splits = 64;
+  dim3 grid(blocks, splits);
+  near_kernel<<<grid, NNT, smem, s>>>(w.W, w.n, w.Npad, w.poles, w.E + e0, w.split.klo + e0, w.split.khi + e0, ne,
+                                      1.0 / (2.0 * w.a), splits, R);
+  return cudaGetLastError();
+}
+
+}  // namespace rm

@@ -53,6 +53,9 @@ void free_plan(Plan* p) {
   for (auto& w : p->waves) {
     dfree(w.l); dfree(w.thr); dfree(w.poles); dfree(w.W); dfree(w.E); dfree(w.flags0);
     dfree(w.n_open); dfree(w.eta); dfree(w.sig_tot); dfree(w.sig_sel); dfree(w.flags);
+    SplitDev& sd = w.split;
+    dfree(sd.omega); dfree(sd.pol); dfree(sd.sigma); dfree(sd.mult_p); dfree(sd.f_p); dfree(sd.klo);
+    dfree(sd.khi); dfree(sd.tau); dfree(sd.mult_e); dfree(sd.Eh); dfree(sd.El); dfree(sd.tiles);
   }
   dfree(p->energies); dfree(p->sel_dev); dfree(p->Rbuf); dfree(p->asym); dfree(p->slot);
   dfree(p->err_word);
@@ -130,6 +133,10 @@ rm_status_t prepare(Plan* p, const rm_wave* waves, const double* energies, int32
       p->launches++;
     }
     if (p->n_e > 0) RM_CUDA(cudaMemsetAsync(d.flags, 0, p->n_e, s), "clear flags");
+    if (p->prec == RM_PREC_SPLIT_BF16) {
+      RM_CUDA(split_prepare(*p, d, s), "split-precision preparation");
+      p->launches += 4;
+    }
   }
   RM_CUDA(cudaStreamSynchronize(s), "prepare");
   for (int g = 0; g < p->n_waves; ++g)
@@ -204,7 +211,15 @@ rm_status_t polesum_chunk(Plan* p, const WaveDev& w, int64_t c0, int ne, double*
     RM_CUDA(launch_polesum_fp64(w, c0, ne, R, p->stream), "FP64 pole-sum kernel");
     return RM_OK;
   }
-  return fail(RM_ERR_ARG, "precision mode not available in this build");
+  {
+    Prof pr(p, RM_KERNEL_POLESUM_SPLIT);
+    RM_CUDA(launch_polesum_split(*p, w, c0, ne, R, p->stream), "split pole-sum kernel");
+  }
+  {
+    Prof pr(p, RM_KERNEL_NEAR);
+    RM_CUDA(launch_near(*p, w, c0, ne, R, p->stream), "near-window kernel");
+  }
+  return RM_OK;
 }
 
 // Pipeline over [e0, e1) for one wave.  Any output may be null; device outputs
@@ -242,6 +257,15 @@ rm_status_t run_range(Plan* p, int32_t wave, int64_t e0, int64_t e1, const Range
       RM_CUDA(launch_solve(*p, w, c0, ne, R, p->asym, ld, so, p->stream), "solve kernel");
     }
   }
+  return RM_OK;
+}
+
+// Read the device error word (after the stream was synchronised).
+rm_status_t check_err_word(Plan* p) {
+  int32_t err = 0;
+  RM_CUDA(cudaMemcpy(&err, p->err_word, sizeof(int32_t), cudaMemcpyDeviceToHost), "read error word");
+  if (err == RM_ERR_TIMEOUT) return fail(RM_ERR_TIMEOUT, "a device-side wait ran out (tensor-core pipeline)");
+  if (err != 0) return fail((rm_status_t)err, "device reported an error");
   return RM_OK;
 }
 
@@ -371,12 +395,33 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if ((st = dalloc(p, &d.sig_tot, n_e * n_sel)) != RM_OK) break;
       if ((st = dalloc(p, &d.sig_sel, n_e * n_sel * d.n)) != RM_OK) break;
       if ((st = dalloc(p, &d.flags, n_e)) != RM_OK) break;
+      if (o.prec == RM_PREC_SPLIT_BF16) {
+        SplitDev& sd = d.split;
+        if ((st = dalloc(p, &sd.omega, 2ll * d.n * d.Npad)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.pol, 2ll * d.Npad)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.sigma, d.n)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.mult_p, np)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.f_p, np)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.klo, n_e)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.khi, n_e)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.tau, n_e)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.mult_e, n_e)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.Eh, n_e)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.El, n_e)) != RM_OK) break;
+        std::vector<int2> tl = split_tiles(d.n);
+        sd.n_tiles = (int)tl.size();
+        if ((st = dalloc(p, &sd.tiles, sd.n_tiles)) != RM_OK) break;
+        if (cudaMemcpy(sd.tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+          st = fail(RM_ERR_CUDA, "copy tile list");
+          break;
+        }
+      }
     }
     p->n_max = n_max;
     if (st == RM_OK) {
       int chunk = o.chunk;
       if (chunk == 0) {
-        const int64_t budget = 96ll << 20;
+        const int64_t budget = (o.prec == RM_PREC_SPLIT_BF16 ? 288ll : 96ll) << 20;
         int64_t c = budget / (np_max * 8) / 128 * 128;
         c = c < 128 ? 128 : (c > 8192 ? 8192 : c);
         chunk = (int)c;
@@ -399,6 +444,10 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     }
     if (st == RM_OK && solve_smem_bytes(n_max) > (size_t)prop.sharedMemPerBlockOptin)
       st = fail(RM_ERR_ARG, "n_ch too large for the solve kernel's shared memory");
+    if (st == RM_OK && o.prec == RM_PREC_SPLIT_BF16 &&
+        (polesum_tc_smem_bytes() > (size_t)prop.sharedMemPerBlockOptin ||
+         near_smem_bytes(n_max) > (size_t)prop.sharedMemPerBlockOptin))
+      st = fail(RM_ERR_ARG, "split-precision kernels do not fit this device's shared memory");
     if (st == RM_OK) st = prepare(p, waves, energies, o.mem);
     if (st != RM_OK) {
       free_plan(p);
@@ -452,7 +501,7 @@ rm_status_t rm_rmatrix(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double
                               cudaMemcpyDeviceToHost, p->stream), "copy R");
       RM_CUDA(cudaStreamSynchronize(p->stream), "rm_rmatrix");
     }
-    return RM_OK;
+    return check_err_word(p);
   } catch (...) {
     return fail(RM_ERR_NOMEM, "unexpected host exception");
   }
@@ -478,7 +527,10 @@ rm_status_t rm_kmatrix(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double
     if ((st = copy_back(p, K, o.so.K, ne * w.n * w.n, mem)) != RM_OK) return st;
     if ((st = copy_back(p, n_open, o.so.n_open, ne, mem)) != RM_OK) return st;
     if ((st = copy_back(p, flags, o.so.flags, ne, mem)) != RM_OK) return st;
-    if (mem == RM_MEM_HOST) RM_CUDA(cudaStreamSynchronize(p->stream), "rm_kmatrix");
+    if (mem == RM_MEM_HOST) {
+      RM_CUDA(cudaStreamSynchronize(p->stream), "rm_kmatrix");
+      return check_err_word(p);
+    }
     return RM_OK;
   } catch (...) {
     return fail(RM_ERR_NOMEM, "unexpected host exception");
@@ -505,7 +557,10 @@ rm_status_t rm_xsec(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* e
     if ((st = copy_back(p, eigsum, o.so.eta, ne, mem)) != RM_OK) return st;
     if ((st = copy_back(p, sig_tot, o.so.sig_tot, ne * p->n_sel, mem)) != RM_OK) return st;
     if ((st = copy_back(p, sig_sel, o.so.sig_sel, ne * p->n_sel * w.n, mem)) != RM_OK) return st;
-    if (mem == RM_MEM_HOST) RM_CUDA(cudaStreamSynchronize(p->stream), "rm_xsec");
+    if (mem == RM_MEM_HOST) {
+      RM_CUDA(cudaStreamSynchronize(p->stream), "rm_xsec");
+      return check_err_word(p);
+    }
     return RM_OK;
   } catch (...) {
     return fail(RM_ERR_NOMEM, "unexpected host exception");
@@ -558,7 +613,10 @@ rm_status_t rm_results(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double
       if (n_open) RM_CUDA(cudaMemcpyAsync(n_open, w.n_open + e0, sizeof(int32_t) * ne, k, s), "copy n_open");
       if (flags) RM_CUDA(cudaMemcpyAsync(flags, w.flags + e0, ne, k, s), "copy flags");
     }
-    if (mem == RM_MEM_HOST) RM_CUDA(cudaStreamSynchronize(s), "rm_results");
+    if (mem == RM_MEM_HOST) {
+      RM_CUDA(cudaStreamSynchronize(s), "rm_results");
+      return check_err_word(p);
+    }
     return RM_OK;
   } catch (...) {
     return fail(RM_ERR_NOMEM, "unexpected host exception");
@@ -569,10 +627,7 @@ rm_status_t rm_sync(rm_plan_t h) {
   Plan* p = as_plan(h);
   if (!p) return fail(RM_ERR_ARG, "null plan");
   RM_CUDA(cudaStreamSynchronize(p->stream), "rm_sync");
-  int32_t err = 0;
-  RM_CUDA(cudaMemcpy(&err, p->err_word, sizeof(int32_t), cudaMemcpyDeviceToHost), "read error word");
-  if (err == RM_ERR_TIMEOUT) return fail(RM_ERR_TIMEOUT, "a device-side wait ran out");
-  return RM_OK;
+  return check_err_word(p);
 }
 
 rm_status_t rm_plan_info(rm_plan_t h, int32_t wave, int32_t* n_ch, int32_t* n_poles, int64_t* n_e,

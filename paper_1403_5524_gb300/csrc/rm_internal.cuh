@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the R-matrix library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +33,25 @@ __host__ __device__ inline int64_t pair_index(int n, int i, int j) {
 // ---------------------------------------------------------------------------
 // per-wave device data
 // ---------------------------------------------------------------------------
+// Split-precision pole-sum data (RM_PREC_SPLIT_BF16).
+struct SplitDev {
+  float* omega = nullptr;   // [2n * Npad] w_ik / sigma_i: FP32 hi row 2i, lo row 2i+1
+  float* pol = nullptr;     // [2 * Npad] poles as FP32 hi (row 0) + lo (row 1)
+  double* sigma = nullptr;  // [n] power-of-two channel scales
+  float* mult_p = nullptr;  // [n_p] 2^(e_p + 8)
+  double* f_p = nullptr;    // [n_p] sigma_i sigma_j 2^-e_p 2^-48 / (2a)
+  int32_t* klo = nullptr;   // [n_e] near window [klo, khi) in pole indices
+  int32_t* khi = nullptr;
+  double* tau = nullptr;    // [n_e] power-of-two D scale
+  float* mult_e = nullptr;  // [n_e] 256 / tau
+  float* Eh = nullptr;      // [n_e] energy FP32 hi
+  float* El = nullptr;      // [n_e] energy FP32 lo
+  int2* tiles = nullptr;    // [n_tiles] (8-channel i-block, 16-channel j-block)
+  int n_tiles = 0;
+  CUtensorMap map_omega;  // TMA descriptors (64-byte aligned type)
+  CUtensorMap map_pol;
+};
+
 struct WaveDev {
   int n = 0;         // channels
   int N = 0;         // poles
@@ -50,6 +70,7 @@ struct WaveDev {
   double* sig_tot = nullptr;  // [n_e * n_sel]
   double* sig_sel = nullptr;  // [n_e * n_sel * n]
   uint8_t* flags = nullptr;   // [n_e]
+  SplitDev split;
 };
 
 struct Plan {
@@ -113,5 +134,13 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
                          const double* asym, int ld_chunk, const SolveOut& out, cudaStream_t s);
 size_t solve_smem_bytes(int n_max);
 int64_t solve_slot_doubles(int n_max, int n_sel);
+
+// split-precision pole sum
+std::vector<int2> split_tiles(int n);
+cudaError_t split_prepare(const Plan& p, WaveDev& w, cudaStream_t s);
+cudaError_t launch_polesum_split(const Plan& p, const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s);
+cudaError_t launch_near(const Plan& p, const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s);
+size_t polesum_tc_smem_bytes();
+size_t near_smem_bytes(int n);
 
 }  // namespace rm

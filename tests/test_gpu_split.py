@@ -1,0 +1,158 @@
+"""Parity of the split-precision path (sliced BF16 tcgen05 pole sum + FP64
+near-pole window + FP64 solves) with the FP64 CPU oracle (needs a GPU).
+
+Tolerances:
+* R per element: each far term P_pk D_ke carries the FP32 rounding of omega_i,
+  omega_j, their product and of D (difference and reciprocal), at most about
+  6 * 2^-24 relative; slicing and accumulation are exact.  So
+  |R - R*| <= 4e-7 (1/2a) sum_k |w_ik w_jk / (E_k - E)|, checked per element.
+* R, K normwise <= 1e-6 and sigma <= 1e-8 (normalised by sigma_tot of the
+  initial channel): the accuracy targets of the method's split form, on
+  energies the oracle does not flag ILLCOND.
+"""
+import numpy as np
+import pytest
+
+from oracle import rmatrix as orc
+from paper_1403_5524_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_R_NORM = 1e-6
+TOL_K = 1e-6
+TOL_SIG = 1e-8
+
+
+@pytest.fixture(scope="module")
+def rm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1403_5524_gb300 import rm as _rm
+    _rm.load_library()
+    return _rm
+
+
+def abs_sum(w, E):
+    d = np.abs(1.0 / (w.poles - E))
+    return (np.abs(w.W) * d[None, :]) @ np.abs(w.W).T / (2.0 * w.a)
+
+
+def run_split(rm, wl, sel=(0,), idx=None, chunk=0, delta=None):
+    w = wl.waves[0]
+    n = w.n
+    idx = np.arange(wl.n_e) if idx is None else np.asarray(idx)
+    out = {"R": [], "K": [], "eta": [], "sig": [], "flags": [], "n_open": []}
+    with rm.Plan(wl.waves, wl.energies, prec="split_bf16", delta=wl.delta if delta is None else delta,
+                 sel=sel, chunk=chunk) as p:
+        for e in idx:
+            e = int(e)
+            R = np.zeros((1, n * (n + 1) // 2))
+            p.rmatrix(0, e, e + 1, R)
+            K = np.zeros((1, n, n))
+            no = np.zeros(1, np.int32)
+            fl = np.zeros(1, np.uint8)
+            p.kmatrix(0, e, e + 1, K=K, n_open=no, flags=fl)
+            eta = np.zeros(1)
+            sig = np.zeros((1, len(sel), n))
+            p.xsec(0, e, e + 1, eigsum=eta, sig_sel=sig)
+            out["R"].append(R[0]); out["K"].append(K[0]); out["eta"].append(eta[0]); out["sig"].append(sig[0])
+            out["flags"].append(fl[0]); out["n_open"].append(no[0])
+    return {k: np.array(v) for k, v in out.items()}
+
+
+def check(wl, g, ref, per_element=True):
+    w = wl.waves[0]
+    n = w.n
+    worst = {"R": 0.0, "K": 0.0, "sig": 0.0}
+    for t in range(ref["E"].shape[0]):
+        Rg = orc.unpack_upper(g["R"][t], n)
+        Ro = orc.unpack_upper(ref["R"][t], n)
+        if per_element:
+            bound = 4e-7 * abs_sum(w, ref["E"][t]) + 1e-300
+            assert np.all(np.abs(Rg - Ro) <= bound), (t, float(np.max(np.abs(Rg - Ro) / bound)))
+        eR = np.abs(Rg - Ro).max() / np.abs(Ro).max()
+        worst["R"] = max(worst["R"], eR)
+        assert eR <= TOL_R_NORM, (t, eR)
+        assert g["n_open"][t] == ref["n_open"][t]
+        if ref["flags"][t] & (orc.FLAG_ILLCOND | orc.FLAG_SINGULAR | orc.FLAG_NO_OPEN):
+            continue
+        no = ref["n_open"][t]
+        Ko = ref["K"][t, :no, :no]
+        eK = np.abs(g["K"][t, :no, :no] - Ko).max() / np.abs(Ko).max()
+        worst["K"] = max(worst["K"], eK)
+        assert eK <= TOL_K, (t, eK)
+        for q in range(ref["sig_tot"].shape[1]):
+            st = ref["sig_tot"][t, q]
+            if st > 0:
+                eS = np.abs(g["sig"][t, q] - ref["sig_sel"][t, q]).max() / st
+                worst["sig"] = max(worst["sig"], eS)
+                assert eS <= TOL_SIG, (t, q, eS)
+    return worst
+
+
+@pytest.mark.parametrize("seed,n,N,ne", [(1, 4, 200, 40), (2, 9, 513, 30), (3, 17, 1000, 25), (4, 33, 2049, 20),
+                                         (5, 130, 700, 12)])
+def test_split_small(rm, seed, n, N, ne):
+    # ragged channel counts (not multiples of 8/16), poles not multiples of 32,
+    # pole density high enough that every energy has a near window
+    wl = synth.small(seed, n, N, ne, e_lo=0.05, e_hi=3.5, pole_lo=-3.0, pole_hi=12.0, a=20.0, delta=0.05)
+    sel = (0, min(1, n - 1))
+    g = run_split(rm, wl, sel=sel)
+    ref = orc.sweep(wl.waves[0], wl.energies, sel=sel)
+    check(wl, g, ref)
+
+
+def test_split_window_edges(rm):
+    # energies placed exactly delta away from poles, and on poles (nudged)
+    wl = synth.small(11, 6, 300, 1, pole_lo=0.0, pole_hi=4.0, a=15.0)
+    w = wl.waves[0]
+    E = np.sort(np.array([w.poles[40] + 0.05, w.poles[80] - 0.05, w.poles[120], w.poles[160] + 0.0499999,
+                          1.7, 2.2]))
+    wl2 = synth.Workload("edges", [w], E, delta=0.05)
+    g = run_split(rm, wl2, sel=(0,))
+    ref = orc.sweep(w, E, sel=(0,))
+    check(wl2, g, ref)
+
+
+def test_split_chunk_tiles_and_run(rm):
+    # energies across several 128-energy tiles and chunks; rm_run equals rm_xsec
+    wl = synth.small(12, 20, 800, 300, e_lo=0.02, e_hi=3.0, pole_lo=-2.0, pole_hi=8.0, a=18.0)
+    w = wl.waves[0]
+    sel = (0, 3)
+    with rm.Plan(wl.waves, wl.energies, prec="split_bf16", delta=0.05, sel=sel, chunk=256) as p:
+        p.run()
+        out = rm.host_outputs(wl.n_e, w.n, 2)
+        p.results(0, 0, wl.n_e, **out)
+        out2 = rm.host_outputs(wl.n_e, w.n, 2)
+        p.xsec(0, 0, wl.n_e, eigsum=out2["eigsum"], sig_tot=out2["sig_tot"], sig_sel=out2["sig_sel"])
+        p.sync()
+    assert np.array_equal(out["sig_sel"], out2["sig_sel"])
+    assert np.array_equal(out["eigsum"], out2["eigsum"])
+    idx = np.arange(0, wl.n_e, 23)
+    ref = orc.sweep(w, wl.energies, sel=sel, energy_idx=idx)
+    for t, e in enumerate(idx):
+        if ref["flags"][t] & orc.FLAG_ILLCOND:
+            continue
+        for q in range(2):
+            st = ref["sig_tot"][t, q]
+            if st > 0:
+                assert np.abs(out["sig_sel"][e, q] - ref["sig_sel"][t, q]).max() / st <= TOL_SIG
+
+
+def test_split_deterministic(rm):
+    wl = synth.small(13, 24, 900, 16)
+    a = run_split(rm, wl)
+    b = run_split(rm, wl)
+    for k in ("R", "K", "eta", "sig"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_split_config3_sampled(rm):
+    # the full n_ch=256, N=20000 workload, checked on sampled energies of the mesh
+    wl = synth.config(3)
+    idx = np.linspace(0, wl.n_e - 1, 6).astype(int)
+    g = run_split(rm, wl, sel=(0,), idx=idx)
+    ref = orc.sweep(wl.waves[0], wl.energies, sel=(0,), energy_idx=idx)
+    worst = check(wl, g, ref, per_element=False)
+    print("config3 split worst normwise errors", worst)
