@@ -30,6 +30,32 @@ from paper_1403_5524_gb300 import synth  # noqa: E402
 
 METRIC = "energies/sec (R+K+σ) split-precision vs FP64 GPU at n_ch=256; max rel err"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU
+SPLIT_PRODUCTS = 13      # BF16 slice products per far term in the tensor-core pole sum
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def split_tiles(n):
+    """Pair tiles of the tensor-core kernel: 8-channel i-blocks x 16-channel j-blocks with some i <= j."""
+    return sum(1 for I in range((n + 7) // 8) for J in range((n + 15) // 16) if 16 * J + 15 >= 8 * I)
+
+
+def tensor_flops(wl, chunk):
+    """Tensor-pipe FLOPs the split kernel issues per step (13 products, padded tiles)."""
+    tot = 0.0
+    for w in wl.waves:
+        npad = (w.N + 63) // 64 * 64
+        ntile_e = 0
+        for c0 in range(0, wl.n_e, chunk):
+            ntile_e += (min(chunk, wl.n_e - c0) + 127) // 128
+        tot += SPLIT_PRODUCTS * 2.0 * 128 * 128 * npad * split_tiles(w.n) * ntile_e
+    return tot
 
 
 def parse():
@@ -39,7 +65,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=3)
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "split_bf16"])
+    ap.add_argument("--prec", default="split_bf16", choices=["fp64", "split_bf16"])
+    ap.add_argument("--fp64-stride", type=int, default=25,
+                    help="mesh stride of the plain FP64 GPU comparison run (0 = skip it)")
     ap.add_argument("--stride", type=int, default=0,
                     help="use every stride-th energy of the mesh (0 = automatic)")
     ap.add_argument("--sel", type=int, default=1, help="number of selected initial channels")
@@ -231,6 +259,7 @@ def run_ours(args):
         ev[s][1].record(stream)
     barrier()
     clocks = clk.stop()
+    plan.sync()
     launches = plan.launches() - l0
     prof = plan.profile_read()
     plan.profile(False)
@@ -252,7 +281,12 @@ def run_ours(args):
     pole_flops, solve_flops = algorithmic_flops(wl, n_open, len(sel))
     kern = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    near_flops = 0.0
     flops_per_step = {"polesum_fp64": pole_flops, "solve": solve_flops}
+    for k in kern:
+        if k in flops_per_step:
+            kern[k]["tflops_algorithmic"] = flops_per_step[k] * args.steps / (kern[k]["ms_total"] / 1000.0) / 1e12
+    peaks = measured_peaks()
     roof = None
     if dom in flops_per_step:
         total_fl = flops_per_step[dom] * args.steps
@@ -261,11 +295,24 @@ def run_ours(args):
         achieved = (total_fl / n_l) / (avg_ms / 1000.0) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "peak_source": "FP64 pipe: nominal 1.25 TFLOP/s (a DFMA probe measured 1.2)",
                 "flops_per_launch": total_fl / n_l, "avg_launch_ms": avg_ms}
-    for k in kern:
-        if k in flops_per_step:
-            kern[k]["tflops"] = flops_per_step[k] * args.steps / (kern[k]["ms_total"] / 1000.0) / 1e12
+    roof_tc = None
+    if "polesum_split" in kern:
+        info = plan.info(0)
+        hw = tensor_flops(wl, info["chunk"]) * args.steps
+        n_l = kern["polesum_split"]["launches"]
+        avg_ms = kern["polesum_split"]["ms_total"] / n_l
+        achieved = (hw / n_l) / (avg_ms / 1000.0) / 1e12
+        pk = peaks.get("bf16_tflops_sustained") or 1700.0
+        roof_tc = {"kernel": "polesum_split", "bound": "tensor", "achieved": achieved, "peak": pk,
+                   "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
+                   "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks
+                   else "fallback 1.7 PFLOP/s sustained",
+                   "flops_per_launch": hw / n_l, "avg_launch_ms": avg_ms,
+                   "algorithmic_tflops": pole_flops * args.steps / (kern["polesum_split"]["ms_total"]
+                                                                    + kern.get("near", {}).get("ms_total", 0.0)) / 1e9,
+                   "note": f"{SPLIT_PRODUCTS} BF16 products per far term; algorithmic = 2 n_p N n_e of Eq. 1-2"}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -295,6 +342,25 @@ def run_ours(args):
         e2e = {"value": world * len(wl.waves) * wl.n_e / dt, "unit": "energies/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
 
+    # the plain FP64 GPU form on a strided sub-mesh of the same workload
+    fp64 = None
+    if args.prec != "fp64" and args.fp64_stride > 0 and rank == 0:
+        sub = wl.energies[::args.fp64_stride].copy()
+        dsub = torch.from_numpy(sub).to(dev)
+        with rm.Plan(dwaves, dsub, prec="fp64", sel=sel, stream=stream) as p64:
+            p64.run()
+            torch.cuda.synchronize(dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(1)
+            a0.record(stream)
+            p64.run()
+            a1.record(stream)
+            p64.sync()
+            ms64 = a0.elapsed_time(a1)
+        v64 = len(wl.waves) * sub.shape[0] / (ms64 / 1000.0)
+        fp64 = {"value": v64, "unit": "energies/s", "sample": f"every {args.fp64_stride}th energy of the mesh "
+                f"({sub.shape[0]} energies), one timed pass", "split_speedup": value / v64}
+
     # CPU baseline leg: the oracle timed on a bounded sample of the same mesh;
     # its outputs for those energies also give the accuracy report.
     cpu = None
@@ -317,7 +383,8 @@ def run_ours(args):
                            "n_ch": [w.n for w in wl.waves][:4], "n_poles": [w.N for w in wl.waves][:4],
                            "n_sel": len(sel), "l2": "flushed (512 MB write) between timed steps",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "kernels": kern, "gpu_launches": int(launches),
+                "roofline": roof, "roofline_tensor": roof_tc, "kernels": kern, "gpu_launches": int(launches),
+                "fp64_gpu": fp64,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "errors": errors}
         print(json.dumps(line), flush=True)
     plan.close()
