@@ -175,6 +175,45 @@ rm_status_t rm_plan_destroy(rm_plan_t plan);
 const char* rm_status_str(rm_status_t s);
 const char* rm_last_error(void);
 
+/*
+ * K-matrix / S-step without any device allocation.  The paper has no
+ * counterpart to this call: it exists for callers that are not allowed to
+ * call cudaMalloc (code that runs inside another library's stream capture,
+ * plug-ins bound to a host application's fixed memory pool, real-time loops
+ * where an allocation may block or fail).  It computes what rm_kmatrix and
+ * rm_xsec compute, from packed R-matrices the caller already holds, with the
+ * same kernels; its only scratch is a static device array of
+ * RM_STATIC_SCRATCH_BYTES inside this library, which every GPU that loads the
+ * library holds until the process exits.  It allocates nothing, host or
+ * device, and calls no allocating library routine.
+ *
+ * All array pointers are DEVICE pointers except sel_init (host; NULL = {0}).
+ *   R_packed  [n_e * n_p] packed upper triangles, energy-major (as rm_rmatrix)
+ *   l, thresh [n_ch]; pole_E [n_poles] (used only to nudge energies that sit
+ *             on a pole, exactly as rm_plan_create does); energies [n_e]
+ *   outputs   as rm_kmatrix / rm_xsec (K [n_e*n*n], eigsum [n_e],
+ *             sig_tot [n_e*n_sel], sig_sel [n_e*n_sel*n], flags, n_open);
+ *             any may be NULL
+ * Inputs are not validated on the device: thresholds and poles must be sorted
+ * ascending and finite.  The work is enqueued on cuda_stream (NULL = default
+ * stream) and the call returns without waiting.
+ * Sizes: n_ch is limited by the scratch (one solve workspace of about
+ * 4 n_ch^2 + 2 n_ch n_sel doubles must fit); larger n_ch returns RM_ERR_ARG.
+ * Set-up: the first call on each device looks up the scratch array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one scratch array and every call overwrites
+ * it, so calls that may overlap on the GPU (different streams, or threads)
+ * race and must be serialised by the caller.  Errors: rm_static_last_error().
+ */
+#define RM_STATIC_SCRATCH_BYTES (64ll << 20)
+rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_ch, int32_t n_poles, double a,
+                                  const int32_t* l, const double* thresh, const double* pole_E,
+                                  const double* energies, int64_t n_e, const int32_t* sel_init,
+                                  int32_t n_sel, double* K, double* eigsum, double* sig_tot,
+                                  double* sig_sel, uint8_t* flags, int32_t* n_open,
+                                  void* cuda_stream);
+const char* rm_static_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif
