@@ -89,8 +89,9 @@ __device__ __forceinline__ void df_recip_diff(float kh, float kl, float eh, floa
   const float dl0 = __fadd_rn(err, __fsub_rn(kl, el));
   const float dh = __fadd_rn(s, dl0);
   const float dl = __fsub_rn(dl0, __fsub_rn(dh, s));
-  rh = __frcp_rn(dh);
-  float c = __fmaf_rn(-dh, rh, 1.0f);  // exact residual of the rounded reciprocal
+  // approximate reciprocal (1 ulp); the residual correction below absorbs its error
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rh) : "f"(dh));
+  float c = __fmaf_rn(-dh, rh, 1.0f);  // exact residual 1 - dh * rh
   c = __fmaf_rn(-dl, rh, c);
   rl = __fmul_rn(rh, c);
 }
@@ -237,12 +238,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     // -------------------------------------------------- producers and drains
     const int w = warp;
-    // A role: pair row rA = ai*16 + jj, k-pairs kpa + 2t
-    const int ai = w >> 1, jj = lane & 15, kpa = (w & 1) * 8 + (lane >> 4);
-    const int rA = ai * 16 + jj;
-    const int gi = I0 + ai, gj = J0 + jj;
-    float mp = 0.0f;
-    if (gi < n && gj < n && gi <= gj) mp = g.mult_p[pair_index(n, gi, gj)];
+    // A role: i-row ai, j-rows jj = jbase + 2t (t = 0..3), k-pair kpa (all 16 k-pairs per
+    // half-warp); a half-warp reads one staged row contiguously and writes one full slice row.
+    const int ai = w >> 1, kpa = lane & 15, jbase = (w & 1) * 8 + (lane >> 4);
+    const int gi = I0 + ai;
+    float mp[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int gj = J0 + jbase + 2 * t;
+      mp[t] = (gi < n && gj < n && gi <= gj) ? g.mult_p[pair_index(n, gi, gj)] : 0.0f;
+    }
     // B role: energy row rb, k-pairs kpb + 4t
     const int rb = w * 8 + (lane & 7), kpb = lane >> 3;
     const int eloc = n0 + rb;
@@ -277,25 +282,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const float* PO = WJ + WJ_FLOATS;
       uint8_t* Ab = st;
       uint8_t* Bb = st + A_BYTES;
-#pragma unroll
+      const int ka = 2 * kpa;
+      const float2 wih = *reinterpret_cast<const float2*>(WI + (2 * ai) * KS + ka);
+      const float2 wil = *reinterpret_cast<const float2*>(WI + (2 * ai + 1) * KS + ka);
+#pragma unroll 1
       for (int t = 0; t < 4; ++t) {
-        const int k = 2 * (kpa + 2 * t);
-        const float2 wih = *reinterpret_cast<const float2*>(WI + (2 * ai) * KS + k);
-        const float2 wil = *reinterpret_cast<const float2*>(WI + (2 * ai + 1) * KS + k);
+        const int jj = jbase + 2 * t;
+        const int k = ka;
         const float2 wjh = *reinterpret_cast<const float2*>(WJ + (2 * jj) * KS + k);
         const float2 wjl = *reinterpret_cast<const float2*>(WJ + (2 * jj + 1) * KS + k);
         float ph0, pl0, ph1, pl1;
         df_mul(wih.x, wil.x, wjh.x, wjl.x, ph0, pl0);
         df_mul(wih.y, wil.y, wjh.y, wjl.y, ph1, pl1);
         float s0[4], s1[4];
-        slice4(__fmul_rn(ph0, mp), __fmul_rn(pl0, mp), s0);
-        slice4(__fmul_rn(ph1, mp), __fmul_rn(pl1, mp), s1);
-        const uint32_t off = swz(rA, k);
+        slice4(__fmul_rn(ph0, mp[t]), __fmul_rn(pl0, mp[t]), s0);
+        slice4(__fmul_rn(ph1, mp[t]), __fmul_rn(pl1, mp[t]), s1);
+        const uint32_t off = swz(ai * 16 + jj, k);
 #pragma unroll
         for (int u = 0; u < 4; ++u) *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + off) = pack_bf16x2(s0[u], s1[u]);
       }
       const int k0 = j * KS;
-#pragma unroll
+#pragma unroll 1
       for (int t = 0; t < 4; ++t) {
         const int k = 2 * (kpb + 4 * t);
         const int kg = k0 + k;

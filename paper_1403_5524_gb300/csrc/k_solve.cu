@@ -42,6 +42,7 @@ struct Ops<double> {
   __device__ static double inv(double x) { return 1.0 / x; }
   __device__ static double mul(double a, double b) { return a * b; }
   __device__ static double fms(double acc, double a, double b) { return fma(-a, b, acc); }
+  __device__ static double fma_acc(double acc, double a, double b) { return fma(a, b, acc); }
 };
 
 template <>
@@ -62,7 +63,17 @@ struct Ops<cplx> {
   __device__ static cplx fms(cplx acc, cplx a, cplx b) {
     return cplx{fma(-a.re, b.re, fma(a.im, b.im, acc.re)), fma(-a.re, b.im, fma(-a.im, b.re, acc.im))};
   }
+  __device__ static cplx fma_acc(cplx acc, cplx a, cplx b) {
+    return cplx{fma(a.re, b.re, fma(-a.im, b.im, acc.re)), fma(a.re, b.im, fma(a.im, b.re, acc.im))};
+  }
 };
+
+template <typename T>
+__device__ __forceinline__ T make_neg_one();
+template <>
+__device__ __forceinline__ double make_neg_one<double>() { return -1.0; }
+template <>
+__device__ __forceinline__ cplx make_neg_one<cplx>() { return cplx{-1.0, 0.0}; }
 
 struct LUStat {
   double pmin, pmax;
@@ -108,9 +119,48 @@ __device__ int panel_argmax(const T* panel, int rows, int j, Red* red) {
 // LU with partial pivoting of the leading n x n block of A (row-major, ld),
 // row operations applied to all m columns, then back substitution on
 // columns [n, m).  smem: panel[n_max*NB], tile[NB*TC], ipiv[n_max].
+// A[r][col] -= sum_j L[r][j] * U[j] for rows r = r0, r0 + 4, ... < r1, where L[r][j] is
+// panel row r (NB wide) and U[j] = tile[j * TC]; four rows per iteration so that
+// four independent loads are in flight, the tile column held in registers.
 template <typename T>
-__device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* tile, int* ipiv,
-                         Red* red, LUStat& st) {
+__device__ __forceinline__ void rank_update(T* __restrict__ A, int ld, int col, int r0, int r1, const T* panel,
+                                            const T* tile, int nb) {
+  using O = Ops<T>;
+  constexpr int RS = NT / TC;  // row stride between the threads of one column
+  T u[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) u[j] = (j < nb) ? tile[j * TC] : O::zero();
+  int r = r0;
+  for (; r + 3 * RS < r1; r += 4 * RS) {
+    T v0 = A[(int64_t)r * ld + col];
+    T v1 = A[(int64_t)(r + RS) * ld + col];
+    T v2 = A[(int64_t)(r + 2 * RS) * ld + col];
+    T v3 = A[(int64_t)(r + 3 * RS) * ld + col];
+    const T* l0 = panel + (int64_t)r * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      v0 = O::fms(v0, l0[j], u[j]);
+      v1 = O::fms(v1, l0[RS * NB + j], u[j]);
+      v2 = O::fms(v2, l0[2 * RS * NB + j], u[j]);
+      v3 = O::fms(v3, l0[3 * RS * NB + j], u[j]);
+    }
+    A[(int64_t)r * ld + col] = v0;
+    A[(int64_t)(r + RS) * ld + col] = v1;
+    A[(int64_t)(r + 2 * RS) * ld + col] = v2;
+    A[(int64_t)(r + 3 * RS) * ld + col] = v3;
+  }
+  for (; r < r1; r += RS) {
+    T v = A[(int64_t)r * ld + col];
+    const T* l0 = panel + (int64_t)r * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) v = O::fms(v, l0[j], u[j]);
+    A[(int64_t)r * ld + col] = v;
+  }
+}
+
+template <typename T>
+__device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* tile, T* tmp, T* tri,
+                         int* ipiv, Red* red, LUStat& st) {
   using O = Ops<T>;
   const int t = threadIdx.x;
   st.pmin = INFINITY;
@@ -129,9 +179,9 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
     for (int j = 0; j < nb; ++j) {
       const int p = panel_argmax(panel, rows, j, red);
       if (t < NB && p != j) {
-        const T tmp = panel[j * NB + t];
+        const T tmpv = panel[j * NB + t];
         panel[j * NB + t] = panel[p * NB + t];
-        panel[p * NB + t] = tmp;
+        panel[p * NB + t] = tmpv;
       }
       if (t == 0) {
         ipiv[kb + j] = kb + p;
@@ -157,40 +207,47 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
       const int r = idx / NB, c = idx % NB;
       if (c < nb) A[(int64_t)(kb + r) * ld + kb + c] = panel[idx];
     }
-    // columns right of the panel, in tiles of TC
+    // row interchanges on every column right of the panel (all threads, one column each)
+    for (int col = kb + nb + t; col < m; col += NT) {
+      for (int j = 0; j < nb; ++j) {
+        const int r1 = kb + j, r2 = ipiv[kb + j];
+        if (r1 != r2) {
+          const T a1 = A[(int64_t)r1 * ld + col];
+          A[(int64_t)r1 * ld + col] = A[(int64_t)r2 * ld + col];
+          A[(int64_t)r2 * ld + col] = a1;
+        }
+      }
+    }
+    // inverse of the unit-lower diagonal block, column t by thread t
+    if (t < NB) {
+      for (int i = 0; i < NB; ++i) tri[i * NB + t] = (i == t) ? O::one() : O::zero();
+      if (t < nb) {
+        for (int i = t + 1; i < nb; ++i) {
+          T acc = O::zero();
+          for (int k = t; k < i; ++k) acc = O::fms(acc, panel[i * NB + k], tri[k * NB + t]);
+          tri[i * NB + t] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    // columns right of the panel, in tiles of TC: U12 = L11^-1 A12, then the rank-nb update
     for (int c0 = kb + nb; c0 < m; c0 += TC) {
-      const int tc = t % TC, tr = t / TC;
-      const int col = c0 + tc;
-      if (t < TC && col < m) {
-        T u[NB];
-        for (int j = 0; j < nb; ++j) {
-          const int r1 = kb + j, r2 = ipiv[kb + j];
-          if (r1 != r2) {
-            const T a1 = A[(int64_t)r1 * ld + col];
-            A[(int64_t)r1 * ld + col] = A[(int64_t)r2 * ld + col];
-            A[(int64_t)r2 * ld + col] = a1;
-          }
-        }
-        for (int j = 0; j < nb; ++j) {
-          T v = A[(int64_t)(kb + j) * ld + col];
-          for (int i = 0; i < j; ++i) v = O::fms(v, panel[j * NB + i], u[i]);
-          u[j] = v;
-        }
-        for (int j = 0; j < nb; ++j) {
-          A[(int64_t)(kb + j) * ld + col] = u[j];
-          tile[j * TC + t] = u[j];
-        }
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        tmp[idx] = (j < nb && col < m) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
       }
       __syncthreads();
-      if (col < m) {
-        for (int r = kb + nb + tr; r < n; r += NT / TC) {
-          T v = A[(int64_t)r * ld + col];
-          const T* lrow = panel + (r - kb) * NB;
-#pragma unroll 4
-          for (int j = 0; j < nb; ++j) v = O::fms(v, lrow[j], tile[j * TC + tc]);
-          A[(int64_t)r * ld + col] = v;
-        }
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        // L11^-1 is unit lower triangular: terms i <= j only (j is uniform across a warp)
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        T u = tmp[j * TC + c];
+        for (int i = 0; i < j; ++i) u = O::fma_acc(u, tri[j * NB + i], tmp[i * TC + c]);
+        tile[idx] = u;
+        if (j < nb && col < m) A[(int64_t)(kb + j) * ld + col] = u;
       }
+      __syncthreads();
+      const int tc = t % TC, tr = t / TC;
+      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, kb + nb + tr, n, panel - (int64_t)kb * NB, tile + tc, nb);
       __syncthreads();
     }
   }
@@ -204,32 +261,39 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
       panel[idx] = (c < nb) ? A[(int64_t)r * ld + kb + c] : O::zero();
     }
     __syncthreads();
+    // inverse of the upper diagonal block U11 (rows/cols kb..kb+nb), column t by thread t
+    if (t < NB) {
+      for (int i = 0; i < NB; ++i) tri[i * NB + t] = O::zero();
+      if (t < nb) {
+        const T* U = panel + (int64_t)kb * NB;  // U[i][k] = U[i * NB + k]
+        const double dm = O::mag(U[t * NB + t]);
+        tri[t * NB + t] = (dm == 0.0) ? O::zero() : O::inv(U[t * NB + t]);
+        for (int i = t - 1; i >= 0; --i) {
+          T acc = O::zero();
+          for (int k = i + 1; k <= t; ++k) acc = O::fms(acc, U[i * NB + k], tri[k * NB + t]);
+          const double di = O::mag(U[i * NB + i]);
+          tri[i * NB + t] = (di == 0.0) ? O::zero() : O::mul(acc, O::inv(U[i * NB + i]));
+        }
+      }
+    }
+    __syncthreads();
     for (int c0 = n; c0 < m; c0 += TC) {
-      const int tc = t % TC, tr = t / TC;
-      const int col = c0 + tc;
-      if (t < TC && col < m) {
-        T y[NB];
-        for (int j = nb - 1; j >= 0; --j) {
-          T v = A[(int64_t)(kb + j) * ld + col];
-          for (int i = j + 1; i < nb; ++i) v = O::fms(v, panel[(kb + j) * NB + i], y[i]);
-          const T d = panel[(kb + j) * NB + j];
-          y[j] = (O::mag(d) == 0.0) ? O::zero() : O::mul(v, O::inv(d));
-        }
-        for (int j = 0; j < nb; ++j) {
-          A[(int64_t)(kb + j) * ld + col] = y[j];
-          tile[j * TC + t] = y[j];
-        }
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        tmp[idx] = (j < nb && col < m) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
       }
       __syncthreads();
-      if (col < m) {
-        for (int r = tr; r < kb; r += NT / TC) {
-          T v = A[(int64_t)r * ld + col];
-          const T* urow = panel + r * NB;
-#pragma unroll 4
-          for (int j = 0; j < nb; ++j) v = O::fms(v, urow[j], tile[j * TC + tc]);
-          A[(int64_t)r * ld + col] = v;
-        }
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        // U11^-1 is upper triangular: terms i >= j only (j is uniform across a warp)
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        T y = O::zero();
+        for (int i = j; i < nb; ++i) y = O::fma_acc(y, tri[j * NB + i], tmp[i * TC + c]);
+        tile[idx] = y;
+        if (j < nb && col < m) A[(int64_t)(kb + j) * ld + col] = y;
       }
+      __syncthreads();
+      const int tc = t % TC, tr = t / TC;
+      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, tr, kb, panel, tile + tc, nb);
       __syncthreads();
     }
   }
@@ -261,7 +325,9 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
   const int n = g.n;
   cplx* panel_c = reinterpret_cast<cplx*>(smem_raw);
   cplx* tile_c = panel_c + (size_t)n * NB;
-  int* ipiv = reinterpret_cast<int*>(tile_c + NB * TC);
+  cplx* tmp_c = tile_c + NB * TC;
+  cplx* tri_c = tmp_c + NB * TC;
+  int* ipiv = reinterpret_cast<int*>(tri_c + NB * NB);
   double* panel_d = reinterpret_cast<double*>(panel_c);
   double* tile_d = reinterpret_cast<double*>(tile_c);
 
@@ -313,7 +379,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
     }
     __syncthreads();
     LUStat st;
-    lu_solve<double>(A, n, m, g.ldR, panel_d, tile_d, ipiv, &red, st);
+    lu_solve<double>(A, n, m, g.ldR, panel_d, tile_d, reinterpret_cast<double*>(tmp_c),
+                     reinterpret_cast<double*>(tri_c), ipiv, &red, st);
     __shared__ int s_singular;
     __shared__ double s_ratio;
     if (t == 0) {
@@ -354,7 +421,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
       C[(int64_t)i * g.ldC + j] = v;
     }
     __syncthreads();
-    lu_solve<cplx>(C, no, mc, g.ldC, panel_c, tile_c, ipiv, &red, st);
+    lu_solve<cplx>(C, no, mc, g.ldC, panel_c, tile_c, tmp_c, tri_c, ipiv, &red, st);
     if (t == 0 && g.out.eta) {
       double ph = 0.0;
       for (int j = 0; j < no; ++j) {
@@ -397,7 +464,8 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
 }  // namespace
 
 size_t solve_smem_bytes(int n_max) {
-  return (size_t)n_max * NB * sizeof(cplx) + (size_t)NB * TC * sizeof(cplx) + (size_t)n_max * sizeof(int) + 16;
+  return (size_t)n_max * NB * sizeof(cplx) + 2 * (size_t)NB * TC * sizeof(cplx) + (size_t)NB * NB * sizeof(cplx) +
+         (size_t)n_max * sizeof(int) + 16;
 }
 
 int64_t solve_slot_doubles(int n_max, int n_sel) {
