@@ -96,6 +96,8 @@ typedef struct {
   int32_t n_sel;           /* entries in sel_init (ignored when sel_init is NULL) */
   int32_t mem;             /* rm_mem_t of every input pointer (waves and energies) */
   int32_t chunk;           /* energies per internal chunk; 0 = automatic */
+  int32_t autotune;        /* 1: time candidate energy-chunk sizes of rm_run at plan creation */
+  const char* tune_cache;  /* optional file caching autotuned choices (NULL = none) */
 } rm_options;
 
 /* Fill *opt with defaults: FP64, delta 0.05, sel {0}, host inputs, auto chunk. */
@@ -135,7 +137,12 @@ rm_status_t rm_xsec(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, double
 
 /* The whole sweep: every wave, every energy, R -> K -> S, eigenphase sum and
    cross sections into plan-owned device buffers (read them with
-   rm_results).  This is the call the benchmark times. */
+   rm_results).  All waves run together: one launch per kernel and energy
+   chunk covers every wave (tensor-core tiles ordered longest first, solve
+   units claimed dynamically in decreasing cost), and the whole sequence is
+   captured once in a CUDA graph and replayed.  While per-kernel timing is
+   enabled the same launches are issued directly (no graph) so that each
+   can be bracketed by events.  This is the call the benchmark times. */
 rm_status_t rm_run(rm_plan_t plan);
 
 /* Copy results of the last rm_run for one wave and energies [e0, e1).
@@ -147,7 +154,7 @@ rm_status_t rm_results(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, dou
 /* Wait for the plan's stream; reports device-side error words. */
 rm_status_t rm_sync(rm_plan_t plan);
 
-/* Sizes: n_ch, n_poles of a wave; the plan's n_e, n_sel, chunk and device
+/* Sizes: n_ch, n_poles of a wave; the plan's n_e, n_sel, rm_run energy-chunk size and device
    workspace bytes.  Any output may be NULL. */
 rm_status_t rm_plan_info(rm_plan_t plan, int32_t wave, int32_t* n_ch, int32_t* n_poles,
                          int64_t* n_e, int32_t* n_sel, int32_t* chunk, int64_t* workspace_bytes);

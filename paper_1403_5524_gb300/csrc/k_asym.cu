@@ -14,6 +14,8 @@
 // khat is run upward on the scaled sequence exp(x) khat_l:
 // g_{l+1} = g_{l-1} + ((2l+1)/x) g_l, g_{-1} = g_0 = 1; the exponential
 // cancels in the log-derivative, khat_l'/khat_l = (-g_{l-1} - (l/x) g_l)/g_l.
+#include <vector>
+
 #include "rm_internal.cuh"
 
 namespace rm {
@@ -116,7 +118,66 @@ __global__ void asym_kernel(const int32_t* __restrict__ lch, const double* __res
   out[3 * ld + t] = c;
 }
 
+struct AsymWave {
+  const int32_t* l;
+  const double* thr;
+  const double* E;  // nudged mesh (base)
+  double* out;      // chunk buffer [4][chunk * n]
+  double a;
+  int n;
+};
+
+// grid.y = wave; energies e_begin .. e_begin + ne of every wave
+__global__ void asym_grouped_kernel(const AsymWave* __restrict__ waves, int64_t e_begin, int ne, int64_t ld_chunk) {
+  const AsymWave w = waves[blockIdx.y];
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ne * w.n) return;
+  // ld between the four quantities is chunk * n of this wave
+  const int64_t ld = ld_chunk * w.n;
+  const int e = (int)(t / w.n), i = (int)(t % w.n);
+  const double k2 = w.E[e_begin + e] - w.thr[i];
+  const int l = w.l[i];
+  double lam, s = 0.0, sp = 0.0, c = 0.0;
+  if (k2 > 0.0) {
+    const double k = sqrt(k2), sk = sqrt(k);
+    double j, jp, y, yp;
+    riccati_open(l, k * w.a, j, jp, y, yp);
+    s = j / sk;
+    sp = jp * sk;
+    c = -y / sk;
+    lam = k * yp / y;
+  } else {
+    const double kap = sqrt(-k2);
+    lam = kap * khat_logderiv(l, kap * w.a);
+  }
+  w.out[0 * ld + t] = lam;
+  w.out[1 * ld + t] = s;
+  w.out[2 * ld + t] = sp;
+  w.out[3 * ld + t] = c;
+}
+
 }  // namespace
+
+cudaError_t group_setup_asym(Plan& p) {
+  GroupDev& G = p.grp;
+  std::vector<AsymWave> h(p.n_waves);
+  for (int g = 0; g < p.n_waves; ++g) {
+    const WaveDev& w = p.waves[g];
+    h[g] = AsymWave{w.l, w.thr, w.E, G.asym[g], w.a, w.n};
+  }
+  cudaError_t err;
+  if (!G.asym_waves && (err = cudaMalloc(&G.asym_waves, sizeof(AsymWave) * p.n_waves)) != cudaSuccess) return err;
+  return cudaMemcpy(G.asym_waves, h.data(), sizeof(AsymWave) * p.n_waves, cudaMemcpyHostToDevice);
+}
+
+cudaError_t launch_asym_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {
+  if (ne <= 0) return cudaSuccess;
+  const int bs = 256;
+  dim3 grid((unsigned)(((int64_t)ne * p.n_max + bs - 1) / bs), p.n_waves);
+  asym_grouped_kernel<<<grid, bs, 0, s>>>(reinterpret_cast<const AsymWave*>(p.grp.asym_waves), e0, ne,
+                                          (int64_t)p.grp.chunk);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_asym(const WaveDev& w, int64_t e0, int ne, double* asym, int ld_chunk,
                         cudaStream_t s) {

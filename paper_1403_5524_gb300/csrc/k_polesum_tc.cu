@@ -25,6 +25,8 @@
 // index ranges [klo, khi) and summed in FP64 by the near-window kernel, so the
 // two parts partition the pole set exactly.
 #include <cuda_bf16.h>
+#include <algorithm>
+#include <vector>
 #include <cudaTypedefs.h>
 
 #include "rm_internal.cuh"
@@ -118,11 +120,12 @@ struct TCArgs {
   int32_t* err;
 };
 
-__global__ void __launch_bounds__(NTHREADS, 1)
-    polesum_tc_kernel(const __grid_constant__ CUtensorMap map_omega, const __grid_constant__ CUtensorMap map_pol,
-                      TCArgs g) {
+// One 128-pair x 128-energy output tile: pairs from i-block I0 (8 channels) and
+// j-block J0 (16 channels), energies n0 .. n0+127 of the chunk that starts at
+// absolute energy index g.e_begin and holds g.ne energies.
+__device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUtensorMap* map_pol, const TCArgs& g,
+                                        int I0, int J0, int n0, unsigned char* smem_raw) {
   using namespace ptx;
-  extern __shared__ unsigned char smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_STRIDE);
   uint64_t* full = bars;
@@ -135,9 +138,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int2 tile = g.tiles[blockIdx.x];
-  const int I0 = tile.x * 8, J0 = tile.y * 16;
-  const int n0 = blockIdx.y * BN;
   const int nK = g.nK;
   const int n = g.n;
 
@@ -174,10 +174,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float* PO = WJ + WJ_FLOATS;
         mbar_arrive_expect_tx(wfull + s, TX_BYTES);
         const int x = j * KS;
-        tma_load_2d(WI, &map_omega, wfull + s, x, 2 * I0);
-        tma_load_2d(WJ, &map_omega, wfull + s, x, 2 * J0);
-        tma_load_2d(WJ + 16 * KS, &map_omega, wfull + s, x, 2 * J0 + 16);
-        tma_load_2d(PO, &map_pol, wfull + s, x, 0);
+        tma_load_2d(WI, map_omega, wfull + s, x, 2 * I0);
+        tma_load_2d(WJ, map_omega, wfull + s, x, 2 * J0);
+        tma_load_2d(WJ + 16 * KS, map_omega, wfull + s, x, 2 * J0 + 16);
+        tma_load_2d(PO, map_pol, wfull + s, x, 0);
         tma_last[s] = j;
       };
       for (int s = 0; s < STAGES && s < nK; ++s) issue_tma(s, s);
@@ -374,6 +374,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0 && *abort_flag) atomicMax(g.err, (int)RM_ERR_TIMEOUT);
 }
 
+__global__ void __launch_bounds__(NTHREADS, 1)
+    polesum_tc_kernel(const __grid_constant__ CUtensorMap map_omega, const __grid_constant__ CUtensorMap map_pol,
+                      TCArgs g) {
+  extern __shared__ unsigned char smem_raw[];
+  const int2 tile = g.tiles[blockIdx.x];
+  tc_tile(&map_omega, &map_pol, g, tile.x * 8, tile.y * 16, blockIdx.y * BN, smem_raw);
+}
+
+// Every wave of a plan in one launch: tile list entries (wave, i-block, j-block),
+// per-wave arguments and TMA descriptors in global memory; the chunk's energy
+// range is shared by all waves.
+__global__ void __launch_bounds__(NTHREADS, 1)
+    polesum_tc_grouped_kernel(const TCArgs* __restrict__ waves, const CUtensorMap* __restrict__ maps,
+                              const int4* __restrict__ tiles, int64_t e_begin, int ne) {
+  extern __shared__ unsigned char smem_raw[];
+  const int4 t = tiles[blockIdx.x];
+  TCArgs g = waves[t.x];
+  g.e_begin = e_begin;
+  g.ne = ne;
+  tc_tile(maps + 2 * t.x, maps + 2 * t.x + 1, g, t.y * 8, t.z * 16, blockIdx.y * BN, smem_raw);
+}
+
 // ------------------------------------------------------------ preparation
 // sigma_i = 2^ceil(log2 max_k |w_ik|); w_ik / sigma_i as FP32 hi (row 2i) + lo (row 2i+1)
 __global__ void prep_omega_kernel(const double* __restrict__ W, int n, int N, int Npad, double* __restrict__ sigma,
@@ -510,14 +532,23 @@ constexpr int NEB = 8;    // energies per CTA
 constexpr int NKP = 32;   // poles per staged piece
 constexpr int NNT = 256;  // threads
 
-__global__ void __launch_bounds__(NNT) near_kernel(const double* __restrict__ W, int n, int Npad,
-                                                   const double* __restrict__ poles, const double* __restrict__ E,
-                                                   const int32_t* __restrict__ klo, const int32_t* __restrict__ khi,
-                                                   int ne, double inv2a, int splits, double* __restrict__ R) {
-  extern __shared__ double nsm[];
+struct NearWave {
+  const double* W;
+  const double* poles;
+  const double* E;
+  const int32_t* klo;
+  const int32_t* khi;
+  double* R;  // chunk R buffer of this wave
+  double inv2a;
+  int n, Npad;
+};
+
+__device__ __forceinline__ void near_block(const double* __restrict__ W, int n, int Npad,
+                                           const double* __restrict__ poles, const double* __restrict__ E,
+                                           const int32_t* __restrict__ klo, const int32_t* __restrict__ khi, int ne,
+                                           double inv2a, int splits, double* __restrict__ R, int e0, double* nsm) {
   double* Ws = nsm;                       // [n][NKP + 1]
   double* Dm = Ws + (size_t)n * (NKP + 1);  // [NEB][NKP]
-  const int e0 = blockIdx.x * NEB;
   const int e1 = min(ne, e0 + NEB);
   if (e0 >= ne) return;
   const int64_t np = (int64_t)n * (n + 1) / 2;
@@ -565,6 +596,25 @@ __global__ void __launch_bounds__(NNT) near_kernel(const double* __restrict__ W,
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(NNT) near_kernel(const double* __restrict__ W, int n, int Npad,
+                                                   const double* __restrict__ poles, const double* __restrict__ E,
+                                                   const int32_t* __restrict__ klo, const int32_t* __restrict__ khi,
+                                                   int ne, double inv2a, int splits, double* __restrict__ R) {
+  extern __shared__ double nsm[];
+  near_block(W, n, Npad, poles, E, klo, khi, ne, inv2a, splits, R, blockIdx.x * NEB, nsm);
+}
+
+// All waves: job (wave, first energy of the block); energies are chunk-relative.
+__global__ void __launch_bounds__(NNT) near_grouped_kernel(const NearWave* __restrict__ waves,
+                                                           const int2* __restrict__ jobs, int64_t e_begin, int ne,
+                                                           int splits) {
+  extern __shared__ double nsm[];
+  const int2 jb = jobs[blockIdx.x];
+  const NearWave w = waves[jb.x];
+  near_block(w.W, w.n, w.Npad, w.poles, w.E + e_begin, w.klo + e_begin, w.khi + e_begin, ne, w.inv2a, splits, w.R,
+             jb.y, nsm);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
@@ -666,6 +716,101 @@ cudaError_t launch_near(const Plan& p, const WaveDev& w, int64_t e0, int ne, dou
   dim3 grid(blocks, splits);
   near_kernel<<<grid, NNT, smem, s>>>(w.W, w.n, w.Npad, w.poles, w.E + e0, w.split.klo + e0, w.split.khi + e0, ne,
                                       1.0 / (2.0 * w.a), splits, R);
+  return cudaGetLastError();
+}
+
+cudaError_t group_setup_split(Plan& p) {
+  GroupDev& G = p.grp;
+  const int W = p.n_waves;
+  std::vector<TCArgs> tw(W);
+  std::vector<NearWave> nw(W);
+  std::vector<CUtensorMap> maps(2 * W);
+  std::vector<int4> tiles;
+  std::vector<int2> jobs;
+  for (int g = 0; g < W; ++g) {
+    const WaveDev& w = p.waves[g];
+    const SplitDev& sd = w.split;
+    TCArgs a;
+    a.mult_p = sd.mult_p;
+    a.f_p = sd.f_p;
+    a.klo = sd.klo;
+    a.khi = sd.khi;
+    a.tau = sd.tau;
+    a.mult_e = sd.mult_e;
+    a.Eh = sd.Eh;
+    a.El = sd.El;
+    a.tiles = nullptr;
+    a.n = w.n;
+    a.N = w.N;
+    a.nK = w.Npad / KS;
+    a.e_begin = 0;
+    a.ne = 0;
+    a.R = G.R[g];
+    a.err = p.err_word;
+    tw[g] = a;
+    maps[2 * g] = sd.map_omega;
+    maps[2 * g + 1] = sd.map_pol;
+    for (const int2& t : split_tiles(w.n)) tiles.push_back(make_int4(g, t.x, t.y, w.Npad / KS));
+    nw[g] = NearWave{w.W, w.poles, w.E, sd.klo, sd.khi, G.R[g], 1.0 / (2.0 * w.a), w.n, w.Npad};
+    for (int e = 0; e < G.chunk; e += NEB) jobs.push_back(make_int2(g, e));
+  }
+  // longest K loop first, so the last wave of CTAs holds the short tiles
+  std::stable_sort(tiles.begin(), tiles.end(), [](const int4& x, const int4& y) { return x.w > y.w; });
+  int splits = (2 * p.sm_count + (int)jobs.size() - 1) / (int)jobs.size();
+  G.near_splits = splits < 1 ? 1 : (splits > 64 ? 64 : splits);
+  cudaError_t err;
+  auto ensure = [&](void** ptr, size_t bytes, size_t old_bytes) -> cudaError_t {
+    if (*ptr && bytes != old_bytes) {
+      cudaFree(*ptr);
+      *ptr = nullptr;
+    }
+    if (!*ptr) return cudaMalloc(ptr, bytes);
+    return cudaSuccess;
+  };
+  if ((err = ensure(&G.tc_waves, sizeof(TCArgs) * W, sizeof(TCArgs) * W)) != cudaSuccess) return err;
+  if ((err = ensure(reinterpret_cast<void**>(&G.maps), sizeof(CUtensorMap) * 2 * W, sizeof(CUtensorMap) * 2 * W)) !=
+      cudaSuccess)
+    return err;
+  if ((err = ensure(reinterpret_cast<void**>(&G.tiles), sizeof(int4) * tiles.size(), sizeof(int4) * G.n_tiles)) !=
+      cudaSuccess)
+    return err;
+  if ((err = ensure(&G.near_waves, sizeof(NearWave) * W, sizeof(NearWave) * W)) != cudaSuccess) return err;
+  if ((err = ensure(reinterpret_cast<void**>(&G.near_jobs), sizeof(int2) * jobs.size(),
+                    sizeof(int2) * G.n_near_jobs)) != cudaSuccess)
+    return err;
+  G.n_tiles = (int)tiles.size();
+  G.n_near_jobs = (int)jobs.size();
+  if ((err = cudaMemcpy(G.tc_waves, tw.data(), sizeof(TCArgs) * W, cudaMemcpyHostToDevice)) != cudaSuccess) return err;
+  if ((err = cudaMemcpy(G.maps, maps.data(), sizeof(CUtensorMap) * 2 * W, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return err;
+  if ((err = cudaMemcpy(G.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return err;
+  if ((err = cudaMemcpy(G.near_waves, nw.data(), sizeof(NearWave) * W, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return err;
+  if ((err = cudaMemcpy(G.near_jobs, jobs.data(), sizeof(int2) * jobs.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return err;
+  if ((err = cudaFuncSetAttribute(polesum_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TC_SMEM)) != cudaSuccess)
+    return err;
+  return cudaFuncSetAttribute(near_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)near_smem_bytes(p.n_max));
+}
+
+cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {
+  if (ne <= 0) return cudaSuccess;
+  const GroupDev& G = p.grp;
+  dim3 grid(G.n_tiles, (ne + BN - 1) / BN);
+  polesum_tc_grouped_kernel<<<grid, NTHREADS, TC_SMEM, s>>>(reinterpret_cast<const TCArgs*>(G.tc_waves), G.maps,
+                                                            G.tiles, e0, ne);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {
+  if (ne <= 0) return cudaSuccess;
+  const GroupDev& G = p.grp;
+  dim3 grid(G.n_near_jobs, G.near_splits);
+  near_grouped_kernel<<<grid, NNT, near_smem_bytes(p.n_max), s>>>(reinterpret_cast<const NearWave*>(G.near_waves),
+                                                                  G.near_jobs, e0, ne, G.near_splits);
   return cudaGetLastError();
 }
 

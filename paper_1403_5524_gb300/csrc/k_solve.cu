@@ -20,6 +20,9 @@
 // the rank-16 update).  Each matrix lives in a per-CTA global workspace slot
 // that stays in L2 while the CTA works on it.  GB300 retires about two FP64
 // FMAs per clock per SM, so one 256-thread CTA per SM saturates the FP64 pipe.
+#include <algorithm>
+#include <vector>
+
 #include "rm_internal.cuh"
 
 namespace rm {
@@ -67,13 +70,6 @@ struct Ops<cplx> {
     return cplx{fma(a.re, b.re, fma(-a.im, b.im, acc.re)), fma(a.re, b.im, fma(a.im, b.re, acc.im))};
   }
 };
-
-template <typename T>
-__device__ __forceinline__ T make_neg_one();
-template <>
-__device__ __forceinline__ double make_neg_one<double>() { return -1.0; }
-template <>
-__device__ __forceinline__ cplx make_neg_one<cplx>() { return cplx{-1.0, 0.0}; }
 
 struct LUStat {
   double pmin, pmax;
@@ -318,10 +314,9 @@ struct SolveArgs {
   SolveOut out;
 };
 
-__global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ Red red;
-  __shared__ double s_acc;
+// One energy e of the argument block: build the matching system from R and the
+// asymptotic data, LU -> K, then (optionally) the complex S-step.
+__device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw, Red& red, double& s_acc) {
   const int n = g.n;
   cplx* panel_c = reinterpret_cast<cplx*>(smem_raw);
   cplx* tile_c = panel_c + (size_t)n * NB;
@@ -330,134 +325,171 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
   int* ipiv = reinterpret_cast<int*>(tri_c + NB * NB);
   double* panel_d = reinterpret_cast<double*>(panel_c);
   double* tile_d = reinterpret_cast<double*>(tile_c);
-
   double* A = g.slot + (int64_t)blockIdx.x * g.slot_doubles;
   cplx* C = reinterpret_cast<cplx*>(A + (int64_t)n * g.ldR);
   const int64_t np = (int64_t)n * (n + 1) / 2;
   const int t = threadIdx.x;
 
-  for (int e = blockIdx.x; e < g.ne; e += gridDim.x) {
-    const int no = g.n_open_in[e];
-    uint8_t fl = g.flags_in[e];
-    const double* Re = g.R + (int64_t)e * np;
-    const double* lam = g.asym + 0 * g.ld_asym + (int64_t)e * n;
-    const double* s = g.asym + 1 * g.ld_asym + (int64_t)e * n;
-    const double* sp = g.asym + 2 * g.ld_asym + (int64_t)e * n;
-    const double* c = g.asym + 3 * g.ld_asym + (int64_t)e * n;
-    if (g.out.K) {
-      for (int64_t idx = t; idx < (int64_t)n * n; idx += NT) g.out.K[(int64_t)e * n * n + idx] = 0.0;
-    }
-    if (no == 0) {
-      fl |= RM_FLAG_NO_OPEN;
-      if (t == 0) {
-        if (g.out.flags) g.out.flags[e] = fl;
-        if (g.out.n_open) g.out.n_open[e] = 0;
-        if (g.out.eta) g.out.eta[e] = 0.0;
-      }
-      if (g.out.sig_tot)
-        for (int q = t; q < g.n_sel; q += NT) g.out.sig_tot[(int64_t)e * g.n_sel + q] = 0.0;
-      if (g.out.sig_sel)
-        for (int64_t idx = t; idx < (int64_t)g.n_sel * n; idx += NT)
-          g.out.sig_sel[(int64_t)e * g.n_sel * n + idx] = 0.0;
-      __syncthreads();
-      continue;
-    }
-    // ---------------------------------------------------------------- build
-    const int m = n + no;
-    for (int64_t idx = t; idx < (int64_t)n * m; idx += NT) {
-      const int i = (int)(idx / m), j = (int)(idx % m);
-      double v;
-      if (j < n) {
-        const double rij = Re[pair_index(n, min(i, j), max(i, j))];
-        v = ((i == j) ? 1.0 : 0.0) - g.a * rij * lam[j];
-      } else {
-        const int mo = j - n;
-        const double rim = Re[pair_index(n, min(i, mo), max(i, mo))];
-        v = -(((i == mo) ? s[mo] : 0.0) - g.a * rim * sp[mo]);
-      }
-      A[(int64_t)i * g.ldR + j] = v;
-    }
-    __syncthreads();
-    LUStat st;
-    lu_solve<double>(A, n, m, g.ldR, panel_d, tile_d, reinterpret_cast<double*>(tmp_c),
-                     reinterpret_cast<double*>(tri_c), ipiv, &red, st);
-    __shared__ int s_singular;
-    __shared__ double s_ratio;
-    if (t == 0) {
-      s_singular = st.singular ? 1 : 0;
-      s_ratio = (st.pmax > 0.0) ? st.pmin / st.pmax : 0.0;
-    }
-    __syncthreads();
-    if (s_singular) fl |= RM_FLAG_SINGULAR;
-    else if (s_ratio < 1e-12) fl |= RM_FLAG_ILLCOND;
-    // K_jm = Y_jm / c_j
-    if (g.out.K) {
-      for (int64_t idx = t; idx < (int64_t)no * no; idx += NT) {
-        const int j = (int)(idx / no), mo = (int)(idx % no);
-        g.out.K[(int64_t)e * n * n + (int64_t)j * n + mo] = A[(int64_t)j * g.ldR + n + mo] / c[j];
-      }
-    }
+  const int no = g.n_open_in[e];
+  uint8_t fl = g.flags_in[e];
+  const double* Re = g.R + (int64_t)e * np;
+  const double* lam = g.asym + 0 * g.ld_asym + (int64_t)e * n;
+  const double* s = g.asym + 1 * g.ld_asym + (int64_t)e * n;
+  const double* sp = g.asym + 2 * g.ld_asym + (int64_t)e * n;
+  const double* c = g.asym + 3 * g.ld_asym + (int64_t)e * n;
+  if (g.out.K) {
+    for (int64_t idx = t; idx < (int64_t)n * n; idx += NT) g.out.K[(int64_t)e * n * n + idx] = 0.0;
+  }
+  if (no == 0) {
+    fl |= RM_FLAG_NO_OPEN;
     if (t == 0) {
       if (g.out.flags) g.out.flags[e] = fl;
-      if (g.out.n_open) g.out.n_open[e] = no;
+      if (g.out.n_open) g.out.n_open[e] = 0;
+      if (g.out.eta) g.out.eta[e] = 0.0;
     }
-    if (!g.out.do_xsec) {
-      __syncthreads();
-      continue;
-    }
-    // --------------------------------------------------------------- S-step
-    const int r = g.n_sel;
-    const int mc = no + r;
-    for (int64_t idx = t; idx < (int64_t)no * mc; idx += NT) {
-      const int i = (int)(idx / mc), j = (int)(idx % mc);
-      cplx v;
-      if (j < no) {
-        const double kij = A[(int64_t)i * g.ldR + n + j] / c[i];
-        v = cplx{(i == j) ? 1.0 : 0.0, -kij};
-      } else {
-        const int sq = g.sel[j - no];
-        v = cplx{(sq < no) ? A[(int64_t)i * g.ldR + n + sq] / c[i] : 0.0, 0.0};
-      }
-      C[(int64_t)i * g.ldC + j] = v;
-    }
+    if (g.out.sig_tot)
+      for (int q = t; q < g.n_sel; q += NT) g.out.sig_tot[(int64_t)e * g.n_sel + q] = 0.0;
+    if (g.out.sig_sel)
+      for (int64_t idx = t; idx < (int64_t)g.n_sel * n; idx += NT)
+        g.out.sig_sel[(int64_t)e * g.n_sel * n + idx] = 0.0;
     __syncthreads();
-    lu_solve<cplx>(C, no, mc, g.ldC, panel_c, tile_c, tmp_c, tri_c, ipiv, &red, st);
-    if (t == 0 && g.out.eta) {
-      double ph = 0.0;
-      for (int j = 0; j < no; ++j) {
-        const cplx d = C[(int64_t)j * g.ldC + j];
-        ph += atan2(d.im, d.re);
-      }
-      ph += M_PI * (double)(st.swaps & 1);
-      double eta = -ph;
-      eta = eta - 2.0 * M_PI * floor((eta + M_PI) / (2.0 * M_PI));  // [-pi, pi)
-      if (eta == -M_PI) eta = M_PI;
-      g.out.eta[e] = s_singular ? NAN : eta;
+    return;
+  }
+  // ---------------------------------------------------------------- build
+  const int m = n + no;
+  for (int64_t idx = t; idx < (int64_t)n * m; idx += NT) {
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    double v;
+    if (j < n) {
+      const double rij = Re[pair_index(n, min(i, j), max(i, j))];
+      v = ((i == j) ? 1.0 : 0.0) - g.a * rij * lam[j];
+    } else {
+      const int mo = j - n;
+      const double rim = Re[pair_index(n, min(i, mo), max(i, mo))];
+      v = -(((i == mo) ? s[mo] : 0.0) - g.a * rim * sp[mo]);
     }
-    for (int q = 0; q < r; ++q) {
-      const int sq = g.sel[q];
-      const bool open_i = sq < no;
-      const double k2 = g.E[e] - g.thr[min(sq, n - 1)];
-      double part = 0.0;
-      for (int j = t; j < n; j += NT) {
-        double sig = 0.0;
-        if (open_i && j < no) {
-          const cplx x = C[(int64_t)j * g.ldC + no + q];
-          sig = 4.0 * M_PI / k2 * (x.re * x.re + x.im * x.im);
-        }
-        if (s_singular) sig = NAN;
-        if (g.out.sig_sel) g.out.sig_sel[((int64_t)e * r + q) * n + j] = sig;
-        part += sig;
+    A[(int64_t)i * g.ldR + j] = v;
+  }
+  __syncthreads();
+  LUStat st;
+  lu_solve<double>(A, n, m, g.ldR, panel_d, tile_d, reinterpret_cast<double*>(tmp_c),
+                   reinterpret_cast<double*>(tri_c), ipiv, &red, st);
+  __shared__ int s_singular;
+  __shared__ double s_ratio;
+  if (t == 0) {
+    s_singular = st.singular ? 1 : 0;
+    s_ratio = (st.pmax > 0.0) ? st.pmin / st.pmax : 0.0;
+  }
+  __syncthreads();
+  if (s_singular) fl |= RM_FLAG_SINGULAR;
+  else if (s_ratio < 1e-12) fl |= RM_FLAG_ILLCOND;
+  // K_jm = Y_jm / c_j
+  if (g.out.K) {
+    for (int64_t idx = t; idx < (int64_t)no * no; idx += NT) {
+      const int j = (int)(idx / no), mo = (int)(idx % no);
+      g.out.K[(int64_t)e * n * n + (int64_t)j * n + mo] = A[(int64_t)j * g.ldR + n + mo] / c[j];
+    }
+  }
+  if (t == 0) {
+    if (g.out.flags) g.out.flags[e] = fl;
+    if (g.out.n_open) g.out.n_open[e] = no;
+  }
+  if (!g.out.do_xsec) {
+    __syncthreads();
+    return;
+  }
+  // --------------------------------------------------------------- S-step
+  const int r = g.n_sel;
+  const int mc = no + r;
+  for (int64_t idx = t; idx < (int64_t)no * mc; idx += NT) {
+    const int i = (int)(idx / mc), j = (int)(idx % mc);
+    cplx v;
+    if (j < no) {
+      const double kij = A[(int64_t)i * g.ldR + n + j] / c[i];
+      v = cplx{(i == j) ? 1.0 : 0.0, -kij};
+    } else {
+      const int sq = g.sel[j - no];
+      v = cplx{(sq < no) ? A[(int64_t)i * g.ldR + n + sq] / c[i] : 0.0, 0.0};
+    }
+    C[(int64_t)i * g.ldC + j] = v;
+  }
+  __syncthreads();
+  lu_solve<cplx>(C, no, mc, g.ldC, panel_c, tile_c, tmp_c, tri_c, ipiv, &red, st);
+  if (t == 0 && g.out.eta) {
+    double ph = 0.0;
+    for (int j = 0; j < no; ++j) {
+      const cplx d = C[(int64_t)j * g.ldC + j];
+      ph += atan2(d.im, d.re);
+    }
+    ph += M_PI * (double)(st.swaps & 1);
+    double eta = -ph;
+    eta = eta - 2.0 * M_PI * floor((eta + M_PI) / (2.0 * M_PI));  // [-pi, pi)
+    if (eta == -M_PI) eta = M_PI;
+    g.out.eta[e] = s_singular ? NAN : eta;
+  }
+  for (int q = 0; q < r; ++q) {
+    const int sq = g.sel[q];
+    const bool open_i = sq < no;
+    const double k2 = g.E[e] - g.thr[min(sq, n - 1)];
+    double part = 0.0;
+    for (int j = t; j < n; j += NT) {
+      double sig = 0.0;
+      if (open_i && j < no) {
+        const cplx x = C[(int64_t)j * g.ldC + no + q];
+        sig = 4.0 * M_PI / k2 * (x.re * x.re + x.im * x.im);
       }
+      if (s_singular) sig = NAN;
+      if (g.out.sig_sel) g.out.sig_sel[((int64_t)e * r + q) * n + j] = sig;
+      part += sig;
+    }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-      if (t == 0) s_acc = 0.0;
-      __syncthreads();
-      if ((t & 31) == 0) atomicAdd(&s_acc, part);
-      __syncthreads();
-      if (t == 0 && g.out.sig_tot) g.out.sig_tot[(int64_t)e * r + q] = s_acc;
-      __syncthreads();
-    }
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    if (t == 0) s_acc = 0.0;
+    __syncthreads();
+    if ((t & 31) == 0) atomicAdd(&s_acc, part);
+    __syncthreads();
+    if (t == 0 && g.out.sig_tot) g.out.sig_tot[(int64_t)e * r + q] = s_acc;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Red red;
+  __shared__ double s_acc;
+  for (int e = blockIdx.x; e < g.ne; e += gridDim.x) solve_energy(g, e, smem_raw, red, s_acc);
+}
+
+// All waves of a plan: persistent CTAs claim (wave, chunk energy) units from a
+// list sorted by decreasing cost through an atomic counter.  Per-wave
+// arguments hold base pointers; the chunk offset e_begin is applied here.
+__global__ void __launch_bounds__(NT, 1) solve_grouped_kernel(const SolveArgs* __restrict__ waves,
+                                                              const int2* __restrict__ units, int n_units,
+                                                              int64_t e_begin, int ne, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Red red;
+  __shared__ double s_acc;
+  __shared__ int s_unit;
+  while (true) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+    __syncthreads();
+    const int u = s_unit;
+    __syncthreads();
+    if (u >= n_units) break;
+    const int2 un = units[u];
+    if (un.y >= ne) continue;
+    SolveArgs g = waves[un.x];
+    g.E += e_begin;
+    g.n_open_in += e_begin;
+    g.flags_in += e_begin;
+    if (g.out.K) g.out.K += e_begin * g.n * g.n;
+    if (g.out.eta) g.out.eta += e_begin;
+    if (g.out.sig_tot) g.out.sig_tot += e_begin * g.n_sel;
+    if (g.out.sig_sel) g.out.sig_sel += e_begin * g.n_sel * g.n;
+    if (g.out.flags) g.out.flags += e_begin;
+    if (g.out.n_open) g.out.n_open += e_begin;
+    g.ne = ne;
+    solve_energy(g, un.y, smem_raw, red, s_acc);
   }
 }
 
@@ -501,6 +533,77 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   if (err != cudaSuccess) return err;
   const int grid = min(ne, p.solve_slots);
   solve_kernel<<<grid, NT, smem, s>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t group_setup_solve(Plan& p) {
+  GroupDev& G = p.grp;
+  std::vector<SolveArgs> h(p.n_waves);
+  for (int g = 0; g < p.n_waves; ++g) {
+    const WaveDev& w = p.waves[g];
+    SolveArgs a;
+    a.n = w.n;
+    a.n_sel = p.n_sel;
+    a.a = w.a;
+    a.R = G.R[g];
+    a.asym = G.asym[g];
+    a.ld_asym = (int64_t)G.chunk * w.n;
+    a.E = w.E;
+    a.thr = w.thr;
+    a.n_open_in = w.n_open;
+    a.flags_in = w.flags0;
+    a.sel = p.sel_dev;
+    a.ne = 0;
+    a.slot = p.slot;
+    a.slot_doubles = p.slot_doubles;
+    a.ldR = 2 * p.n_max;
+    a.ldC = p.n_max + p.n_sel;
+    a.out = SolveOut();
+    a.out.eta = w.eta;
+    a.out.sig_tot = w.sig_tot;
+    a.out.sig_sel = w.sig_sel;
+    a.out.flags = w.flags;
+    a.out.do_xsec = true;
+    h[g] = a;
+  }
+  // units of one chunk, waves in decreasing cost (n^3), energies in order
+  std::vector<int> order(p.n_waves);
+  for (int g = 0; g < p.n_waves; ++g) order[g] = g;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return p.waves[x].n > p.waves[y].n; });
+  std::vector<int2> units;
+  units.reserve((size_t)p.n_waves * G.chunk);
+  for (int g : order)
+    for (int e = 0; e < G.chunk; ++e) units.push_back(make_int2(g, e));
+  cudaError_t err;
+  if (!G.solve_waves) {
+    if ((err = cudaMalloc(&G.solve_waves, sizeof(SolveArgs) * p.n_waves)) != cudaSuccess) return err;
+  }
+  if (G.units && G.n_units != (int)units.size()) {
+    cudaFree(G.units);
+    G.units = nullptr;
+  }
+  if (!G.units) {
+    if ((err = cudaMalloc(&G.units, sizeof(int2) * units.size())) != cudaSuccess) return err;
+  }
+  if (!G.counter) {
+    if ((err = cudaMalloc(&G.counter, sizeof(int))) != cudaSuccess) return err;
+  }
+  G.n_units = (int)units.size();
+  if ((err = cudaMemcpy(G.solve_waves, h.data(), sizeof(SolveArgs) * p.n_waves, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return err;
+  if ((err = cudaMemcpy(G.units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return err;
+  return cudaFuncSetAttribute(solve_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)solve_smem_bytes(p.n_max));
+}
+
+cudaError_t launch_solve_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {
+  const GroupDev& G = p.grp;
+  cudaError_t err = cudaMemsetAsync(G.counter, 0, sizeof(int), s);
+  if (err != cudaSuccess) return err;
+  const int grid = std::min(p.solve_slots, p.n_waves * ne);
+  solve_grouped_kernel<<<grid, NT, solve_smem_bytes(p.n_max), s>>>(
+      reinterpret_cast<const SolveArgs*>(G.solve_waves), G.units, G.n_units, e0, ne, G.counter);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // C ABI of the R-matrix outer-region sweep: plan management and the chunked
 // per-energy pipeline (pole sum -> asymptotic data -> matching LU -> S-step).
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -59,6 +60,13 @@ void free_plan(Plan* p) {
   }
   dfree(p->energies); dfree(p->sel_dev); dfree(p->Rbuf); dfree(p->asym); dfree(p->slot);
   dfree(p->err_word);
+  GroupDev& G = p->grp;
+  for (double* r : G.R) dfree(r);
+  for (double* a : G.asym) dfree(a);
+  dfree(G.tc_waves); dfree(G.maps); dfree(G.tiles); dfree(G.near_waves); dfree(G.near_jobs);
+  dfree(G.asym_waves); dfree(G.solve_waves); dfree(G.units); dfree(G.counter);
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (G.cap) cudaStreamDestroy(G.cap);
   for (int k = 0; k < RM_KERNEL_COUNT; ++k)
     for (auto& pr : p->ev_live[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   for (auto e : p->ev_pool) cudaEventDestroy(e);
@@ -98,6 +106,16 @@ rm_status_t upload_wave(Plan* p, WaveDev& d, const rm_wave& w, int32_t mem) {
     for (int i = 0; i < d.n; ++i) lmax = w.l[i] > lmax ? w.l[i] : lmax;
     d.lmax = lmax;
   }
+  return RM_OK;
+}
+
+// Device work lists of the grouped run for the current group chunk.
+rm_status_t group_setup(Plan* p) {
+  if (p->n_e == 0) return RM_OK;
+  if (p->prec == RM_PREC_SPLIT_BF16) RM_CUDA(group_setup_split(*p), "grouped split setup");
+  RM_CUDA(group_setup_asym(*p), "grouped asymptotics setup");
+  RM_CUDA(group_setup_solve(*p), "grouped solve setup");
+  p->grp.ready = true;
   return RM_OK;
 }
 
@@ -143,6 +161,8 @@ rm_status_t prepare(Plan* p, const rm_wave* waves, const double* energies, int32
     for (int q = 0; q < p->n_sel; ++q)
       if (p->sel[q] >= p->waves[g].n && p->n_waves == 1)
         return fail(RM_ERR_ARG, "selected initial channel out of range");
+  rm_status_t st = group_setup(p);
+  if (st != RM_OK) return st;
   p->ran = false;
   return RM_OK;
 }
@@ -164,17 +184,20 @@ cudaEvent_t pool_event(Plan* p) {
 struct Prof {
   Plan* p;
   int k;
+  cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
-  Prof(Plan* p_, int k_) : p(p_), k(k_) {
-    p->launches++;
-    if (!p->prof) return;
+  Prof(Plan* p_, int k_) : Prof(p_, k_, p_->prof, p_->stream, true) {}
+  // count = false while capturing into a graph (graph launches are counted per replay)
+  Prof(Plan* p_, int k_, bool on, cudaStream_t s_, bool count) : p(p_), k(k_), s(s_) {
+    if (count) p->launches++;
+    if (!on) return;
     a = pool_event(p);
     b = pool_event(p);
-    if (a) cudaEventRecord(a, p->stream);
+    if (a) cudaEventRecord(a, s);
   }
   ~Prof() {
     if (!a || !b) return;
-    cudaEventRecord(b, p->stream);
+    cudaEventRecord(b, s);
     p->ev_live[k].push_back({a, b});
   }
 };
@@ -293,6 +316,147 @@ rm_status_t copy_back(Plan* p, T* user, T* dev, int64_t count, int32_t mem) {
   return RM_OK;
 }
 
+// Enqueue the grouped sweep (every wave per launch) on stream s.
+rm_status_t enqueue_grouped(Plan* p, cudaStream_t s, bool prof, int* kernels, bool count) {
+  GroupDev& G = p->grp;
+  int nk = 0;
+  for (int64_t c0 = 0; c0 < p->n_e; c0 += G.chunk) {
+    const int ne = (int)((p->n_e - c0) < G.chunk ? (p->n_e - c0) : G.chunk);
+    if (p->prec == RM_PREC_SPLIT_BF16) {
+      {
+        Prof pr(p, RM_KERNEL_POLESUM_SPLIT, prof, s, count);
+        RM_CUDA(launch_polesum_split_grouped(*p, c0, ne, s), "grouped split pole-sum kernel");
+      }
+      {
+        Prof pr(p, RM_KERNEL_NEAR, prof, s, count);
+        RM_CUDA(launch_near_grouped(*p, c0, ne, s), "grouped near-window kernel");
+      }
+      nk += 2;
+    } else {
+      for (int g = 0; g < p->n_waves; ++g) {
+        Prof pr(p, RM_KERNEL_POLESUM_FP64, prof, s, count);
+        RM_CUDA(launch_polesum_fp64(p->waves[g], c0, ne, G.R[g], s), "FP64 pole-sum kernel");
+        ++nk;
+      }
+    }
+    {
+      Prof pr(p, RM_KERNEL_ASYM, prof, s, count);
+      RM_CUDA(launch_asym_grouped(*p, c0, ne, s), "grouped asymptotics kernel");
+    }
+    {
+      Prof pr(p, RM_KERNEL_SOLVE, prof, s, count);
+      RM_CUDA(launch_solve_grouped(*p, c0, ne, s), "grouped solve kernel");
+    }
+    nk += 2;
+  }
+  if (kernels) *kernels = nk;
+  return RM_OK;
+}
+
+// Capture the grouped sweep once into a CUDA graph (on a private stream).
+rm_status_t build_graph(Plan* p) {
+  GroupDev& G = p->grp;
+  if (G.exec) return RM_OK;
+  if (!G.cap) RM_CUDA(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking), "create capture stream");
+  RM_CUDA(cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  int nk = 0;
+  rm_status_t st = enqueue_grouped(p, G.cap, false, &nk, false);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(G.cap, &graph);
+  if (st != RM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "end capture");
+  e = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    G.exec = nullptr;
+    return cuda_fail(e, "instantiate graph");
+  }
+  G.graph_kernels = nk;
+  return RM_OK;
+}
+
+// Energy-chunk size of the grouped run: time each candidate on the first
+// energies of the mesh and keep the fastest per energy; optional cache file
+// keyed by the plan's sizes.
+std::string tune_key(const Plan* p) {
+  std::string k = "rm1 prec=" + std::to_string(p->prec) + " ne=" + std::to_string(p->n_e) +
+                  " sel=" + std::to_string(p->n_sel);
+  for (const auto& w : p->waves) k += " " + std::to_string(w.n) + "x" + std::to_string(w.N);
+  return k;
+}
+
+int cache_lookup(const char* path, const std::string& key) {
+  if (!path) return 0;
+  FILE* f = fopen(path, "r");
+  if (!f) return 0;
+  char line[8192];
+  int found = 0;
+  while (fgets(line, sizeof(line), f)) {
+    std::string l(line);
+    const size_t bar = l.rfind('|');
+    if (bar == std::string::npos) continue;
+    if (l.substr(0, bar) == key) found = atoi(l.c_str() + bar + 1);
+  }
+  fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, int chunk) {
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s|%d\n", key.c_str(), chunk);
+  fclose(f);
+}
+
+rm_status_t autotune_chunk(Plan* p, const char* cache, int chunk_max) {
+  GroupDev& G = p->grp;
+  const std::string key = tune_key(p);
+  int best = cache_lookup(cache, key);
+  if (best > 0 && best <= chunk_max) {
+    G.chunk = best;
+    return group_setup(p);
+  }
+  const int64_t ne_t = p->n_e < chunk_max ? p->n_e : chunk_max;
+  cudaEvent_t a = nullptr, b = nullptr;
+  RM_CUDA(cudaEventCreate(&a), "event");
+  RM_CUDA(cudaEventCreate(&b), "event");
+  double best_t = 1e300;
+  best = chunk_max;
+  const int64_t n_e_saved = p->n_e;
+  for (int c = 256; c <= chunk_max; c *= 2) {
+    G.chunk = c;
+    rm_status_t st = group_setup(p);
+    if (st != RM_OK) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
+    p->n_e = ne_t;  // time the first ne_t energies only
+    st = enqueue_grouped(p, p->stream, false, nullptr, true);
+    if (st == RM_OK) {
+      cudaEventRecord(a, p->stream);
+      st = enqueue_grouped(p, p->stream, false, nullptr, true);
+      cudaEventRecord(b, p->stream);
+    }
+    p->n_e = n_e_saved;
+    if (st != RM_OK) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best_t * 0.97) {  // prefer the smaller chunk unless clearly slower
+      best_t = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  G.chunk = best;
+  rm_status_t st = group_setup(p);
+  if (st == RM_OK) cache_store(cache, key, best);
+  p->autotuned = true;
+  return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -361,6 +525,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
 
     Plan* p = new (std::nothrow) Plan();
     if (!p) return fail(RM_ERR_NOMEM, "host allocation failed");
+    int grp_chunk_max = 0;
     p->device = dev;
     p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     p->n_waves = n_waves;
@@ -437,6 +602,22 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if (st == RM_OK) st = dalloc(p, &p->asym, 4ll * chunk * n_max);
       if (st == RM_OK) st = dalloc(p, &p->slot, (int64_t)p->solve_slots * p->slot_doubles);
       if (st == RM_OK) st = dalloc(p, &p->err_word, 1);
+      // grouped-run chunk buffers (all waves at once), at most 2 GiB
+      int64_t per_e = 0;
+      for (const auto& w : p->waves) per_e += (int64_t)w.n * (w.n + 1) / 2 + 4ll * w.n;
+      int64_t cmax = o.chunk > 0 ? o.chunk : ((2ll << 30) / (8 * per_e)) / 256 * 256;
+      if (o.chunk == 0) cmax = cmax < 256 ? 256 : (cmax > 2048 ? 2048 : cmax);
+      if (n_e > 0 && cmax > n_e) cmax = n_e;
+      if (cmax < 1) cmax = 1;
+      grp_chunk_max = (int)cmax;
+      p->grp.chunk = o.chunk > 0 ? o.chunk : (int)(cmax < 1024 ? cmax : 1024);
+      p->grp.R.assign(n_waves, nullptr);
+      p->grp.asym.assign(n_waves, nullptr);
+      for (int g = 0; g < n_waves && st == RM_OK; ++g) {
+        const WaveDev& d = p->waves[g];
+        st = dalloc(p, &p->grp.R[g], cmax * ((int64_t)d.n * (d.n + 1) / 2));
+        if (st == RM_OK) st = dalloc(p, &p->grp.asym[g], 4ll * cmax * d.n);
+      }
     }
     if (st == RM_OK) {
       if (cudaMemcpy(p->sel_dev, p->sel, sizeof(int32_t) * n_sel, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -449,6 +630,8 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
          near_smem_bytes(n_max) > (size_t)prop.sharedMemPerBlockOptin))
       st = fail(RM_ERR_ARG, "split-precision kernels do not fit this device's shared memory");
     if (st == RM_OK) st = prepare(p, waves, energies, o.mem);
+    if (st == RM_OK && o.autotune && o.chunk == 0 && n_e > 0 && grp_chunk_max >= 256)
+      st = autotune_chunk(p, o.tune_cache, grp_chunk_max);
     if (st != RM_OK) {
       free_plan(p);
       return st;
@@ -572,17 +755,19 @@ rm_status_t rm_run(rm_plan_t h) {
     Plan* p = as_plan(h);
     if (!p) return fail(RM_ERR_ARG, "null plan");
     if (cudaSetDevice(p->device) != cudaSuccess) return fail(RM_ERR_CUDA, "cudaSetDevice failed");
-    for (int g = 0; g < p->n_waves; ++g) {
-      WaveDev& w = p->waves[g];
-      RangeOut o;
-      o.need_solve = true;
-      o.so.do_xsec = true;
-      o.so.eta = w.eta;
-      o.so.sig_tot = w.sig_tot;
-      o.so.sig_sel = w.sig_sel;
-      o.so.flags = w.flags;
-      rm_status_t st = run_range(p, g, 0, p->n_e, o);
+    if (p->n_e == 0) {
+      p->ran = true;
+      return RM_OK;
+    }
+    if (!p->grp.ready) return fail(RM_ERR_STATE, "grouped work lists not prepared");
+    if (p->prof) {
+      rm_status_t st = enqueue_grouped(p, p->stream, true, nullptr, true);
       if (st != RM_OK) return st;
+    } else {
+      rm_status_t st = build_graph(p);
+      if (st != RM_OK) return st;
+      RM_CUDA(cudaGraphLaunch(p->grp.exec, p->stream), "graph launch");
+      p->launches += p->grp.graph_kernels;
     }
     p->ran = true;
     return RM_OK;
@@ -632,6 +817,7 @@ rm_status_t rm_sync(rm_plan_t h) {
 
 rm_status_t rm_plan_info(rm_plan_t h, int32_t wave, int32_t* n_ch, int32_t* n_poles, int64_t* n_e,
                          int32_t* n_sel, int32_t* chunk, int64_t* workspace_bytes) {
+  // chunk reports the energy-chunk size of rm_run (the grouped, graph-captured sweep)
   Plan* p = as_plan(h);
   if (!p) return fail(RM_ERR_ARG, "null plan");
   if (wave < 0 || wave >= p->n_waves) return fail(RM_ERR_ARG, "wave index out of range");
@@ -639,7 +825,7 @@ rm_status_t rm_plan_info(rm_plan_t h, int32_t wave, int32_t* n_ch, int32_t* n_po
   if (n_poles) *n_poles = p->waves[wave].N;
   if (n_e) *n_e = p->n_e;
   if (n_sel) *n_sel = p->n_sel;
-  if (chunk) *chunk = p->chunk;
+  if (chunk) *chunk = p->grp.chunk;
   if (workspace_bytes) *workspace_bytes = p->workspace_bytes;
   return RM_OK;
 }

@@ -73,6 +73,31 @@ struct WaveDev {
   SplitDev split;
 };
 
+// Grouped (all waves in one launch per kernel) run of the sweep, captured in
+// a CUDA graph; per-wave chunk buffers and the device-side work lists.
+struct GroupDev {
+  int chunk = 0;
+  std::vector<double*> R;     // per wave [chunk * n_p]
+  std::vector<double*> asym;  // per wave [4 * chunk * n]
+  void* tc_waves = nullptr;   // per-wave tensor-core arguments
+  CUtensorMap* maps = nullptr;  // [2 * n_waves] TMA descriptors (omega, poles)
+  int4* tiles = nullptr;      // (wave, i-block, j-block), longest K first
+  int n_tiles = 0;
+  void* near_waves = nullptr;
+  int2* near_jobs = nullptr;  // (wave, first energy of an 8-energy block)
+  int n_near_jobs = 0;
+  int near_splits = 1;
+  void* asym_waves = nullptr;
+  void* solve_waves = nullptr;
+  int2* units = nullptr;      // (wave, chunk energy), decreasing cost
+  int n_units = 0;
+  int* counter = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_kernels = 0;
+  bool ready = false;
+};
+
 struct Plan {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -105,6 +130,8 @@ struct Plan {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_live[RM_KERNEL_COUNT];
   double prof_ms[RM_KERNEL_COUNT] = {0};
   int64_t prof_n[RM_KERNEL_COUNT] = {0};
+  GroupDev grp;
+  bool autotuned = false;
 };
 
 // ---------------------------------------------------------------------------
@@ -142,5 +169,14 @@ cudaError_t launch_polesum_split(const Plan& p, const WaveDev& w, int64_t e0, in
 cudaError_t launch_near(const Plan& p, const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s);
 size_t polesum_tc_smem_bytes();
 size_t near_smem_bytes(int n);
+
+// grouped run (all waves per launch)
+cudaError_t group_setup_split(Plan& p);
+cudaError_t group_setup_asym(Plan& p);
+cudaError_t group_setup_solve(Plan& p);
+cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
+cudaError_t launch_near_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
+cudaError_t launch_asym_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
+cudaError_t launch_solve_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
 
 }  // namespace rm

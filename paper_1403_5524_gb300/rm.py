@@ -37,7 +37,7 @@ class rm_wave(C.Structure):
 class rm_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("delta", C.c_double), ("slices", C.c_int32),
                 ("sel_init", C.c_void_p), ("n_sel", C.c_int32), ("mem", C.c_int32),
-                ("chunk", C.c_int32)]
+                ("chunk", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p)]
 
 
 class RMError(RuntimeError):
@@ -117,7 +117,8 @@ class Plan:
     """
 
     def __init__(self, waves: Sequence, energies, prec: str = "fp64", delta: float = 0.05,
-                 sel: Sequence[int] = (0,), chunk: int = 0, slices: int = 0, stream=None):
+                 sel: Sequence[int] = (0,), chunk: int = 0, slices: int = 0, stream=None,
+                 autotune: bool = False, tune_cache: Optional[str] = None):
         self.lib = load_library()
         self._keep = []
         self.mem = RM_MEM_DEVICE if _is_dev(energies) else RM_MEM_HOST
@@ -132,6 +133,9 @@ class Plan:
         opt.n_sel = int(self._sel.size)
         opt.mem = self.mem
         opt.chunk = int(chunk)
+        opt.autotune = 1 if autotune else 0
+        self._tune_cache = tune_cache.encode() if tune_cache else None
+        opt.tune_cache = self._tune_cache
         h = C.c_void_p()
         self.n_e = int(energies.shape[0])
         self.n_waves = len(waves)

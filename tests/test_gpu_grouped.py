@@ -1,0 +1,99 @@
+"""Grouped sweep (all partial waves per launch, CUDA-graph replay, autotuned
+energy chunks) on the 40-wave workload (needs a GPU)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import rmatrix as orc
+from paper_1403_5524_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1403_5524_gb300 import rm as _rm
+    _rm.load_library()
+    return _rm
+
+
+def test_forty_waves_against_oracle(rm):
+    # the 40-wave workload (n_ch 9..387, N = 40 n_ch) on a 600-energy mesh
+    wl = synth.config(4)
+    E = np.linspace(0.01, 5.0, 600)
+    sel = (0,)
+    with rm.Plan(wl.waves, E, prec="split_bf16", delta=0.05, sel=sel) as p:
+        p.run()
+        outs = []
+        for g, w in enumerate(wl.waves):
+            o = rm.host_outputs(E.size, w.n, 1)
+            p.results(g, 0, E.size, **o)
+            outs.append(o)
+    for g, w in enumerate(wl.waves):
+        idx = np.array([7 + 13 * g % 580, 599 - 7 * g % 300])
+        ref = orc.sweep(w, E, sel=sel, energy_idx=idx, keep_R=False, keep_K=False)
+        for t, e in enumerate(idx):
+            assert outs[g]["n_open"][e] == ref["n_open"][t]
+            if ref["flags"][t] & orc.FLAG_ILLCOND:
+                continue
+            st = ref["sig_tot"][t, 0]
+            err = np.abs(outs[g]["sig_sel"][e, 0] - ref["sig_sel"][t, 0]).max() / st
+            assert err <= 1e-8, (g, w.n, e, err)
+            d = outs[g]["eigsum"][e] - ref["eta"][t]
+            assert abs(np.mod(d + np.pi, 2 * np.pi) - np.pi) <= 1e-7, (g, e)
+
+
+def test_graph_replay_and_launch_count(rm):
+    waves = [synth.small(300 + g, n, 40 * n, 1, pole_lo=-3, pole_hi=12, a=20.0).waves[0]
+             for g, n in enumerate([7, 30, 12])]
+    E = np.linspace(0.05, 3.0, 300)
+    with rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=(0, 1), chunk=128) as p:
+        l0 = p.launches()
+        p.run()
+        l1 = p.launches()
+        first = [rm.host_outputs(E.size, w.n, 2) for w in waves]
+        for g in range(3):
+            p.results(g, 0, E.size, **first[g])
+        p.run()
+        p.run()
+        l3 = p.launches()
+        for g in range(3):
+            o = rm.host_outputs(E.size, waves[g].n, 2)
+            p.results(g, 0, E.size, **o)
+            for k in ("eigsum", "sig_sel", "sig_tot"):
+                assert np.array_equal(o[k], first[g][k]), k
+        # 3 chunks x (pole sum, near window, asymptotics, solve) per replay
+        assert l1 - l0 == 12 and l3 - l1 == 24
+        # profiled (direct) launches give the same numbers as the graph replay
+        p.profile(True)
+        p.run()
+        prof = p.profile_read()
+        p.profile(False)
+        assert prof["solve"][1] == 3 and prof["polesum_split"][1] == 3
+        for g in range(3):
+            o = rm.host_outputs(E.size, waves[g].n, 2)
+            p.results(g, 0, E.size, **o)
+            assert np.array_equal(o["sig_sel"], first[g]["sig_sel"])
+
+
+def test_autotune_and_cache(rm, tmp_path):
+    wl = synth.small(41, 24, 900, 1500, e_lo=0.05, e_hi=3.0, pole_lo=-3, pole_hi=10, a=18.0)
+    cache = str(tmp_path / "tune.txt")
+    with rm.Plan(wl.waves, wl.energies, prec="split_bf16", delta=0.05, autotune=True, tune_cache=cache) as p:
+        chunk = p.info(0)["chunk"]
+        p.run()
+        o1 = rm.host_outputs(wl.n_e, 24, 1)
+        p.results(0, 0, wl.n_e, **o1)
+    assert chunk in (256, 512, 1024) and os.path.exists(cache)
+    line = open(cache).read().strip().splitlines()[-1]
+    assert line.endswith("|%d" % chunk)
+    with rm.Plan(wl.waves, wl.energies, prec="split_bf16", delta=0.05, autotune=True, tune_cache=cache) as p:
+        assert p.info(0)["chunk"] == chunk
+        p.run()
+        o2 = rm.host_outputs(wl.n_e, 24, 1)
+        p.results(0, 0, wl.n_e, **o2)
+    assert np.array_equal(o1["sig_sel"], o2["sig_sel"])

@@ -156,3 +156,34 @@ def test_split_config3_sampled(rm):
     ref = orc.sweep(wl.waves[0], wl.energies, sel=(0,), energy_idx=idx)
     worst = check(wl, g, ref, per_element=False)
     print("config3 split worst normwise errors", worst)
+
+
+def test_split_multiwave(rm):
+    # several partial waves of uneven size in one plan, one shared energy mesh
+    rng_sizes = [(5, 200), (23, 900), (9, 360), (40, 1600)]
+    waves = []
+    for g, (n, N) in enumerate(rng_sizes):
+        waves.append(synth.small(200 + g, n, N, 1, pole_lo=-3.0, pole_hi=10.0, a=18.0).waves[0])
+    E = np.linspace(0.03, 3.2, 140)
+    sel = (0, 1)
+    with rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, chunk=128) as p:
+        p.run()
+        outs = []
+        for g, w in enumerate(waves):
+            o = rm.host_outputs(E.size, w.n, 2)
+            p.results(g, 0, E.size, **o)
+            outs.append(o)
+    idx = np.arange(0, E.size, 9)
+    for g, w in enumerate(waves):
+        ref = orc.sweep(w, E, sel=sel, energy_idx=idx, keep_R=False)
+        for t, e in enumerate(idx):
+            assert outs[g]["n_open"][e] == ref["n_open"][t]
+            if ref["flags"][t] & orc.FLAG_ILLCOND:
+                continue
+            for q in range(2):
+                st = ref["sig_tot"][t, q]
+                if st > 0:
+                    err = np.abs(outs[g]["sig_sel"][e, q] - ref["sig_sel"][t, q]).max() / st
+                    assert err <= TOL_SIG, (g, e, q, err)
+            d = outs[g]["eigsum"][e] - ref["eta"][t]
+            assert abs(np.mod(d + np.pi, 2 * np.pi) - np.pi) <= 1e-7
