@@ -65,7 +65,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=3)
-    ap.add_argument("--prec", default="split_bf16", choices=["fp64", "split_bf16"])
+    ap.add_argument("--prec", default="split_bf16", choices=["fp64", "split_bf16", "split_fp16", "fp32_simt"])
+    ap.add_argument("--variants", action="store_true",
+                    help="compare the pole-sum forms (split BF16, split FP16, FP32 SIMT, FP64) on this workload")
     ap.add_argument("--fp64-stride", type=int, default=25,
                     help="mesh stride of the plain FP64 GPU comparison run (0 = skip it)")
     ap.add_argument("--stride", type=int, default=0,
@@ -233,7 +235,7 @@ def run_ours(args):
                          poles=torch.from_numpy(w.poles).to(dev), W=torch.from_numpy(w.W).to(dev), a=w.a)
               for w in wl.waves]
     dE = torch.from_numpy(wl.energies).to(dev)
-    plan = rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream)
+    plan = rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream, autotune=True)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
     def barrier():
@@ -379,6 +381,7 @@ def run_ours(args):
                 "dtype": "f64" if args.prec == "fp64" else "bf16-split+f64",
                 "data": "synthetic (seeded, workload distributions of the paper's problem class)",
                 "config": {"workload": wl.name, "prec": args.prec, "mesh_stride": stride,
+                           "energy_chunk": plan.info(0)["chunk"],
                            "energies_per_step": wl.n_e, "waves": len(wl.waves),
                            "n_ch": [w.n for w in wl.waves][:4], "n_poles": [w.N for w in wl.waves][:4],
                            "n_sel": len(sel), "l2": "flushed (512 MB write) between timed steps",
@@ -423,8 +426,61 @@ def accuracy(plan, wl, sel, idx, ref):
             "norm": "max|x - x*| / max|x*| per energy (sigma: / sigma_tot of the initial channel)"}
 
 
+def run_variants(args):
+    """Pole-sum forms side by side: energies/s of rm_run and errors against the oracle."""
+    import torch
+    from oracle import rmatrix as orc
+    from paper_1403_5524_gb300 import rm
+    dev = torch.device("cuda", 0)
+    wl, _ = workload(args)
+    stride = args.stride if args.stride > 0 else 8
+    E = wl.energies[::stride].copy()
+    w = wl.waves[0]
+    dwaves = [synth.Wave(l=torch.from_numpy(x.l).to(dev), thresh=torch.from_numpy(x.thresh).to(dev),
+                         poles=torch.from_numpy(x.poles).to(dev), W=torch.from_numpy(x.W).to(dev), a=x.a)
+              for x in wl.waves]
+    dE = torch.from_numpy(E).to(dev)
+    idx = np.linspace(0, E.size - 1, 6).astype(int)
+    ref = orc.sweep(w, E, sel=(0,), energy_idx=idx)
+    res = {}
+    for prec in ("split_bf16", "split_fp16", "fp32_simt", "fp64"):
+        with rm.Plan(dwaves, dE, prec=prec, delta=wl.delta, sel=(0,)) as p:
+            p.run()
+            p.sync()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(torch.cuda.current_stream(dev))
+            p.run()
+            a1.record(torch.cuda.current_stream(dev))
+            p.sync()
+            ms = a0.elapsed_time(a1)
+            eR = eK = eS = 0.0
+            n = w.n
+            R = np.zeros((1, n * (n + 1) // 2))
+            K = np.zeros((1, n, n))
+            for t, e in enumerate(idx):
+                e = int(e)
+                p.rmatrix(0, e, e + 1, R)
+                eR = max(eR, float(np.abs(R[0] - ref["R"][t]).max() / np.abs(ref["R"][t]).max()))
+                if ref["flags"][t] & 2:
+                    continue
+                p.kmatrix(0, e, e + 1, K=K)
+                no = ref["n_open"][t]
+                Ko = ref["K"][t, :no, :no]
+                eK = max(eK, float(np.abs(K[0, :no, :no] - Ko).max() / np.abs(Ko).max()))
+                sig = np.zeros((1, 1, n))
+                p.xsec(0, e, e + 1, sig_sel=sig)
+                eS = max(eS, float(np.abs(sig[0, 0] - ref["sig_sel"][t, 0]).max() / ref["sig_tot"][t, 0]))
+        res[prec] = {"energies_per_s": E.size / (ms / 1000.0), "ms_per_sweep": ms, "err_R": eR, "err_K": eK,
+                     "err_sigma": eS}
+    print(json.dumps({"variants": res, "config": {"workload": wl.name, "mesh_stride": stride,
+                                                  "energies": int(E.size), "errors_on": int(idx.size)}}))
+
+
 def main():
     args = parse()
+    if args.variants:
+        run_variants(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -62,8 +62,11 @@ typedef enum { RM_MEM_HOST = 0, RM_MEM_DEVICE = 1 } rm_mem_t;
 
 typedef enum {
   RM_PREC_FP64 = 0,        /* pole sum over all poles in FP64 (baseline form) */
-  RM_PREC_SPLIT_BF16 = 1   /* far poles: sliced BF16 tcgen05 GEMM, FP32 TMEM
+  RM_PREC_SPLIT_BF16 = 1,  /* far poles: sliced BF16 tcgen05 GEMM, FP32 TMEM
                               accumulation; |E_k - E| < delta in FP64 */
+  RM_PREC_SPLIT_FP16 = 2,  /* as SPLIT_BF16 with the slices held in FP16 */
+  RM_PREC_FP32_SIMT = 3    /* far poles: plain FP32 products and FP32 accumulation
+                              on the CUDA cores; near window in FP64 (comparison form) */
 } rm_precision_t;
 
 /* per-energy flag bits */

@@ -25,6 +25,7 @@
 // index ranges [klo, khi) and summed in FP64 by the near-window kernel, so the
 // two parts partition the pole set exactly.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <algorithm>
 #include <vector>
 #include <cudaTypedefs.h>
@@ -103,6 +104,18 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// The slices s0..s2 sit on grids 1, 2^-8, 2^-16 with at most 8 significant
+// bits, so they are exact in FP16 as well (the 2^-16 grid lies in FP16's
+// subnormal range, spacing 2^-24); s3 is rounded to 2^-24 there.
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+  __half2 v = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_slice(float lo, float hi, bool f16) {
+  return f16 ? pack_f16x2(lo, hi) : pack_bf16x2(lo, hi);
+}
+
 struct TCArgs {
   const float* mult_p;
   const double* f_p;
@@ -114,6 +127,7 @@ struct TCArgs {
   const float* El;
   const int2* tiles;
   int n, N, nK;
+  int f16;          // slices in FP16 instead of BF16
   int64_t e_begin;  // absolute index of the chunk's first energy
   int ne;           // energies in the chunk
   double* R;        // [ne * np]
@@ -181,8 +195,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         tma_last[s] = j;
       };
       for (int s = 0; s < STAGES && s < nK; ++s) issue_tma(s, s);
-      const uint32_t idN256 = idesc_bf16_f32(128, 256);
-      const uint32_t idN128 = idesc_bf16_f32(128, 128);
+      const uint32_t idN256 = idesc_bf16_f32(128, 256, g.f16 != 0);
+      const uint32_t idN128 = idesc_bf16_f32(128, 128, g.f16 != 0);
       bool ok = true;
       bool issued = false;
       for (int j = 0; j < nK; ++j) {
@@ -238,6 +252,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
   } else {
     // -------------------------------------------------- producers and drains
     const int w = warp;
+    const bool f16 = g.f16 != 0;
     // A role: i-row ai, j-rows jj = jbase + 2t (t = 0..3), k-pair kpa (all 16 k-pairs per
     // half-warp); a half-warp reads one staged row contiguously and writes one full slice row.
     const int ai = w >> 1, kpa = lane & 15, jbase = (w & 1) * 8 + (lane >> 4);
@@ -299,7 +314,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         slice4(__fmul_rn(ph1, mp[t]), __fmul_rn(pl1, mp[t]), s1);
         const uint32_t off = swz(ai * 16 + jj, k);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + off) = pack_bf16x2(s0[u], s1[u]);
+        for (int u = 0; u < 4; ++u)
+          *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + off) = pack_slice(s0[u], s1[u], f16);
       }
       const int k0 = j * KS;
 #pragma unroll 1
@@ -319,7 +335,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         slice4(__fmul_rn(rh1, m1), __fmul_rn(rl1, m1), s1);
         const uint32_t off = swz(rb, k);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + off) = pack_bf16x2(s0[v], s1[v]);
+        for (int v = 0; v < 4; ++v)
+          *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + off) = pack_slice(s0[v], s1[v], f16);
       }
       fence_proxy_async_smem();
       __syncwarp();
@@ -691,6 +708,7 @@ cudaError_t launch_polesum_split(const Plan& p, const WaveDev& w, int64_t e0, in
   g.n = w.n;
   g.N = w.N;
   g.nK = w.Npad / KS;
+  g.f16 = p.prec == RM_PREC_SPLIT_FP16 ? 1 : 0;
   g.e_begin = e0;
   g.ne = ne;
   g.R = R;
@@ -743,6 +761,7 @@ cudaError_t group_setup_split(Plan& p) {
     a.n = w.n;
     a.N = w.N;
     a.nK = w.Npad / KS;
+    a.f16 = p.prec == RM_PREC_SPLIT_FP16 ? 1 : 0;
     a.e_begin = 0;
     a.ne = 0;
     a.R = G.R[g];

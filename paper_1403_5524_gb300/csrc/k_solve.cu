@@ -71,6 +71,14 @@ struct Ops<cplx> {
   }
 };
 
+// smallest power of two >= min(TC, w), at least 1
+__device__ __forceinline__ int tile_width_pow2(int w) {
+  w = w < TC ? w : TC;
+  int p = 1;
+  while (p < w) p <<= 1;
+  return p;
+}
+
 struct LUStat {
   double pmin, pmax;
   int swaps;
@@ -120,9 +128,8 @@ __device__ int panel_argmax(const T* panel, int rows, int j, Red* red) {
 // four independent loads are in flight, the tile column held in registers.
 template <typename T>
 __device__ __forceinline__ void rank_update(T* __restrict__ A, int ld, int col, int r0, int r1, const T* panel,
-                                            const T* tile, int nb) {
+                                            const T* tile, int nb, int RS) {
   using O = Ops<T>;
-  constexpr int RS = NT / TC;  // row stride between the threads of one column
   T u[NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) u[j] = (j < nb) ? tile[j * TC] : O::zero();
@@ -236,14 +243,18 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
       for (int idx = t; idx < NB * TC; idx += NT) {
         // L11^-1 is unit lower triangular: terms i <= j only (j is uniform across a warp)
         const int j = idx / TC, c = idx % TC, col = c0 + c;
+        if (col >= m) continue;  // columns past the matrix are never read
         T u = tmp[j * TC + c];
         for (int i = 0; i < j; ++i) u = O::fma_acc(u, tri[j * NB + i], tmp[i * TC + c]);
         tile[idx] = u;
         if (j < nb && col < m) A[(int64_t)(kb + j) * ld + col] = u;
       }
       __syncthreads();
-      const int tc = t % TC, tr = t / TC;
-      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, kb + nb + tr, n, panel - (int64_t)kb * NB, tile + tc, nb);
+      // threads over (column, row group); narrow tiles get more row groups so
+      // that every warp instruction carries full lanes
+      const int cwp = tile_width_pow2(m - c0);
+      const int tc = t % cwp, tr = t / cwp;
+      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, kb + nb + tr, n, panel - (int64_t)kb * NB, tile + tc, nb, NT / cwp);
       __syncthreads();
     }
   }
@@ -282,14 +293,16 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
       for (int idx = t; idx < NB * TC; idx += NT) {
         // U11^-1 is upper triangular: terms i >= j only (j is uniform across a warp)
         const int j = idx / TC, c = idx % TC, col = c0 + c;
+        if (col >= m) continue;  // columns past the matrix are never read
         T y = O::zero();
         for (int i = j; i < nb; ++i) y = O::fma_acc(y, tri[j * NB + i], tmp[i * TC + c]);
         tile[idx] = y;
         if (j < nb && col < m) A[(int64_t)(kb + j) * ld + col] = y;
       }
       __syncthreads();
-      const int tc = t % TC, tr = t / TC;
-      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, tr, kb, panel, tile + tc, nb);
+      const int cwp = tile_width_pow2(m - c0);
+      const int tc = t % cwp, tr = t / cwp;
+      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, tr, kb, panel, tile + tc, nb, NT / cwp);
       __syncthreads();
     }
   }
@@ -383,11 +396,14 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   __syncthreads();
   if (s_singular) fl |= RM_FLAG_SINGULAR;
   else if (s_ratio < 1e-12) fl |= RM_FLAG_ILLCOND;
-  // K_jm = Y_jm / c_j
+  // K_jm = Y_jm / c_j, with one reciprocal per row (kept in the free tmp area)
+  double* rc = reinterpret_cast<double*>(tmp_c);
+  for (int i = t; i < no; i += NT) rc[i] = 1.0 / c[i];
+  __syncthreads();
   if (g.out.K) {
     for (int64_t idx = t; idx < (int64_t)no * no; idx += NT) {
       const int j = (int)(idx / no), mo = (int)(idx % no);
-      g.out.K[(int64_t)e * n * n + (int64_t)j * n + mo] = A[(int64_t)j * g.ldR + n + mo] / c[j];
+      g.out.K[(int64_t)e * n * n + (int64_t)j * n + mo] = A[(int64_t)j * g.ldR + n + mo] * rc[j];
     }
   }
   if (t == 0) {
@@ -405,11 +421,11 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     const int i = (int)(idx / mc), j = (int)(idx % mc);
     cplx v;
     if (j < no) {
-      const double kij = A[(int64_t)i * g.ldR + n + j] / c[i];
+      const double kij = A[(int64_t)i * g.ldR + n + j] * rc[i];
       v = cplx{(i == j) ? 1.0 : 0.0, -kij};
     } else {
       const int sq = g.sel[j - no];
-      v = cplx{(sq < no) ? A[(int64_t)i * g.ldR + n + sq] / c[i] : 0.0, 0.0};
+      v = cplx{(sq < no) ? A[(int64_t)i * g.ldR + n + sq] * rc[i] : 0.0, 0.0};
     }
     C[(int64_t)i * g.ldC + j] = v;
   }

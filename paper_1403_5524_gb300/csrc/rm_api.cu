@@ -112,7 +112,7 @@ rm_status_t upload_wave(Plan* p, WaveDev& d, const rm_wave& w, int32_t mem) {
 // Device work lists of the grouped run for the current group chunk.
 rm_status_t group_setup(Plan* p) {
   if (p->n_e == 0) return RM_OK;
-  if (p->prec == RM_PREC_SPLIT_BF16) RM_CUDA(group_setup_split(*p), "grouped split setup");
+  if (is_split_like(p->prec)) RM_CUDA(group_setup_split(*p), "grouped split setup");
   RM_CUDA(group_setup_asym(*p), "grouped asymptotics setup");
   RM_CUDA(group_setup_solve(*p), "grouped solve setup");
   p->grp.ready = true;
@@ -151,7 +151,7 @@ rm_status_t prepare(Plan* p, const rm_wave* waves, const double* energies, int32
       p->launches++;
     }
     if (p->n_e > 0) RM_CUDA(cudaMemsetAsync(d.flags, 0, p->n_e, s), "clear flags");
-    if (p->prec == RM_PREC_SPLIT_BF16) {
+    if (is_split_like(p->prec)) {
       RM_CUDA(split_prepare(*p, d, s), "split-precision preparation");
       p->launches += 4;
     }
@@ -234,7 +234,10 @@ rm_status_t polesum_chunk(Plan* p, const WaveDev& w, int64_t c0, int ne, double*
     RM_CUDA(launch_polesum_fp64(w, c0, ne, R, p->stream), "FP64 pole-sum kernel");
     return RM_OK;
   }
-  {
+  if (p->prec == RM_PREC_FP32_SIMT) {
+    Prof pr(p, RM_KERNEL_POLESUM_SPLIT);
+    RM_CUDA(launch_polesum_fp32(w, c0, ne, R, p->stream), "FP32 pole-sum kernel");
+  } else {
     Prof pr(p, RM_KERNEL_POLESUM_SPLIT);
     RM_CUDA(launch_polesum_split(*p, w, c0, ne, R, p->stream), "split pole-sum kernel");
   }
@@ -322,8 +325,15 @@ rm_status_t enqueue_grouped(Plan* p, cudaStream_t s, bool prof, int* kernels, bo
   int nk = 0;
   for (int64_t c0 = 0; c0 < p->n_e; c0 += G.chunk) {
     const int ne = (int)((p->n_e - c0) < G.chunk ? (p->n_e - c0) : G.chunk);
-    if (p->prec == RM_PREC_SPLIT_BF16) {
-      {
+    if (is_split_like(p->prec)) {
+      if (p->prec == RM_PREC_FP32_SIMT) {
+        for (int g = 0; g < p->n_waves; ++g) {
+          Prof pr(p, RM_KERNEL_POLESUM_SPLIT, prof, s, count);
+          RM_CUDA(launch_polesum_fp32(p->waves[g], c0, ne, G.R[g], s), "FP32 pole-sum kernel");
+          ++nk;
+        }
+        --nk;
+      } else {
         Prof pr(p, RM_KERNEL_POLESUM_SPLIT, prof, s, count);
         RM_CUDA(launch_polesum_split_grouped(*p, c0, ne, s), "grouped split pole-sum kernel");
       }
@@ -499,7 +509,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     rm_options o;
     if (opt) o = *opt; else rm_options_default(&o);
     if (!valid_mem(o.mem)) return fail(RM_ERR_ARG, "bad memory space");
-    if (o.prec != RM_PREC_FP64 && o.prec != RM_PREC_SPLIT_BF16) return fail(RM_ERR_ARG, "bad precision mode");
+    if (o.prec < RM_PREC_FP64 || o.prec > RM_PREC_FP32_SIMT) return fail(RM_ERR_ARG, "bad precision mode");
     if (o.prec != RM_PREC_FP64 && !(o.delta > 0.0)) return fail(RM_ERR_ARG, "delta must be > 0");
     if (o.chunk < 0) return fail(RM_ERR_ARG, "chunk must be >= 0");
     int n_sel = 1;
@@ -560,7 +570,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if ((st = dalloc(p, &d.sig_tot, n_e * n_sel)) != RM_OK) break;
       if ((st = dalloc(p, &d.sig_sel, n_e * n_sel * d.n)) != RM_OK) break;
       if ((st = dalloc(p, &d.flags, n_e)) != RM_OK) break;
-      if (o.prec == RM_PREC_SPLIT_BF16) {
+      if (is_split_like(o.prec)) {
         SplitDev& sd = d.split;
         if ((st = dalloc(p, &sd.omega, 2ll * d.n * d.Npad)) != RM_OK) break;
         if ((st = dalloc(p, &sd.pol, 2ll * d.Npad)) != RM_OK) break;
@@ -586,7 +596,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     if (st == RM_OK) {
       int chunk = o.chunk;
       if (chunk == 0) {
-        const int64_t budget = (o.prec == RM_PREC_SPLIT_BF16 ? 288ll : 96ll) << 20;
+        const int64_t budget = (is_split_like(o.prec) ? 288ll : 96ll) << 20;
         int64_t c = budget / (np_max * 8) / 128 * 128;
         c = c < 128 ? 128 : (c > 8192 ? 8192 : c);
         chunk = (int)c;
@@ -625,7 +635,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     }
     if (st == RM_OK && solve_smem_bytes(n_max) > (size_t)prop.sharedMemPerBlockOptin)
       st = fail(RM_ERR_ARG, "n_ch too large for the solve kernel's shared memory");
-    if (st == RM_OK && o.prec == RM_PREC_SPLIT_BF16 &&
+    if (st == RM_OK && is_split_like(o.prec) &&
         (polesum_tc_smem_bytes() > (size_t)prop.sharedMemPerBlockOptin ||
          near_smem_bytes(n_max) > (size_t)prop.sharedMemPerBlockOptin))
       st = fail(RM_ERR_ARG, "split-precision kernels do not fit this device's shared memory");

@@ -167,6 +167,10 @@ std::vector<int2> split_tiles(int n);
 cudaError_t split_prepare(const Plan& p, WaveDev& w, cudaStream_t s);
 cudaError_t launch_polesum_split(const Plan& p, const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s);
 cudaError_t launch_near(const Plan& p, const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s);
+cudaError_t launch_polesum_fp32(const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s);
+inline bool is_split_like(int prec) {
+  return prec == RM_PREC_SPLIT_BF16 || prec == RM_PREC_SPLIT_FP16 || prec == RM_PREC_FP32_SIMT;
+}
 size_t polesum_tc_smem_bytes();
 size_t near_smem_bytes(int n);
 

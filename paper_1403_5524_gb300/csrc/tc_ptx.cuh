@@ -121,11 +121,11 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw64(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+// Instruction descriptor, kind::f16: BF16 (or FP16) A and B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool f16 = false) {
   return (1u << 4)                          // D format: F32
-         | (1u << 7)                        // A format: BF16
-         | (1u << 10)                       // B format: BF16
+         | ((f16 ? 0u : 1u) << 7)           // A format: BF16 (1) or F16 (0)
+         | ((f16 ? 0u : 1u) << 10)          // B format: BF16 (1) or F16 (0)
          | ((uint32_t)(N >> 3) << 17)       // N / 8
          | ((uint32_t)(M >> 4) << 24);      // M / 16
 }
