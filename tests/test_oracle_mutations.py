@@ -1,0 +1,177 @@
+"""Plant plausible mistakes in the FP64 oracle (on the CPU) and check that the
+independent pins catch every one.
+
+Each mutation rewrites one line of an oracle function (a flipped sign, a
+dropped factor, a transposed scaling, a wrong index, an inverted Cayley map,
+...), compiles the result into the oracle module for the duration of the test,
+and runs a compact set of pins: single-pole Breit-Wigner, Lane-Thomas l = 1,
+hard sphere, the Bloch-operator resolvent, closed-channel elimination, K
+symmetry / S unitarity, detailed balance, and the nudge.  A mutation that no
+pin rejects would mean the oracle is not pinned where that mistake lives.
+"""
+import inspect
+import math
+import textwrap
+
+import numpy as np
+import pytest
+from scipy.special import spherical_kn
+
+from oracle import rmatrix as o
+from paper_1403_5524_gb300 import synth
+from tests.test_oracle_pins import (bloch_inner_region, jhat_explicit, nhat_explicit,
+                                    one_channel_wave)
+
+
+def mutate(func, old, new):
+    src = textwrap.dedent(inspect.getsource(func))
+    assert old in src, (func.__name__, old)
+    ns = dict(vars(o))
+    exec(compile(src.replace(old, new, 1), "<mutant>", "exec"), ns)
+    return ns[func.__name__]
+
+
+# ---------------------------------------------------------------- pins
+def pin_breit_wigner():
+    a, w, E1, E = 20.0, 0.7, 2.5, 1.1
+    out = o.sweep(one_channel_wave(0, w, E1, a), np.array([E]))
+    k = math.sqrt(E)
+    d = -k * a + math.atan(k * w * w / (2.0 * (E1 - E)))
+    sig = 4.0 * math.pi / k ** 2 * math.sin(d) ** 2
+    S, _ = o.smatrix(out["K"][0, :1, :1])
+    return (abs(math.sin(math.atan(out["K"][0, 0, 0]) - d)) < 1e-10
+            and abs(out["sig_sel"][0, 0, 0] - sig) < 1e-10 * sig
+            and abs(math.sin(out["eta"][0] - d)) < 1e-10
+            and abs(S[0, 0] - np.exp(2j * d)) < 1e-10)
+
+
+def pin_lane_thomas():
+    a, w, E1, E, l = 20.0, 0.5, 2.5, 0.6, 1
+    out = o.sweep(one_channel_wave(l, w, E1, a), np.array([E]))
+    k = math.sqrt(E)
+    x = k * a
+    j, jp = jhat_explicit(l, x)
+    n, np_ = nhat_explicit(l, x)
+    O, Op = complex(-n, j), complex(-np_, jp)
+    L = x * Op / O
+    R = w * w / (2.0 * a * (E1 - E))
+    d = -np.angle(O) + math.atan2(L.imag * R, 1.0 - L.real * R)
+    return abs(math.sin(math.atan(out["K"][0, 0, 0]) - d)) < 1e-10
+
+
+def pin_hard_sphere():
+    a, E = 12.0, 1.3
+    wave = synth.Wave(l=np.array([0, 1, 2, 1], np.int32), thresh=np.array([0.0, 0.2, 0.5, 1.5]),
+                      poles=np.array([-1.0, 4.0]), W=np.zeros((4, 2)), a=a)
+    out = o.sweep(wave, np.array([E]))
+    K = out["K"][0]
+    ok = out["n_open"][0] == 3 and np.all(np.isfinite(K))
+    for i in range(3):
+        x = math.sqrt(E - wave.thresh[i]) * a
+        j, _ = jhat_explicit(int(wave.l[i]), x)
+        n, _ = nhat_explicit(int(wave.l[i]), x)
+        ok &= abs(K[i, i] - j / n) <= 1e-10 * max(1.0, abs(j / n))
+    return ok
+
+
+def pin_bloch():
+    import scipy.linalg as sl
+    a = 10.0
+    H, O, Bv = bloch_inner_region(2, 10, a, [0, 1], [0.0, 0.35], seed=11)
+    Ek, C = sl.eigh(H, O)
+    W = math.sqrt(2.0) * (Bv.T @ C)
+    E = 0.57
+    Rp = o.rmatrix(W, Ek, E, a)
+    Rd = (Bv.T @ np.linalg.solve(H - E * O, Bv)) / a
+    return np.abs(Rp - Rd).max() <= 1e-9 * np.abs(Rd).max()
+
+
+def pin_closed_channel():
+    rng = np.random.default_rng(9)
+    N = 25
+    poles = np.sort(rng.uniform(-2, 12, N))
+    W = rng.normal(0, 1 / math.sqrt(N), (2, N))
+    a, lc, E = 8.0, 2, 0.9
+    wave = synth.Wave(l=np.array([0, lc], np.int32), thresh=np.array([0.0, 2.0]), poles=poles, W=W, a=a)
+    out = o.sweep(wave, np.array([E]))
+    d0 = 1.0 / (poles - E)
+    R = (W * d0[None, :]) @ W.T / (2.0 * a)   # independent of the oracle's pole sum
+    kap = math.sqrt(2.0 - E)
+    x = kap * a
+    L1 = kap * (spherical_kn(lc, x) + x * spherical_kn(lc, x, derivative=True)) / (x * spherical_kn(lc, x))
+    Reff = R[0, 0] + a * R[0, 1] * L1 * R[1, 0] / (1.0 - a * R[1, 1] * L1)
+    k = math.sqrt(E)
+    d = -k * a + math.atan(k * a * Reff)
+    return out["n_open"][0] == 1 and abs(math.sin(math.atan(out["K"][0, 0, 0]) - d)) < 1e-10
+
+
+def pin_symmetry_unitarity_balance():
+    wl = synth.config(1)
+    w = wl.waves[0]
+    out = o.sweep(w, wl.energies[600:1000:80], sel=(0, 1, 2, 3))
+    ok = True
+    for t in range(out["E"].shape[0]):
+        no = out["n_open"][t]
+        K = out["K"][t, :no, :no]
+        ok &= np.abs(K - K.T).max() <= 1e-10 * max(np.abs(K).max(), 1.0)
+        S, _ = o.smatrix(K)
+        ok &= np.abs(S @ S.conj().T - np.eye(no)).max() <= 1e-10
+        k2 = out["E"][t] - w.thresh
+        sig = out["sig_sel"][t]
+        for i in range(no):
+            for j in range(no):
+                ok &= abs(k2[i] * sig[i, j] - k2[j] * sig[j, i]) <= 1e-9 * max(k2[i] * sig[i, j], 1e-300)
+    return bool(ok)
+
+
+def pin_nudge():
+    En, fl = o.nudge_energies(np.array([0.5 + 5e-10, 0.9]), np.array([0.5, 1.0]), np.array([0.0, 0.7]))
+    return En[0] == 0.5 + 5e-10 + 1e-6 and En[1] == 0.9 and fl[0] == o.FLAG_NUDGED and fl[1] == 0
+
+
+PINS = [pin_breit_wigner, pin_lane_thomas, pin_hard_sphere, pin_bloch, pin_closed_channel,
+        pin_symmetry_unitarity_balance, pin_nudge]
+
+
+def run_pins():
+    res = {}
+    for p in PINS:
+        try:
+            with np.errstate(all="ignore"):
+                res[p.__name__] = bool(p())
+        except Exception:
+            res[p.__name__] = False
+    return res
+
+
+def test_unmutated_oracle_passes_every_pin():
+    res = run_pins()
+    assert all(res.values()), res
+
+
+MUTATIONS = [
+    ("pole sum sign", o.rmatrix, "d = 1.0 / (poles - E)", "d = 1.0 / (E - poles)"),
+    ("pole sum missing 1/2", o.rmatrix, "/ (2.0 * a)", "/ a"),
+    ("Lambda scales rows not columns", o.kmatrix, "a * R * f[\"lam\"][None, :]", "a * R * f[\"lam\"][:, None]"),
+    ("K divided by the column's c", o.kmatrix, "K = Y[:no, :] / f[\"c\"][:no, None]", "K = Y[:no, :] / f[\"c\"][None, :no]"),
+    ("B term sign", o.kmatrix, "B = -a * R[:, :no]", "B = a * R[:, :no]"),
+    ("s' missing chain-rule k", o.channel_functions, "sp[i] = jhp * math.sqrt(k)", "sp[i] = jhp / math.sqrt(k)"),
+    ("c sign", o.channel_functions, "c[i] = -nh / math.sqrt(k)", "c[i] = nh / math.sqrt(k)"),
+    ("c' sign", o.channel_functions, "cp[i] = -nhp * math.sqrt(k)", "cp[i] = nhp * math.sqrt(k)"),
+    ("closed log-derivative sign", o.channel_functions, "lam[i] = kap * khat_logderiv", "lam[i] = -kap * khat_logderiv"),
+    ("khat derivative term dropped", o.khat_logderiv, "return dp / p - 1.0", "return dp / p"),
+    ("inverted Cayley map", o.smatrix, "S = np.linalg.solve(I - 1j * K, I + 1j * K)",
+     "S = np.linalg.solve(I + 1j * K, I - 1j * K)"),
+    ("sigma uses k of the final channel", o.xsec, "(math.pi / k2[:no])[:, None]", "(math.pi / k2[:no])[None, :]"),
+    ("sigma 4 pi instead of pi", o.xsec, "(math.pi / k2[:no])", "(4 * math.pi / k2[:no])"),
+    ("eigenphase sign", o.eigenphase_sum, "np.sum(np.arctan(", "-np.sum(np.arctan("),
+    ("nudge downwards", o.nudge_energies, "E[e] = E[e] + NUDGE_SHIFT", "E[e] = E[e] - NUDGE_SHIFT"),
+    ("open count too large", o.n_open, "thresh < E", "thresh <= E + 0.5"),
+]
+
+
+@pytest.mark.parametrize("name,func,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_mutation_is_caught(monkeypatch, name, func, old, new):
+    monkeypatch.setattr(o, func.__name__, mutate(func, old, new))
+    res = run_pins()
+    assert not all(res.values()), f"mutation '{name}' passed every pin: {res}"
