@@ -98,8 +98,11 @@ typedef struct {
   const int32_t* sel_init; /* host array of selected initial channels; NULL = {0} */
   int32_t n_sel;           /* entries in sel_init (ignored when sel_init is NULL) */
   int32_t mem;             /* rm_mem_t of every input pointer (waves and energies) */
-  int32_t chunk;           /* energies per internal chunk; 0 = automatic */
-  int32_t autotune;        /* 1: time candidate energy-chunk sizes of rm_run at plan creation */
+  int32_t chunk;           /* energies per rm_run chunk; 0 = automatic: the whole mesh when its
+                              R-matrices fit min(24 GiB, a third of free device memory), else
+                              the largest multiple of 256 energies that does */
+  int32_t autotune;        /* 1: time chunk sizes 256, 512, ..., 8192 and the automatic one on
+                              the mesh's first energies at plan creation and keep the fastest */
   const char* tune_cache;  /* optional file caching autotuned choices (NULL = none) */
 } rm_options;
 

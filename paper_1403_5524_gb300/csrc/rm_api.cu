@@ -423,6 +423,9 @@ void cache_store(const char* path, const std::string& key, int chunk) {
 }
 
 rm_status_t autotune_chunk(Plan* p, const char* cache, int chunk_max) {
+  // Candidates 256, 512, ... up to 8192 (and chunk_max), timed on the first
+  // min(n_e, largest candidate) energies; when the largest candidate wins and
+  // the whole mesh fits, the sweep runs unchunked.
   GroupDev& G = p->grp;
   const std::string key = tune_key(p);
   int best = cache_lookup(cache, key);
@@ -430,14 +433,18 @@ rm_status_t autotune_chunk(Plan* p, const char* cache, int chunk_max) {
     G.chunk = best;
     return group_setup(p);
   }
-  const int64_t ne_t = p->n_e < chunk_max ? p->n_e : chunk_max;
+  const int c_top = chunk_max < 8192 ? chunk_max : 8192;
+  const int64_t ne_t = p->n_e < c_top ? p->n_e : c_top;
   cudaEvent_t a = nullptr, b = nullptr;
   RM_CUDA(cudaEventCreate(&a), "event");
   RM_CUDA(cudaEventCreate(&b), "event");
   double best_t = 1e300;
-  best = chunk_max;
+  best = c_top;
   const int64_t n_e_saved = p->n_e;
-  for (int c = 256; c <= chunk_max; c *= 2) {
+  std::vector<int> cands;
+  for (int c = 256; c < c_top; c *= 2) cands.push_back(c);
+  cands.push_back(c_top);
+  for (int c : cands) {
     G.chunk = c;
     rm_status_t st = group_setup(p);
     if (st != RM_OK) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
@@ -460,6 +467,7 @@ rm_status_t autotune_chunk(Plan* p, const char* cache, int chunk_max) {
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  if (best == c_top && chunk_max >= p->n_e) best = (int)p->n_e;
   G.chunk = best;
   rm_status_t st = group_setup(p);
   if (st == RM_OK) cache_store(cache, key, best);
@@ -612,15 +620,21 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if (st == RM_OK) st = dalloc(p, &p->asym, 4ll * chunk * n_max);
       if (st == RM_OK) st = dalloc(p, &p->slot, (int64_t)p->solve_slots * p->slot_doubles);
       if (st == RM_OK) st = dalloc(p, &p->err_word, 1);
-      // grouped-run chunk buffers (all waves at once), at most 2 GiB
+      // grouped-run buffers (all waves at once).  R for the whole mesh when it
+      // fits min(24 GiB, a third of free device memory): one launch per kernel
+      // and sweep, no chunk tails; otherwise chunks (autotuned when asked).
       int64_t per_e = 0;
       for (const auto& w : p->waves) per_e += (int64_t)w.n * (w.n + 1) / 2 + 4ll * w.n;
-      int64_t cmax = o.chunk > 0 ? o.chunk : ((2ll << 30) / (8 * per_e)) / 256 * 256;
-      if (o.chunk == 0) cmax = cmax < 256 ? 256 : (cmax > 2048 ? 2048 : cmax);
-      if (n_e > 0 && cmax > n_e) cmax = n_e;
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 2ull << 30; }
+      int64_t budget = (int64_t)(free_b / 3);
+      if (budget > (24ll << 30)) budget = 24ll << 30;
+      int64_t cmax = o.chunk > 0 ? o.chunk : budget / (8 * per_e);
+      if (o.chunk == 0 && cmax < n_e && cmax >= 256) cmax = cmax / 256 * 256;
       if (cmax < 1) cmax = 1;
-      grp_chunk_max = (int)cmax;
-      p->grp.chunk = o.chunk > 0 ? o.chunk : (int)(cmax < 1024 ? cmax : 1024);
+      if (n_e > 0 && cmax > n_e) cmax = n_e;
+      grp_chunk_max = (int)(cmax > (1 << 30) ? (1 << 30) : cmax);
+      p->grp.chunk = o.chunk > 0 ? o.chunk : grp_chunk_max;
       p->grp.R.assign(n_waves, nullptr);
       p->grp.asym.assign(n_waves, nullptr);
       for (int g = 0; g < n_waves && st == RM_OK; ++g) {

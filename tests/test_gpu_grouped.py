@@ -88,7 +88,8 @@ def test_autotune_and_cache(rm, tmp_path):
         p.run()
         o1 = rm.host_outputs(wl.n_e, 24, 1)
         p.results(0, 0, wl.n_e, **o1)
-    assert chunk in (256, 512, 1024) and os.path.exists(cache)
+    # candidates: powers of two from 256 below the mesh size, and the whole mesh
+    assert chunk in (256, 512, 1024, wl.n_e) and os.path.exists(cache)
     line = open(cache).read().strip().splitlines()[-1]
     assert line.endswith("|%d" % chunk)
     with rm.Plan(wl.waves, wl.energies, prec="split_bf16", delta=0.05, autotune=True, tune_cache=cache) as p:
