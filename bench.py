@@ -382,6 +382,7 @@ def run_ours(args):
                 "data": "synthetic (seeded, workload distributions of the paper's problem class)",
                 "config": {"workload": wl.name, "prec": args.prec, "mesh_stride": stride,
                            "energy_chunk": plan.info(0)["chunk"],
+                           "tc_cluster": "%dx%d" % plan.cluster(),
                            "energies_per_step": wl.n_e, "waves": len(wl.waves),
                            "n_ch": [w.n for w in wl.waves][:4], "n_poles": [w.N for w in wl.waves][:4],
                            "n_sel": len(sel), "l2": "flushed (512 MB write) between timed steps",

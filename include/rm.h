@@ -104,6 +104,12 @@ typedef struct {
   int32_t autotune;        /* 1: time chunk sizes 256, 512, ..., 8192 and the automatic one on
                               the mesh's first energies at plan creation and keep the fastest */
   const char* tune_cache;  /* optional file caching autotuned choices (NULL = none) */
+  int32_t cluster_x;       /* split modes, rm_run: CTAs per cluster sharing one energy tile
+                              (each forms 1/cluster_x of the D slices): 1, 2 or 4; 0 = automatic */
+  int32_t cluster_y;       /* CTAs per cluster sharing one pair tile (each forms 1/cluster_y of
+                              the P slices): 1, 2 or 4; 0 = automatic.  At most 8 CTAs per
+                              cluster; a shape the device cannot co-schedule is rejected with
+                              RM_ERR_ARG. */
 } rm_options;
 
 /* Fill *opt with defaults: FP64, delta 0.05, sel {0}, host inputs, auto chunk. */
@@ -164,6 +170,9 @@ rm_status_t rm_sync(rm_plan_t plan);
    workspace bytes.  Any output may be NULL. */
 rm_status_t rm_plan_info(rm_plan_t plan, int32_t wave, int32_t* n_ch, int32_t* n_poles,
                          int64_t* n_e, int32_t* n_sel, int32_t* chunk, int64_t* workspace_bytes);
+
+/* Cluster shape of rm_run's tensor-core pole-sum launch (1 x 1 outside split modes). */
+rm_status_t rm_plan_cluster(rm_plan_t plan, int32_t* cluster_x, int32_t* cluster_y);
 
 /* Number of kernel launches this plan has issued since creation. */
 int64_t rm_plan_launches(rm_plan_t plan);

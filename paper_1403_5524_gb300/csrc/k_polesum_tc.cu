@@ -17,9 +17,10 @@
 // all ten with u + v <= 3 and the three order-4 products (1,3), (2,2), (3,1)
 // that the four slices provide.  They go to four FP32 TMEM accumulators, one
 // per order (order 4 shares the order-3 one); orders 0-2 hold values on a
-// fixed grid, so their FP32 sums are exact while below 2^24 of that grid, and
-// the accumulators are drained into exact 64-bit fixed-point sums (unit
-// 2^-32) every 2048 poles.
+// fixed grid, so their FP32 sums are exact while below 2^24 of that grid.
+// Every 2048 poles the accumulators are drained into double-float running
+// sums (FP32 hi + lo) by error-free additions (TwoSum), on the FP32 pipe: the
+// sums keep about 48 bits, and the FP64 pipe stays out of the drain.
 //
 // Poles with |E_k - E_e| < delta are excluded from the GEMM by per-energy pole
 // index ranges [klo, khi) and summed in FP64 by the near-window kernel, so the
@@ -42,7 +43,7 @@ constexpr int BN = 128;                 // energies per tile
 constexpr int KS = 32;                  // poles per k-step (64-byte BF16 rows)
 constexpr int STAGES = 3;
 constexpr int NWORK = 16;               // producer / drain warps
-constexpr int NTHREADS = (NWORK + 1) * 32;
+constexpr int NTHREADS = (NWORK + 2) * 32;  // + MMA issue warp + cluster copy warp
 constexpr int DRAIN_KSTEPS = 64;        // drain every 2048 poles
 constexpr int SLICE_BYTES = BM * KS * 2;          // 8 KB: 128 rows x 64 B
 constexpr int A_BYTES = 4 * SLICE_BYTES;          // 4 slices of P
@@ -52,7 +53,7 @@ constexpr int WJ_FLOATS = 32 * KS;   // 16 channels x (hi, lo) rows
 constexpr int PO_FLOATS = 2 * KS;    // poles hi row, lo row
 constexpr int TX_BYTES = (WI_FLOATS + WJ_FLOATS + PO_FLOATS) * 4;  // 6400
 constexpr int STAGE_STRIDE = ((A_BYTES + B_BYTES + TX_BYTES + 1023) / 1024) * 1024;
-constexpr int NBARS = 3 * STAGES + 3;
+constexpr int NBARS = 4 * STAGES + 3;
 constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_STRIDE + 1024 + NBARS * 8 + 16;
 constexpr long long WAIT_BUDGET = 4000000000LL;   // clock cycles (~2 s)
 
@@ -99,6 +100,13 @@ __device__ __forceinline__ void df_recip_diff(float kh, float kl, float eh, floa
   rl = __fmul_rn(rh, c);
 }
 
+// s + e = a + b exactly (round to nearest, no overflow): Knuth's TwoSum
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
@@ -137,15 +145,34 @@ struct TCArgs {
 // One 128-pair x 128-energy output tile: pairs from i-block I0 (8 channels) and
 // j-block J0 (16 channels), energies n0 .. n0+127 of the chunk that starts at
 // absolute energy index g.e_begin and holds g.ne energies.
+//
+// Cluster sharing (CX x CY CTAs, rank = rx + CX ry): the CX CTAs of one
+// cluster row hold different pair tiles of one wave and the same energy tile,
+// the CY CTAs of one cluster column the same pair tile and different energy
+// tiles.  Each CTA forms 1/CX of the D slices (energy rows) and 1/CY of the P
+// slices (pair rows) of a k-step in its own stage buffer; once they are
+// written (barrier `gen`), a copy warp forwards those contiguous row blocks to
+// the same place in the stage buffers of the CTAs that share them, by bulk
+// copies into distributed shared memory that complete as transaction bytes on
+// the receivers' `full` barriers.  Slice formation per CTA thus shrinks to
+// 1/CX + 1/CY of a full tile while the MMAs stay local.  A stage is empty
+// when the MMAs of every CTA that it feeds are done (their commits are
+// multicast to the senders).
+template <int CX, int CY>
 __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUtensorMap* map_pol, const TCArgs& g,
                                         int I0, int J0, int n0, unsigned char* smem_raw) {
   using namespace ptx;
+  constexpr int CL = CX * CY;
+  static_assert(CX == 1 || CX == 2 || CX == 4, "CX in {1, 2, 4}");
+  static_assert(CY == 1 || CY == 2 || CY == 4, "CY in {1, 2, 4}");
+  static_assert(CX * CY <= 8, "portable cluster size");
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_STRIDE);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* wfull = bars + 2 * STAGES;
-  uint64_t* acc_full = bars + 3 * STAGES;
+  uint64_t* gen = bars + 3 * STAGES;
+  uint64_t* acc_full = bars + 4 * STAGES;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* done = acc_full + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBARS);
@@ -155,11 +182,22 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
   const int nK = g.nK;
   const int n = g.n;
 
+  // cluster position and the CTAs this one exchanges slices with (itself included)
+  uint32_t rank = 0;
+  if constexpr (CL > 1) rank = cluster_ctarank();
+  const int rx = (int)rank % CX, ry = (int)rank / CX;
+  uint32_t peer_mask = 0;
+#pragma unroll
+  for (int q = 0; q < CL; ++q)
+    if (q % CX == rx || q / CX == ry) peer_mask |= 1u << q;
+  constexpr int NPEERS = CX + CY - 1;
+
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full + s, NWORK);
-      mbar_init(empty + s, 1);
+      mbar_init(full + s, CL > 1 ? 1 : NWORK);  // clusters: the copy warp's arrive + incoming bytes
+      mbar_init(empty + s, NPEERS);
       mbar_init(wfull + s, 1);
+      mbar_init(gen + s, NWORK);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NWORK);
@@ -172,7 +210,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
     tmem_relinquish();
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (CL > 1) cluster_sync();  // peers' barriers are initialised before any remote arrive
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -201,7 +240,10 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       bool issued = false;
       for (int j = 0; j < nK; ++j) {
         const int s = j % STAGES;
-        if (!mbar_wait(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) { ok = false; break; }
+        bool got;
+        if constexpr (CL > 1) got = mbar_wait_cluster(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET);
+        else got = mbar_wait(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET);
+        if (!got) { ok = false; break; }
         if (j + STAGES < nK) issue_tma(s, j + STAGES);
         const int d = j / DRAIN_KSTEPS;
         const bool first = (j % DRAIN_KSTEPS) == 0;
@@ -228,8 +270,15 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 3 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 1 * SLICE_BYTES + ko), idN128, 1u);
         }
         issued = true;
-        mma_commit(empty + s);
+        if constexpr (CL > 1) mma_commit_mc(empty + s, (uint16_t)peer_mask);
+        else mma_commit(empty + s);
         if ((j + 1) % DRAIN_KSTEPS == 0 || j == nK - 1) mma_commit(acc_full);
+      }
+      if (ok && CL > 1) {
+        // every peer's commit for the last use of each stage has landed here, so no
+        // arrive can reach this CTA's barriers after it exits
+        for (int j = (nK > STAGES ? nK - STAGES : 0); j < nK; ++j)
+          if (!mbar_wait_cluster(empty + j % STAGES, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) break;
       }
       if (!ok) {
         // abort path: let in-flight TMA loads and MMAs finish before the CTA exits
@@ -249,24 +298,65 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       }
     }
     __syncwarp();
+  } else if (warp == NWORK + 1) {
+    // ------------------------------------- cluster copies (1 thread; CL > 1 only)
+    if (CL > 1 && lane == 0) {
+      constexpr uint32_t ABLK = SLICE_BYTES / CY, BBLK = SLICE_BYTES / CX;
+      constexpr uint32_t IN_BYTES = (CX - 1) * 4 * BBLK + (CY - 1) * 4 * ABLK;
+      const uint32_t sbase = smem_u32(smem);
+      for (int j = 0; j < nK; ++j) {
+        const int s = j % STAGES;
+        if (!mbar_wait(gen + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) break;
+        mbar_arrive_expect_tx(full + s, IN_BYTES);
+        const uint32_t st = sbase + (uint32_t)(s * STAGE_STRIDE);
+#pragma unroll
+        for (int q = 0; q < CX; ++q) {
+          if (q == rx) continue;
+          const uint32_t peer = (uint32_t)(q + CX * ry);
+          const uint32_t bar = mapa(smem_u32(full + s), peer);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const uint32_t src = st + A_BYTES + v * SLICE_BYTES + rx * BBLK;
+            bulk_copy_to_peer(mapa(src, peer), src, BBLK, bar);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < CY; ++q) {
+          if (q == ry) continue;
+          const uint32_t peer = (uint32_t)(rx + CX * q);
+          const uint32_t bar = mapa(smem_u32(full + s), peer);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t src = st + u * SLICE_BYTES + ry * ABLK;
+            bulk_copy_to_peer(mapa(src, peer), src, ABLK, bar);
+          }
+        }
+      }
+    }
+    __syncwarp();
   } else {
     // -------------------------------------------------- producers and drains
     const int w = warp;
     const bool f16 = g.f16 != 0;
-    // A role: i-row ai, j-rows jj = jbase + 2t (t = 0..3), k-pair kpa (all 16 k-pairs per
-    // half-warp); a half-warp reads one staged row contiguously and writes one full slice row.
-    const int ai = w >> 1, kpa = lane & 15, jbase = (w & 1) * 8 + (lane >> 4);
+    // A role (pair rows of i-blocks ry*8/CY .. +8/CY): i-row ai, j-rows
+    // jj = jbase + 2t, k-pair kpa; a half-warp writes one full slice row.
+    constexpr int TA = 4 / CY;   // j-rows per thread
+    const int ai = ry * (8 / CY) + w / (2 * CY);
+    const int kpa = lane & 15, jbase = (w % (2 * CY)) * (8 / CY) + (lane >> 4);
     const int gi = I0 + ai;
-    float mp[4];
+    float mp[TA];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < TA; ++t) {
       const int gj = J0 + jbase + 2 * t;
       mp[t] = (gi < n && gj < n && gi <= gj) ? g.mult_p[pair_index(n, gi, gj)] : 0.0f;
     }
-    // B role: energy row rb, k-pairs kpb + 4t
-    const int rb = w * 8 + (lane & 7), kpb = lane >> 3;
+    // B role (energy rows rx*128/CX .. +128/CX): row rb, k-pairs kpb + 4 (kq0 + t)
+    constexpr int RG = 16 / CX;  // 8-row groups formed by this CTA
+    constexpr int TB = 4 / CX;   // k-pair groups per thread
+    const int rb = rx * (128 / CX) + 8 * (w % RG) + (lane & 7), kpb = lane >> 3;
+    const int kq0 = (w / RG) * TB;
     const int eloc = n0 + rb;
-    float eh = 0.0f, el = 0.0f, me = 0.0f;
+    float eh = 1.0e30f, el = 0.0f, me = 0.0f;  // rows past the chunk: finite and zero
     int klo = 0, khi = 0;
     if (eloc < g.ne) {
       const int64_t ge = g.e_begin + eloc;
@@ -277,15 +367,21 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       khi = g.khi[ge];
     }
     const uint32_t trow = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(32 * (w >> 2));
-    long long V[32];
+    float Vh[32], Vl[32];  // running sums of this thread's 32 accumulator cells
 #pragma unroll
-    for (int c = 0; c < 32; ++c) V[c] = 0;
+    for (int c = 0; c < 32; ++c) Vh[c] = Vl[c] = 0.0f;
     bool ok = true;
     for (int j = 0; j < nK && ok; ++j) {
       const int s = j % STAGES;
-      if (j >= STAGES && !mbar_wait(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, WAIT_BUDGET)) {
-        ok = false;
-        break;
+      if (j >= STAGES) {
+        bool got;
+        if constexpr (CL > 1)
+          got = mbar_wait_cluster(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, WAIT_BUDGET);
+        else got = mbar_wait(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, WAIT_BUDGET);
+        if (!got) {
+          ok = false;
+          break;
+        }
       }
       if (!mbar_wait(wfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) {
         ok = false;
@@ -301,7 +397,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       const float2 wih = *reinterpret_cast<const float2*>(WI + (2 * ai) * KS + ka);
       const float2 wil = *reinterpret_cast<const float2*>(WI + (2 * ai + 1) * KS + ka);
 #pragma unroll 1
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < TA; ++t) {
         const int jj = jbase + 2 * t;
         const int k = ka;
         const float2 wjh = *reinterpret_cast<const float2*>(WJ + (2 * jj) * KS + k);
@@ -319,8 +415,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       }
       const int k0 = j * KS;
 #pragma unroll 1
-      for (int t = 0; t < 4; ++t) {
-        const int k = 2 * (kpb + 4 * t);
+      for (int t = 0; t < TB; ++t) {
+        const int k = 2 * (kpb + 4 * (kq0 + t));
         const int kg = k0 + k;
         const float2 ph = *reinterpret_cast<const float2*>(PO + k);
         const float2 pl = *reinterpret_cast<const float2*>(PO + KS + k);
@@ -338,9 +434,10 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         for (int v = 0; v < 4; ++v)
           *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + off) = pack_slice(s0[v], s1[v], f16);
       }
+      // the MMAs (and, in clusters, the bulk copies) read these slices through the async proxy
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(full + s);
+      if (lane == 0) mbar_arrive(CL > 1 ? gen + s : full + s);
       if ((j + 1) % DRAIN_KSTEPS == 0 || j == nK - 1) {
         const int d = j / DRAIN_KSTEPS;
         if (!mbar_wait(acc_full, (uint32_t)(d & 1), abort_flag, WAIT_BUDGET)) {
@@ -348,7 +445,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           break;
         }
         tc_fence_after();
-        // fixed point with unit 2^-32 (of the product of the two [-256, 256] scales)
+        // orders 0-2 by TwoSum into (hi, lo); the order-3 sum is of the size of lo
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
 #pragma unroll
@@ -357,8 +454,18 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
             tmem_ld16(trow + (uint32_t)(o * 128 + h * 16), r);
             tmem_wait_ld();
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-              V[h * 16 + c] += (long long)__float2ll_rn(__fmul_rn(__uint_as_float(r[c]), 4294967296.0f));
+            for (int c = 0; c < 16; ++c) {
+              const int i = h * 16 + c;
+              const float x = __uint_as_float(r[c]);
+              if (o < 3) {
+                float sh, se;
+                two_sum(Vh[i], x, sh, se);
+                Vh[i] = sh;
+                Vl[i] = __fadd_rn(Vl[i], se);
+              } else {
+                Vl[i] = __fadd_rn(Vl[i], x);
+              }
+            }
           }
         }
         tc_fence_before();
@@ -377,13 +484,14 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int e = n0 + 32 * (w >> 2) + c;
-          if (e < g.ne) g.R[(int64_t)e * np + p] = (double)V[c] * fp * g.tau[g.e_begin + e];
+          if (e < g.ne) g.R[(int64_t)e * np + p] = ((double)Vh[c] + (double)Vl[c]) * fp * g.tau[g.e_begin + e];
         }
       }
     }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (CL > 1) cluster_sync();  // no CTA leaves while a peer may still write to it
+  else __syncthreads();
   if (warp == NWORK) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
@@ -396,12 +504,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                       TCArgs g) {
   extern __shared__ unsigned char smem_raw[];
   const int2 tile = g.tiles[blockIdx.x];
-  tc_tile(&map_omega, &map_pol, g, tile.x * 8, tile.y * 16, blockIdx.y * BN, smem_raw);
+  tc_tile<1, 1>(&map_omega, &map_pol, g, tile.x * 8, tile.y * 16, blockIdx.y * BN, smem_raw);
 }
 
 // Every wave of a plan in one launch: tile list entries (wave, i-block, j-block),
 // per-wave arguments and TMA descriptors in global memory; the chunk's energy
-// range is shared by all waves.
+// range is shared by all waves.  Launched in clusters of CX x CY CTAs: the tile
+// list holds each wave's tiles padded to a multiple of CX, and grid.y is a
+// multiple of CY.
+template <int CX, int CY>
 __global__ void __launch_bounds__(NTHREADS, 1)
     polesum_tc_grouped_kernel(const TCArgs* __restrict__ waves, const CUtensorMap* __restrict__ maps,
                               const int4* __restrict__ tiles, int64_t e_begin, int ne) {
@@ -410,7 +521,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   TCArgs g = waves[t.x];
   g.e_begin = e_begin;
   g.ne = ne;
-  tc_tile(maps + 2 * t.x, maps + 2 * t.x + 1, g, t.y * 8, t.z * 16, blockIdx.y * BN, smem_raw);
+  tc_tile<CX, CY>(maps + 2 * t.x, maps + 2 * t.x + 1, g, t.y * 8, t.z * 16, blockIdx.y * BN, smem_raw);
 }
 
 // ------------------------------------------------------------ preparation
@@ -463,8 +574,7 @@ __global__ void prep_pol_kernel(const double* __restrict__ poles, int N, int Npa
 }
 
 // per pair: 2^e_p with max_k |fl(omega_i omega_j)| 2^e_p <= 1; mult_p = 2^(e_p+8),
-// f_p = sigma_i sigma_j 2^-e_p 2^-48 / (2a)  (2^-16 for the two 2^8 scales,
-// 2^-32 for the fixed-point unit of the drained sums)
+// f_p = sigma_i sigma_j 2^-e_p 2^-16 / (2a)  (2^-16 undoes the two 2^8 scales)
 __global__ void prep_pairs_kernel(const float* __restrict__ omega, const double* __restrict__ sigma, int n, int N,
                                   int Npad, double inv2a, float* __restrict__ mult_p, double* __restrict__ f_p) {
   const int64_t np = (int64_t)n * (n + 1) / 2;
@@ -493,7 +603,7 @@ __global__ void prep_pairs_kernel(const float* __restrict__ omega, const double*
       int ep = -ex;
       if (ep > 110) ep = 110;
       mult_p[p] = ldexpf(1.0f, ep + 8);
-      f_p[p] = ldexp(sigma[i] * sigma[j], -ep - 48) * inv2a;
+      f_p[p] = ldexp(sigma[i] * sigma[j], -ep - 16) * inv2a;
     }
   }
 }
@@ -737,6 +847,34 @@ cudaError_t launch_near(const Plan& p, const WaveDev& w, int64_t e0, int ne, dou
   return cudaGetLastError();
 }
 
+namespace {
+
+using GroupedFn = void (*)(const TCArgs*, const CUtensorMap*, const int4*, int64_t, int);
+
+GroupedFn grouped_fn(int cx, int cy) {
+  if (cx == 1 && cy == 1) return polesum_tc_grouped_kernel<1, 1>;
+  if (cx == 2 && cy == 1) return polesum_tc_grouped_kernel<2, 1>;
+  if (cx == 4 && cy == 1) return polesum_tc_grouped_kernel<4, 1>;
+  if (cx == 1 && cy == 2) return polesum_tc_grouped_kernel<1, 2>;
+  if (cx == 2 && cy == 2) return polesum_tc_grouped_kernel<2, 2>;
+  if (cx == 4 && cy == 2) return polesum_tc_grouped_kernel<4, 2>;
+  if (cx == 2 && cy == 4) return polesum_tc_grouped_kernel<2, 4>;
+  if (cx == 1 && cy == 4) return polesum_tc_grouped_kernel<1, 4>;
+  return nullptr;
+}
+
+cudaError_t set_tc_smem() {
+  const int shapes[8][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 2}, {2, 2}, {4, 2}, {2, 4}, {1, 4}};
+  for (const auto& sh : shapes) {
+    cudaError_t err = cudaFuncSetAttribute(grouped_fn(sh[0], sh[1]), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)TC_SMEM);
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t group_setup_split(Plan& p) {
   GroupDev& G = p.grp;
   const int W = p.n_waves;
@@ -769,11 +907,16 @@ cudaError_t group_setup_split(Plan& p) {
     tw[g] = a;
     maps[2 * g] = sd.map_omega;
     maps[2 * g + 1] = sd.map_pol;
-    for (const int2& t : split_tiles(w.n)) tiles.push_back(make_int4(g, t.x, t.y, w.Npad / KS));
+    const std::vector<int2> wt = split_tiles(w.n);
+    for (const int2& t : wt) tiles.push_back(make_int4(g, t.x, t.y, w.Npad / KS));
+    // pad to a multiple of the cluster width with empty tiles (i-block past the last channel)
+    for (size_t q = wt.size(); q % G.tc_cx != 0; ++q) tiles.push_back(make_int4(g, (w.n + 7) / 8, 0, w.Npad / KS));
     nw[g] = NearWave{w.W, w.poles, w.E, sd.klo, sd.khi, G.R[g], 1.0 / (2.0 * w.a), w.n, w.Npad};
     for (int e = 0; e < G.chunk; e += NEB) jobs.push_back(make_int2(g, e));
   }
-  // longest K loop first, so the last wave of CTAs holds the short tiles
+  // longest K loop first, so the last wave of CTAs holds the short tiles; the sort is
+  // stable and each wave's block is a multiple of the cluster width, so every
+  // cluster holds tiles of one wave
   std::stable_sort(tiles.begin(), tiles.end(), [](const int4& x, const int4& y) { return x.w > y.w; });
   int splits = (2 * p.sm_count + (int)jobs.size() - 1) / (int)jobs.size();
   G.near_splits = splits < 1 ? 1 : (splits > 64 ? 64 : splits);
@@ -808,20 +951,55 @@ cudaError_t group_setup_split(Plan& p) {
     return err;
   if ((err = cudaMemcpy(G.near_jobs, jobs.data(), sizeof(int2) * jobs.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
     return err;
-  if ((err = cudaFuncSetAttribute(polesum_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)TC_SMEM)) != cudaSuccess)
-    return err;
+  if ((err = set_tc_smem()) != cudaSuccess) return err;
   return cudaFuncSetAttribute(near_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)near_smem_bytes(p.n_max));
+}
+
+bool polesum_cluster_ok(int cx, int cy) {
+  GroupedFn fn = grouped_fn(cx, cy);
+  if (!fn) return false;
+  if (cx * cy == 1) return true;
+  if (set_tc_smem() != cudaSuccess) return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cx * 8, cy * 8, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = TC_SMEM;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cx;
+  attr[0].val.clusterDim.y = cy;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n > 0;
 }
 
 cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {
   if (ne <= 0) return cudaSuccess;
   const GroupDev& G = p.grp;
-  dim3 grid(G.n_tiles, (ne + BN - 1) / BN);
-  polesum_tc_grouped_kernel<<<grid, NTHREADS, TC_SMEM, s>>>(reinterpret_cast<const TCArgs*>(G.tc_waves), G.maps,
-                                                            G.tiles, e0, ne);
-  return cudaGetLastError();
+  GroupedFn fn = grouped_fn(G.tc_cx, G.tc_cy);
+  if (!fn) return cudaErrorInvalidValue;
+  const int ny = (ne + BN - 1) / BN;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G.n_tiles, (ny + G.tc_cy - 1) / G.tc_cy * G.tc_cy, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = TC_SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G.tc_cx;
+  attr[0].val.clusterDim.y = G.tc_cy;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (G.tc_cx * G.tc_cy > 1) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, fn, reinterpret_cast<const TCArgs*>(G.tc_waves), (const CUtensorMap*)G.maps,
+                            (const int4*)G.tiles, e0, ne);
 }
 
 cudaError_t launch_near_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {

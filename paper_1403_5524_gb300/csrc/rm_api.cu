@@ -12,6 +12,7 @@ using namespace rm;
 
 namespace {
 
+
 thread_local std::string g_err;
 
 rm_status_t fail(rm_status_t s, const std::string& msg) {
@@ -388,89 +389,140 @@ rm_status_t build_graph(Plan* p) {
   return RM_OK;
 }
 
-// Energy-chunk size of the grouped run: time each candidate on the first
-// energies of the mesh and keep the fastest per energy; optional cache file
-// keyed by the plan's sizes.
+// Autotuned choices (energy chunk and tensor-core cluster shape) are cached in
+// an optional text file, one "key|chunk cluster_x cluster_y" line per plan
+// shape, keyed by the plan's sizes.
 std::string tune_key(const Plan* p) {
-  std::string k = "rm1 prec=" + std::to_string(p->prec) + " ne=" + std::to_string(p->n_e) +
+  std::string k = "rm2 prec=" + std::to_string(p->prec) + " ne=" + std::to_string(p->n_e) +
                   " sel=" + std::to_string(p->n_sel);
   for (const auto& w : p->waves) k += " " + std::to_string(w.n) + "x" + std::to_string(w.N);
   return k;
 }
 
-int cache_lookup(const char* path, const std::string& key) {
-  if (!path) return 0;
+struct Tuned {
+  int chunk = 0, cx = 1, cy = 1;
+};
+
+bool cache_lookup(const char* path, const std::string& key, Tuned& t) {
+  if (!path) return false;
   FILE* f = fopen(path, "r");
-  if (!f) return 0;
+  if (!f) return false;
   char line[8192];
-  int found = 0;
+  bool found = false;
   while (fgets(line, sizeof(line), f)) {
     std::string l(line);
     const size_t bar = l.rfind('|');
-    if (bar == std::string::npos) continue;
-    if (l.substr(0, bar) == key) found = atoi(l.c_str() + bar + 1);
+    if (bar == std::string::npos || l.substr(0, bar) != key) continue;
+    Tuned v;
+    if (sscanf(l.c_str() + bar + 1, "%d %d %d", &v.chunk, &v.cx, &v.cy) == 3) {
+      t = v;
+      found = true;
+    }
   }
   fclose(f);
   return found;
 }
 
-void cache_store(const char* path, const std::string& key, int chunk) {
+void cache_store(const char* path, const std::string& key, const Tuned& t) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s|%d\n", key.c_str(), chunk);
+  fprintf(f, "%s|%d %d %d\n", key.c_str(), t.chunk, t.cx, t.cy);
   fclose(f);
 }
 
-rm_status_t autotune_chunk(Plan* p, const char* cache, int chunk_max) {
-  // Candidates 256, 512, ... up to 8192 (and chunk_max), timed on the first
-  // min(n_e, largest candidate) energies; when the largest candidate wins and
-  // the whole mesh fits, the sweep runs unchunked.
+// Device time of one grouped pass over the first ne_t energies (after one
+// untimed pass), at the plan's current chunk and cluster shape.
+rm_status_t time_grouped(Plan* p, int64_t ne_t, cudaEvent_t a, cudaEvent_t b, float* ms) {
+  rm_status_t st = group_setup(p);
+  if (st != RM_OK) return st;
+  const int64_t n_e_saved = p->n_e;
+  p->n_e = ne_t;
+  st = enqueue_grouped(p, p->stream, false, nullptr, true);
+  if (st == RM_OK) {
+    cudaEventRecord(a, p->stream);
+    st = enqueue_grouped(p, p->stream, false, nullptr, true);
+    cudaEventRecord(b, p->stream);
+  }
+  p->n_e = n_e_saved;
+  if (st != RM_OK) return st;
+  RM_CUDA(cudaEventSynchronize(b), "autotune timing");
+  RM_CUDA(cudaEventElapsedTime(ms, a, b), "autotune timing");
+  return RM_OK;
+}
+
+// Tensor-core cluster shapes in order of preference (the automatic shape is the
+// first one the device co-schedules).
+constexpr int kShapes[][2] = {{2, 2}, {4, 1}, {2, 1}, {1, 2}, {1, 1}};
+
+rm_status_t autotune(Plan* p, const char* cache, int chunk_max, bool tune_chunk, bool tune_cluster) {
+  // 1. cluster shape: every co-schedulable shape, timed at min(chunk_max, 2048)
+  //    energies per chunk (or the caller's chunk);
+  // 2. chunk: 256, 512, ... up to 8192 (and chunk_max), timed on the first
+  //    min(n_e, largest candidate) energies; when the largest candidate wins and
+  //    the whole mesh fits, the sweep runs unchunked.
   GroupDev& G = p->grp;
   const std::string key = tune_key(p);
-  int best = cache_lookup(cache, key);
-  if (best > 0 && best <= chunk_max) {
-    G.chunk = best;
+  Tuned t;
+  if (cache_lookup(cache, key, t) && t.chunk > 0 && t.chunk <= chunk_max &&
+      (!tune_cluster || polesum_cluster_ok(t.cx, t.cy))) {
+    if (tune_chunk) G.chunk = t.chunk;
+    if (tune_cluster) {
+      G.tc_cx = t.cx;
+      G.tc_cy = t.cy;
+    }
     return group_setup(p);
   }
-  const int c_top = chunk_max < 8192 ? chunk_max : 8192;
-  const int64_t ne_t = p->n_e < c_top ? p->n_e : c_top;
   cudaEvent_t a = nullptr, b = nullptr;
   RM_CUDA(cudaEventCreate(&a), "event");
   RM_CUDA(cudaEventCreate(&b), "event");
-  double best_t = 1e300;
-  best = c_top;
-  const int64_t n_e_saved = p->n_e;
-  std::vector<int> cands;
-  for (int c = 256; c < c_top; c *= 2) cands.push_back(c);
-  cands.push_back(c_top);
-  for (int c : cands) {
-    G.chunk = c;
-    rm_status_t st = group_setup(p);
-    if (st != RM_OK) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
-    p->n_e = ne_t;  // time the first ne_t energies only
-    st = enqueue_grouped(p, p->stream, false, nullptr, true);
-    if (st == RM_OK) {
-      cudaEventRecord(a, p->stream);
-      st = enqueue_grouped(p, p->stream, false, nullptr, true);
-      cudaEventRecord(b, p->stream);
+  rm_status_t st = RM_OK;
+  if (tune_cluster) {
+    const int c0 = tune_chunk ? (chunk_max < 2048 ? chunk_max : 2048) : G.chunk;
+    const int64_t ne_t = p->n_e < c0 ? p->n_e : c0;
+    if (tune_chunk) G.chunk = c0;
+    double best_t = 1e300;
+    int bx = G.tc_cx, by = G.tc_cy;
+    for (const auto& sh : kShapes) {
+      if (!polesum_cluster_ok(sh[0], sh[1])) continue;
+      G.tc_cx = sh[0];
+      G.tc_cy = sh[1];
+      float ms = 0.f;
+      if ((st = time_grouped(p, ne_t, a, b, &ms)) != RM_OK) break;
+      if (ms < best_t) {
+        best_t = ms;
+        bx = sh[0];
+        by = sh[1];
+      }
     }
-    p->n_e = n_e_saved;
-    if (st != RM_OK) { cudaEventDestroy(a); cudaEventDestroy(b); return st; }
-    cudaEventSynchronize(b);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (ms < best_t * 0.97) {  // prefer the smaller chunk unless clearly slower
-      best_t = ms;
-      best = c;
+    G.tc_cx = bx;
+    G.tc_cy = by;
+  }
+  if (st == RM_OK && tune_chunk) {
+    const int c_top = chunk_max < 8192 ? chunk_max : 8192;
+    const int64_t ne_t = p->n_e < c_top ? p->n_e : c_top;
+    double best_t = 1e300;
+    int best = c_top;
+    std::vector<int> cands;
+    for (int c = 256; c < c_top; c *= 2) cands.push_back(c);
+    cands.push_back(c_top);
+    for (int c : cands) {
+      G.chunk = c;
+      float ms = 0.f;
+      if ((st = time_grouped(p, ne_t, a, b, &ms)) != RM_OK) break;
+      if (ms < best_t * 0.97) {  // prefer the smaller chunk unless clearly slower
+        best_t = ms;
+        best = c;
+      }
     }
+    if (best == c_top && chunk_max >= p->n_e) best = (int)p->n_e;
+    G.chunk = best;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  if (best == c_top && chunk_max >= p->n_e) best = (int)p->n_e;
-  G.chunk = best;
-  rm_status_t st = group_setup(p);
-  if (st == RM_OK) cache_store(cache, key, best);
+  if (st != RM_OK) return st;
+  st = group_setup(p);
+  if (st == RM_OK) cache_store(cache, key, Tuned{G.chunk, G.tc_cx, G.tc_cy});
   p->autotuned = true;
   return st;
 }
@@ -520,6 +572,10 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     if (o.prec < RM_PREC_FP64 || o.prec > RM_PREC_FP32_SIMT) return fail(RM_ERR_ARG, "bad precision mode");
     if (o.prec != RM_PREC_FP64 && !(o.delta > 0.0)) return fail(RM_ERR_ARG, "delta must be > 0");
     if (o.chunk < 0) return fail(RM_ERR_ARG, "chunk must be >= 0");
+    if (!(o.cluster_x == 0 || o.cluster_x == 1 || o.cluster_x == 2 || o.cluster_x == 4) ||
+        !(o.cluster_y == 0 || o.cluster_y == 1 || o.cluster_y == 2 || o.cluster_y == 4) ||
+        (o.cluster_x > 0 && o.cluster_y > 0 && o.cluster_x * o.cluster_y > 8))
+      return fail(RM_ERR_ARG, "cluster_x, cluster_y must be 0, 1, 2 or 4 with at most 8 CTAs per cluster");
     int n_sel = 1;
     int32_t sel[RM_MAX_SEL] = {0};
     if (o.sel_init) {
@@ -653,9 +709,33 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
         (polesum_tc_smem_bytes() > (size_t)prop.sharedMemPerBlockOptin ||
          near_smem_bytes(n_max) > (size_t)prop.sharedMemPerBlockOptin))
       st = fail(RM_ERR_ARG, "split-precision kernels do not fit this device's shared memory");
+    if (st == RM_OK && is_split_like(o.prec)) {
+      // explicit cluster shape (a missing dimension is 1); automatic: the first
+      // shape of the preference list that the device co-schedules
+      if (o.cluster_x > 0 || o.cluster_y > 0) {
+        p->grp.tc_cx = o.cluster_x > 0 ? o.cluster_x : 1;
+        p->grp.tc_cy = o.cluster_y > 0 ? o.cluster_y : 1;
+        if (!polesum_cluster_ok(p->grp.tc_cx, p->grp.tc_cy))
+          st = fail(RM_ERR_ARG, "cluster shape cannot be co-scheduled on this device");
+      } else {
+        p->grp.tc_cx = 1;
+        p->grp.tc_cy = 1;
+        for (const auto& sh : kShapes) {
+          if (polesum_cluster_ok(sh[0], sh[1])) {
+            p->grp.tc_cx = sh[0];
+            p->grp.tc_cy = sh[1];
+            break;
+          }
+        }
+        cudaGetLastError();
+      }
+    }
     if (st == RM_OK) st = prepare(p, waves, energies, o.mem);
-    if (st == RM_OK && o.autotune && o.chunk == 0 && n_e > 0 && grp_chunk_max >= 256)
-      st = autotune_chunk(p, o.tune_cache, grp_chunk_max);
+    if (st == RM_OK && o.autotune && n_e > 0) {
+      const bool tune_chunk = o.chunk == 0 && grp_chunk_max >= 256;
+      const bool tune_cluster = is_split_like(o.prec) && o.cluster_x == 0 && o.cluster_y == 0;
+      if (tune_chunk || tune_cluster) st = autotune(p, o.tune_cache, grp_chunk_max, tune_chunk, tune_cluster);
+    }
     if (st != RM_OK) {
       free_plan(p);
       return st;
@@ -851,6 +931,14 @@ rm_status_t rm_plan_info(rm_plan_t h, int32_t wave, int32_t* n_ch, int32_t* n_po
   if (n_sel) *n_sel = p->n_sel;
   if (chunk) *chunk = p->grp.chunk;
   if (workspace_bytes) *workspace_bytes = p->workspace_bytes;
+  return RM_OK;
+}
+
+rm_status_t rm_plan_cluster(rm_plan_t h, int32_t* cx, int32_t* cy) {
+  Plan* p = as_plan(h);
+  if (!p) return fail(RM_ERR_ARG, "null plan");
+  if (cx) *cx = p->grp.tc_cx;
+  if (cy) *cy = p->grp.tc_cy;
   return RM_OK;
 }
 

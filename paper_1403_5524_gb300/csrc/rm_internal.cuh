@@ -83,6 +83,7 @@ struct GroupDev {
   CUtensorMap* maps = nullptr;  // [2 * n_waves] TMA descriptors (omega, poles)
   int4* tiles = nullptr;      // (wave, i-block, j-block), longest K first
   int n_tiles = 0;
+  int tc_cx = 1, tc_cy = 1;   // tensor-core cluster shape (pair tiles x energy tiles)
   void* near_waves = nullptr;
   int2* near_jobs = nullptr;  // (wave, first energy of an 8-energy block)
   int n_near_jobs = 0;
@@ -179,6 +180,8 @@ cudaError_t group_setup_split(Plan& p);
 cudaError_t group_setup_asym(Plan& p);
 cudaError_t group_setup_solve(Plan& p);
 cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
+// clusters of this shape can be resident (grouped tensor-core kernel)
+bool polesum_cluster_ok(int cx, int cy);
 cudaError_t launch_near_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
 cudaError_t launch_asym_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
 cudaError_t launch_solve_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);

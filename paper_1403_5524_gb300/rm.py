@@ -38,7 +38,8 @@ class rm_wave(C.Structure):
 class rm_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("delta", C.c_double), ("slices", C.c_int32),
                 ("sel_init", C.c_void_p), ("n_sel", C.c_int32), ("mem", C.c_int32),
-                ("chunk", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p)]
+                ("chunk", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p),
+                ("cluster_x", C.c_int32), ("cluster_y", C.c_int32)]
 
 
 class RMError(RuntimeError):
@@ -72,6 +73,7 @@ def load_library(path: str = LIB_PATH):
     lib.rm_sync.argtypes = [P]
     lib.rm_plan_info.argtypes = [P, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
                                  C.POINTER(i32), C.POINTER(i64)]
+    lib.rm_plan_cluster.argtypes = [P, C.POINTER(i32), C.POINTER(i32)]
     lib.rm_plan_launches.argtypes = [P]
     lib.rm_plan_launches.restype = i64
     lib.rm_plan_destroy.argtypes = [P]
@@ -83,7 +85,7 @@ def load_library(path: str = LIB_PATH):
     lib.rm_last_error.restype = C.c_char_p
     for name in ["rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix", "rm_xsec", "rm_run",
                  "rm_results", "rm_sync", "rm_plan_info", "rm_plan_destroy", "rm_profile_enable",
-                 "rm_profile_read"]:
+                 "rm_profile_read", "rm_plan_cluster"]:
         getattr(lib, name).restype = C.c_int32
     _lib = lib
     return lib
@@ -119,7 +121,8 @@ class Plan:
 
     def __init__(self, waves: Sequence, energies, prec: str = "fp64", delta: float = 0.05,
                  sel: Sequence[int] = (0,), chunk: int = 0, slices: int = 0, stream=None,
-                 autotune: bool = False, tune_cache: Optional[str] = None):
+                 autotune: bool = False, tune_cache: Optional[str] = None,
+                 cluster: Optional[Sequence[int]] = None):
         self.lib = load_library()
         self._keep = []
         self.mem = RM_MEM_DEVICE if _is_dev(energies) else RM_MEM_HOST
@@ -137,6 +140,8 @@ class Plan:
         opt.autotune = 1 if autotune else 0
         self._tune_cache = tune_cache.encode() if tune_cache else None
         opt.tune_cache = self._tune_cache
+        if cluster is not None:
+            opt.cluster_x, opt.cluster_y = int(cluster[0]), int(cluster[1])
         h = C.c_void_p()
         self.n_e = int(energies.shape[0])
         self.n_waves = len(waves)
@@ -177,6 +182,12 @@ class Plan:
                                      C.byref(ch), C.byref(ws)))
         return {"n_ch": n.value, "n_poles": N.value, "n_e": ne.value, "n_sel": ns.value,
                 "chunk": ch.value, "workspace_bytes": ws.value}
+
+    def cluster(self):
+        """(cluster_x, cluster_y) of rm_run's tensor-core pole-sum launch."""
+        cx, cy = C.c_int32(), C.c_int32()
+        _check(self.lib.rm_plan_cluster(self.h, C.byref(cx), C.byref(cy)))
+        return int(cx.value), int(cy.value)
 
     def launches(self) -> int:
         return int(self.lib.rm_plan_launches(self.h))

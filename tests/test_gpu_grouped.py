@@ -85,16 +85,70 @@ def test_autotune_and_cache(rm, tmp_path):
     cache = str(tmp_path / "tune.txt")
     with rm.Plan(wl.waves, wl.energies, prec="split_bf16", delta=0.05, autotune=True, tune_cache=cache) as p:
         chunk = p.info(0)["chunk"]
+        shape = p.cluster()
         p.run()
         o1 = rm.host_outputs(wl.n_e, 24, 1)
         p.results(0, 0, wl.n_e, **o1)
     # candidates: powers of two from 256 below the mesh size, and the whole mesh
     assert chunk in (256, 512, 1024, wl.n_e) and os.path.exists(cache)
+    assert shape in [(2, 2), (4, 1), (2, 1), (1, 2), (1, 1)]
     line = open(cache).read().strip().splitlines()[-1]
-    assert line.endswith("|%d" % chunk)
+    assert line.endswith("|%d %d %d" % (chunk, shape[0], shape[1]))
     with rm.Plan(wl.waves, wl.energies, prec="split_bf16", delta=0.05, autotune=True, tune_cache=cache) as p:
-        assert p.info(0)["chunk"] == chunk
+        assert p.info(0)["chunk"] == chunk and p.cluster() == shape
         p.run()
         o2 = rm.host_outputs(wl.n_e, 24, 1)
         p.results(0, 0, wl.n_e, **o2)
     assert np.array_equal(o1["sig_sel"], o2["sig_sel"])
+
+
+CLUSTERS = [(1, 1), (2, 1), (4, 1), (1, 2), (2, 2), (1, 4), (4, 2), (2, 4)]
+
+
+@pytest.fixture(scope="module")
+def cluster_case(rm):
+    # uneven waves (odd tile counts per wave, so clusters need padding), a mesh
+    # that is not a multiple of 128 energies, two selected channels
+    waves = [synth.small(500 + g, n, 40 * n, 1, pole_lo=-3, pole_hi=12, a=20.0).waves[0]
+             for g, n in enumerate([5, 23, 9, 40, 17])]
+    E = np.linspace(0.04, 3.3, 333)
+    sel = (0, 1)
+    with rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, chunk=200, cluster=(1, 1)) as p:
+        assert p.cluster() == (1, 1)
+        p.run()
+        base = []
+        for g, w in enumerate(waves):
+            o = rm.host_outputs(E.size, w.n, 2)
+            p.results(g, 0, E.size, **o)
+            base.append(o)
+    return waves, E, sel, base
+
+
+@pytest.mark.parametrize("shape", CLUSTERS, ids=["%dx%d" % c for c in CLUSTERS])
+def test_cluster_shapes_identical(rm, cluster_case, shape):
+    # every CTA forms the same slices whichever CTA of a cluster stores them, so
+    # the sums (and everything after them) are bit-identical across cluster shapes
+    waves, E, sel, base = cluster_case
+    try:
+        p = rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, chunk=200, cluster=shape)
+    except rm.RMError as ex:
+        pytest.skip(f"cluster shape {shape} not co-schedulable here: {ex}")
+    with p:
+        assert p.cluster() == shape
+        p.run()
+        for g, w in enumerate(waves):
+            o = rm.host_outputs(E.size, w.n, 2)
+            p.results(g, 0, E.size, **o)
+            for k in ("eigsum", "sig_tot", "sig_sel", "n_open", "flags"):
+                assert np.array_equal(o[k], base[g][k]), (shape, g, k)
+    # and against the oracle on sampled energies
+    for g, w in enumerate(waves):
+        idx = np.array([3 + 31 * g, 332 - 17 * g])
+        ref = orc.sweep(w, E, sel=sel, energy_idx=idx, keep_R=False, keep_K=False)
+        for t, e in enumerate(idx):
+            if ref["flags"][t] & orc.FLAG_ILLCOND:
+                continue
+            for q in range(2):
+                st = ref["sig_tot"][t, q]
+                if st > 0:
+                    assert np.abs(base[g]["sig_sel"][e, q] - ref["sig_sel"][t, q]).max() / st <= 1e-8
