@@ -19,7 +19,9 @@
 // (row interchanges, triangular solve with the unit-lower panel block, then
 // the rank-16 update).  Each matrix lives in a per-CTA global workspace slot
 // that stays in L2 while the CTA works on it.  GB300 retires about two FP64
-// FMAs per clock per SM, so one 256-thread CTA per SM saturates the FP64 pipe.
+// FMAs per clock per SM; two 256-thread CTAs share an SM where their shared
+// memory fits (n_ch up to about 280), so that one CTA's barriers and load
+// latencies are covered by the other's FMAs.
 #include <algorithm>
 #include <vector>
 
@@ -469,7 +471,7 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   }
 }
 
-__global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
+__global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Red red;
   __shared__ double s_acc;
@@ -479,7 +481,7 @@ __global__ void __launch_bounds__(NT, 1) solve_kernel(SolveArgs g) {
 // All waves of a plan: persistent CTAs claim (wave, chunk energy) units from a
 // list sorted by decreasing cost through an atomic counter.  Per-wave
 // arguments hold base pointers; the chunk offset e_begin is applied here.
-__global__ void __launch_bounds__(NT, 1) solve_grouped_kernel(const SolveArgs* __restrict__ waves,
+__global__ void __launch_bounds__(NT, 2) solve_grouped_kernel(const SolveArgs* __restrict__ waves,
                                                               const int2* __restrict__ units, int n_units,
                                                               int64_t e_begin, int ne, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -514,6 +516,19 @@ __global__ void __launch_bounds__(NT, 1) solve_grouped_kernel(const SolveArgs* _
 size_t solve_smem_bytes(int n_max) {
   return (size_t)n_max * NB * sizeof(cplx) + 2 * (size_t)NB * TC * sizeof(cplx) + (size_t)NB * NB * sizeof(cplx) +
          (size_t)n_max * sizeof(int) + 16;
+}
+
+// Resident solve CTAs per SM at this n_max (two when their shared memory fits:
+// one CTA's barrier and load bubbles are then filled by the other's FMAs).
+int solve_blocks_per_sm(int n_max) {
+  const int smem = (int)solve_smem_bytes(n_max);
+  int b = 0;
+  if (cudaFuncSetAttribute(solve_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, solve_grouped_kernel, NT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return b < 1 ? 1 : (b > 2 ? 2 : b);
 }
 
 int64_t solve_slot_doubles(int n_max, int n_sel) {

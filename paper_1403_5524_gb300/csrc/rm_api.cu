@@ -668,7 +668,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if (n_e > 0 && chunk > n_e) chunk = (int)n_e;
       if (chunk < 1) chunk = 1;
       p->chunk = chunk;
-      p->solve_slots = p->sm_count;
+      p->solve_slots = p->sm_count * solve_blocks_per_sm(n_max);
       p->slot_doubles = solve_slot_doubles(n_max, n_sel);
       if (st == RM_OK) st = dalloc(p, &p->energies, n_e);
       if (st == RM_OK) st = dalloc(p, &p->sel_dev, n_sel);

@@ -161,6 +161,7 @@ struct SolveOut {
 cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, const double* R,
                          const double* asym, int ld_chunk, const SolveOut& out, cudaStream_t s);
 size_t solve_smem_bytes(int n_max);
+int solve_blocks_per_sm(int n_max);
 int64_t solve_slot_doubles(int n_max, int n_sel);
 
 // split-precision pole sum
