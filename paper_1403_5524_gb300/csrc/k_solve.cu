@@ -31,8 +31,8 @@ namespace rm {
 
 namespace {
 
-constexpr int NB = 16;   // panel width
 constexpr int TC = 64;   // column tile of the trailing update
+constexpr int PANEL_ROW_BYTES = 128;  // one panel row: 16 doubles or 8 complex values
 constexpr int NT = 256;  // threads per CTA
 constexpr int NWARP = NT / 32;
 
@@ -73,6 +73,18 @@ struct Ops<cplx> {
   }
 };
 
+// Panel width: 16 columns for the real LU, 8 for the complex one, so that a
+// panel row is 128 bytes either way and both LUs do the same FMAs per byte of
+// trailing-matrix traffic (16 real or 8 complex multiply-adds per element).
+template <typename T>
+struct Blk {
+  static constexpr int NB = (int)(PANEL_ROW_BYTES / sizeof(T));
+};
+
+constexpr int TILE_BYTES = Blk<double>::NB * TC * 8;  // NB x TC elements, either type
+constexpr int TRI_BYTES = Blk<double>::NB * Blk<double>::NB * 8;  // the larger of the two
+static_assert(Blk<cplx>::NB * TC * (int)sizeof(cplx) == TILE_BYTES, "tile bytes");
+
 // smallest power of two >= min(TC, w), at least 1
 __device__ __forceinline__ int tile_width_pow2(int w) {
   w = w < TC ? w : TC;
@@ -96,6 +108,7 @@ struct Red {
 // Block-wide argmax of Ops::mag over panel column j, rows [j, rows); ties -> smallest row.
 template <typename T>
 __device__ int panel_argmax(const T* panel, int rows, int j, Red* red) {
+  constexpr int NB = Blk<T>::NB;
   double best = -1.0;
   int bidx = rows;
   for (int r = j + threadIdx.x; r < rows; r += NT) {
@@ -124,7 +137,8 @@ __device__ int panel_argmax(const T* panel, int rows, int j, Red* red) {
 
 // LU with partial pivoting of the leading n x n block of A (row-major, ld),
 // row operations applied to all m columns, then back substitution on
-// columns [n, m).  smem: panel[n_max*NB], tile[NB*TC], ipiv[n_max].
+// columns [n, m).  smem: panel[n_max*NB], tile[NB*TC], tmp[NB*TC], tri[NB*NB],
+// ipiv[n_max], with NB = Blk<T>::NB.
 // A[r][col] -= sum_j L[r][j] * U[j] for rows r = r0, r0 + 4, ... < r1, where L[r][j] is
 // panel row r (NB wide) and U[j] = tile[j * TC]; four rows per iteration so that
 // four independent loads are in flight, the tile column held in registers.
@@ -132,6 +146,7 @@ template <typename T>
 __device__ __forceinline__ void rank_update(T* __restrict__ A, int ld, int col, int r0, int r1, const T* panel,
                                             const T* tile, int nb, int RS) {
   using O = Ops<T>;
+  constexpr int NB = Blk<T>::NB;
   T u[NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) u[j] = (j < nb) ? tile[j * TC] : O::zero();
@@ -167,6 +182,7 @@ template <typename T>
 __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* tile, T* tmp, T* tri,
                          int* ipiv, Red* red, LUStat& st) {
   using O = Ops<T>;
+  constexpr int NB = Blk<T>::NB;
   const int t = threadIdx.x;
   st.pmin = INFINITY;
   st.pmax = 0.0;
@@ -333,13 +349,18 @@ struct SolveArgs {
 // asymptotic data, LU -> K, then (optionally) the complex S-step.
 __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw, Red& red, double& s_acc) {
   const int n = g.n;
-  cplx* panel_c = reinterpret_cast<cplx*>(smem_raw);
-  cplx* tile_c = panel_c + (size_t)n * NB;
-  cplx* tmp_c = tile_c + NB * TC;
-  cplx* tri_c = tmp_c + NB * TC;
-  int* ipiv = reinterpret_cast<int*>(tri_c + NB * NB);
-  double* panel_d = reinterpret_cast<double*>(panel_c);
-  double* tile_d = reinterpret_cast<double*>(tile_c);
+  // shared by both LUs: panel n x 128 B, tile and tmp 8 KB each, tri 2 KB, ipiv
+  unsigned char* panel_b = smem_raw;
+  unsigned char* tile_b = panel_b + (size_t)n * PANEL_ROW_BYTES;
+  unsigned char* tmp_b = tile_b + TILE_BYTES;
+  unsigned char* tri_b = tmp_b + TILE_BYTES;
+  int* ipiv = reinterpret_cast<int*>(tri_b + TRI_BYTES);
+  cplx* panel_c = reinterpret_cast<cplx*>(panel_b);
+  cplx* tile_c = reinterpret_cast<cplx*>(tile_b);
+  cplx* tmp_c = reinterpret_cast<cplx*>(tmp_b);
+  cplx* tri_c = reinterpret_cast<cplx*>(tri_b);
+  double* panel_d = reinterpret_cast<double*>(panel_b);
+  double* tile_d = reinterpret_cast<double*>(tile_b);
   double* A = g.slot + (int64_t)blockIdx.x * g.slot_doubles;
   cplx* C = reinterpret_cast<cplx*>(A + (int64_t)n * g.ldR);
   const int64_t np = (int64_t)n * (n + 1) / 2;
@@ -462,11 +483,13 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-    if (t == 0) s_acc = 0.0;
+    if ((t & 31) == 0) red.v[t >> 5] = part;
     __syncthreads();
-    if ((t & 31) == 0) atomicAdd(&s_acc, part);
-    __syncthreads();
-    if (t == 0 && g.out.sig_tot) g.out.sig_tot[(int64_t)e * r + q] = s_acc;
+    if (t == 0) {
+      double tot = 0.0;  // fixed order: the same bits on every run
+      for (int w = 0; w < NWARP; ++w) tot += red.v[w];
+      if (g.out.sig_tot) g.out.sig_tot[(int64_t)e * r + q] = tot;
+    }
     __syncthreads();
   }
 }
@@ -514,8 +537,7 @@ __global__ void __launch_bounds__(NT, 2) solve_grouped_kernel(const SolveArgs* _
 }  // namespace
 
 size_t solve_smem_bytes(int n_max) {
-  return (size_t)n_max * NB * sizeof(cplx) + 2 * (size_t)NB * TC * sizeof(cplx) + (size_t)NB * NB * sizeof(cplx) +
-         (size_t)n_max * sizeof(int) + 16;
+  return (size_t)n_max * PANEL_ROW_BYTES + 2 * (size_t)TILE_BYTES + TRI_BYTES + (size_t)n_max * sizeof(int) + 16;
 }
 
 // Resident solve CTAs per SM at this n_max (two when their shared memory fits:
