@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--stride", type=int, default=0,
                     help="use every stride-th energy of the mesh (0 = automatic)")
     ap.add_argument("--sel", type=int, default=1, help="number of selected initial channels")
+    ap.add_argument("--chunk", type=int, default=0, help="energies per rm_run chunk (0: automatic)")
+    ap.add_argument("--cluster", default="", help="tensor-core cluster shape CXxCY (default: autotuned)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -235,7 +237,9 @@ def run_ours(args):
                          poles=torch.from_numpy(w.poles).to(dev), W=torch.from_numpy(w.W).to(dev), a=w.a)
               for w in wl.waves]
     dE = torch.from_numpy(wl.energies).to(dev)
-    plan = rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream, autotune=True)
+    cluster = tuple(int(x) for x in args.cluster.split("x")) if args.cluster else None
+    plan = rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream, autotune=True,
+                   chunk=args.chunk, cluster=cluster)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
     def barrier():

@@ -101,8 +101,10 @@ typedef struct {
   int32_t chunk;           /* energies per rm_run chunk; 0 = automatic: the whole mesh when its
                               R-matrices fit min(24 GiB, a third of free device memory), else
                               the largest multiple of 256 energies that does */
-  int32_t autotune;        /* 1: time chunk sizes 256, 512, ..., 8192 and the automatic one on
-                              the mesh's first energies at plan creation and keep the fastest */
+  int32_t autotune;        /* 1: at plan creation, time the tensor-core cluster shapes (split
+                              modes, unless cluster_x/y are given) and, when the mesh does not
+                              fit one chunk, chunk sizes 256 .. 8192 on the mesh's first
+                              energies; keep the fastest */
   const char* tune_cache;  /* optional file caching autotuned choices (NULL = none) */
   int32_t cluster_x;       /* split modes, rm_run: CTAs per cluster sharing one energy tile
                               (each forms 1/cluster_x of the D slices): 1, 2 or 4; 0 = automatic */

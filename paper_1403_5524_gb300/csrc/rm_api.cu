@@ -456,11 +456,11 @@ rm_status_t time_grouped(Plan* p, int64_t ne_t, cudaEvent_t a, cudaEvent_t b, fl
 constexpr int kShapes[][2] = {{2, 2}, {4, 1}, {2, 1}, {1, 2}, {1, 1}};
 
 rm_status_t autotune(Plan* p, const char* cache, int chunk_max, bool tune_chunk, bool tune_cluster) {
-  // 1. cluster shape: every co-schedulable shape, timed at min(chunk_max, 2048)
-  //    energies per chunk (or the caller's chunk);
-  // 2. chunk: 256, 512, ... up to 8192 (and chunk_max), timed on the first
-  //    min(n_e, largest candidate) energies; when the largest candidate wins and
-  //    the whole mesh fits, the sweep runs unchunked.
+  // 1. cluster shape: every co-schedulable shape, timed on the first
+  //    min(n_e, chunk, 4096) energies (chunk: 2048 when it is tuned next);
+  // 2. chunk (only when the mesh does not fit one chunk): 256, 512, ... up to
+  //    8192 (and chunk_max), timed on the first min(n_e, largest candidate)
+  //    energies; a smaller chunk must win by 3%.
   GroupDev& G = p->grp;
   const std::string key = tune_key(p);
   Tuned t;
@@ -479,7 +479,8 @@ rm_status_t autotune(Plan* p, const char* cache, int chunk_max, bool tune_chunk,
   rm_status_t st = RM_OK;
   if (tune_cluster) {
     const int c0 = tune_chunk ? (chunk_max < 2048 ? chunk_max : 2048) : G.chunk;
-    const int64_t ne_t = p->n_e < c0 ? p->n_e : c0;
+    int64_t ne_t = p->n_e < c0 ? p->n_e : c0;
+    if (ne_t > 4096) ne_t = 4096;  // the first 4096 energies are enough to rank the shapes
     if (tune_chunk) G.chunk = c0;
     double best_t = 1e300;
     int bx = G.tc_cx, by = G.tc_cy;
@@ -504,18 +505,18 @@ rm_status_t autotune(Plan* p, const char* cache, int chunk_max, bool tune_chunk,
     double best_t = 1e300;
     int best = c_top;
     std::vector<int> cands;
-    for (int c = 256; c < c_top; c *= 2) cands.push_back(c);
     cands.push_back(c_top);
+    for (int c = 1 << 30; c >= 256; c >>= 1)
+      if (c < c_top) cands.push_back(c);  // descending
     for (int c : cands) {
       G.chunk = c;
       float ms = 0.f;
       if ((st = time_grouped(p, ne_t, a, b, &ms)) != RM_OK) break;
-      if (ms < best_t * 0.97) {  // prefer the smaller chunk unless clearly slower
+      if (ms < best_t * 0.97) {  // a smaller chunk must be clearly faster
         best_t = ms;
         best = c;
       }
     }
-    if (best == c_top && chunk_max >= p->n_e) best = (int)p->n_e;
     G.chunk = best;
   }
   cudaEventDestroy(a);
@@ -732,7 +733,9 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     }
     if (st == RM_OK) st = prepare(p, waves, energies, o.mem);
     if (st == RM_OK && o.autotune && n_e > 0) {
-      const bool tune_chunk = o.chunk == 0 && grp_chunk_max >= 256;
+      // a whole-mesh chunk (when it fits) has the fewest launches and the shortest
+      // solve tail, so the chunk is tuned only when the mesh must be split
+      const bool tune_chunk = o.chunk == 0 && grp_chunk_max >= 256 && grp_chunk_max < n_e;
       const bool tune_cluster = is_split_like(o.prec) && o.cluster_x == 0 && o.cluster_y == 0;
       if (tune_chunk || tune_cluster) st = autotune(p, o.tune_cache, grp_chunk_max, tune_chunk, tune_cluster);
     }
