@@ -31,6 +31,10 @@ from paper_1403_5524_gb300 import synth  # noqa: E402
 METRIC = "energies/sec (R+K+σ) split-precision vs FP64 GPU at n_ch=256; max rel err"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU
 SPLIT_PRODUCTS = 13      # BF16 slice products per far term in the tensor-core pole sum
+# DRAM bytes (read + write) per energy from one ncu capture each, n_ch=256 / N=20000 wave,
+# 1000-energy launch (profiles/solve_grouped_kernel_n256_1000E.md,
+# profiles/polesum_tc_grouped_2x2_n256_1000E.md); scaled to a launch by its energies.
+DRAM_BYTES_PER_ENERGY_N256 = {"solve": 30.348e6, "polesum_split": 0.4638e6}
 
 
 def measured_peaks():
@@ -293,6 +297,15 @@ def run_ours(args):
         if k in flops_per_step:
             kern[k]["tflops_algorithmic"] = flops_per_step[k] * args.steps / (kern[k]["ms_total"] / 1000.0) / 1e12
     peaks = measured_peaks()
+    single_n256 = len(wl.waves) == 1 and wl.waves[0].n == 256 and wl.waves[0].N == 20000
+
+    def traffic(kernel):
+        # per-launch DRAM bytes, scaled from the capture (same kernel code, same wave shape)
+        if not single_n256 or kernel not in DRAM_BYTES_PER_ENERGY_N256:
+            return None
+        e_per_launch = wl.n_e * args.steps / kern[kernel]["launches"]
+        return DRAM_BYTES_PER_ENERGY_N256[kernel] * e_per_launch
+
     roof = None
     if dom in flops_per_step:
         total_fl = flops_per_step[dom] * args.steps
@@ -300,7 +313,7 @@ def run_ours(args):
         avg_ms = kern[dom]["ms_total"] / n_l
         achieved = (total_fl / n_l) / (avg_ms / 1000.0) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic(dom),
                 "peak_source": "FP64 pipe: nominal 1.25 TFLOP/s (a DFMA probe measured 1.2)",
                 "flops_per_launch": total_fl / n_l, "avg_launch_ms": avg_ms}
     roof_tc = None
@@ -312,7 +325,7 @@ def run_ours(args):
         achieved = (hw / n_l) / (avg_ms / 1000.0) / 1e12
         pk = peaks.get("bf16_tflops_sustained") or 1700.0
         roof_tc = {"kernel": "polesum_split", "bound": "tensor", "achieved": achieved, "peak": pk,
-                   "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None,
+                   "unit": "TFLOP/s", "frac": achieved / pk, "traffic": traffic("polesum_split"),
                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks
                    else "fallback 1.7 PFLOP/s sustained",
                    "flops_per_launch": hw / n_l, "avg_launch_ms": avg_ms,
