@@ -20,6 +20,13 @@ in bohr, k^2 = E - e_i):
    c_i = -k^-1/2 nhat_l(kr) (Riccati-Bessel, nhat_l = x y_l(x) ~ -cos(x - l pi/2)),
    so that every open channel has Wronskian s c' - s' c = -1; closed channels
    decay as khat_l(kappa r), kappa = sqrt(e_i - E).
+3'. Ionic targets (residual charge z > 0, potential -2z/r in Rydberg units;
+   the paper's targets are ions but it gives no outer-region formulas, so this
+   is the standard Coulomb reading): open channels use the Coulomb functions
+   F_l(eta, kr), G_l(eta, kr) with eta = -z/k in place of jhat_l and -nhat_l
+   (s = k^-1/2 F, c = k^-1/2 G; z = 0 gives back item 3), closed channels decay
+   as the Whittaker function W_{z/kappa, l+1/2}(2 kappa r).  Both come from
+   mpmath (30 digits); derivatives from the standard recurrence relations.
 4. Matching with Bloch constant b = 0, F(a) = a R F'(a), F_ij ~ s_i d_ij + c_i K_ij
    (open i), F_ij ~ e_i(r) x_ij (closed i).  Column j of the matching matrix is
    divided by c_j (open) or e_j (closed); the system becomes
@@ -171,8 +178,44 @@ def khat_logderiv(l, x):
     return dp / p - 1.0
 
 
-def channel_functions(l, thresh, E, a):
-    """Per-channel matching data at energy E.
+def coulomb_open(l, eta, rho):
+    """Coulomb functions F_l(eta, rho), G_l(eta, rho) and their rho-derivatives.
+
+    Values from mpmath (coulombf / coulombg, 30 significant digits).  The
+    derivatives follow from the relation between orders l and l + 1,
+    (l+1) u_l' = ((l+1)^2 / rho + eta) u_l - sqrt((l+1)^2 + eta^2) u_{l+1}
+    for u = F or G (Abramowitz & Stegun 14.2.1).
+    """
+    import mpmath as mp
+    with mp.workdps(30):
+        r = mp.mpf(rho)
+        e = mp.mpf(eta)
+        L = l + 1
+        c1 = (L * L / r + e) / L
+        c2 = mp.sqrt(L * L + e * e) / L
+        F, F1 = mp.coulombf(l, e, r), mp.coulombf(l + 1, e, r)
+        G, G1 = mp.coulombg(l, e, r), mp.coulombg(l + 1, e, r)
+        return float(F), float(c1 * F - c2 * F1), float(G), float(c1 * G - c2 * G1)
+
+
+def whittaker_logderiv(l, kp, x):
+    """W'(x) / W(x) for the decaying Whittaker function W_{kp, l+1/2}(x).
+
+    Values from mpmath (whitw, 30 digits); the derivative from
+    x W'_{k,m}(x) = (x/2 - k) W_{k,m}(x) - W_{k+1,m}(x).
+    """
+    import mpmath as mp
+    with mp.workdps(30):
+        xx = mp.mpf(x)
+        k = mp.mpf(kp)
+        m = mp.mpf(l) + mp.mpf(1) / 2
+        W0 = mp.whitw(k, m, xx)
+        W1 = mp.whitw(k + 1, m, xx)
+        return float(((xx / 2 - k) * W0 - W1) / (xx * W0))
+
+
+def channel_functions(l, thresh, E, a, z=0.0):
+    """Per-channel matching data at energy E (residual target charge z >= 0).
 
     Returns dict with n_o, k2 (E - e_i), and for open channels s, s', c, c'
     (r-derivatives); for every channel the scaled log-derivative Lambda used as
@@ -184,6 +227,19 @@ def channel_functions(l, thresh, E, a):
     s = np.zeros(n); sp = np.zeros(n); c = np.zeros(n); cp = np.zeros(n)
     lam = np.zeros(n)
     for i in range(n):
+        if z != 0.0:
+            if k2[i] > 0.0:
+                k = math.sqrt(k2[i])
+                F, Fp, G, Gp = coulomb_open(int(l[i]), -z / k, k * a)
+                s[i] = F / math.sqrt(k)
+                sp[i] = Fp * math.sqrt(k)
+                c[i] = G / math.sqrt(k)
+                cp[i] = Gp * math.sqrt(k)
+                lam[i] = cp[i] / c[i]
+            else:
+                kap = math.sqrt(-k2[i])
+                lam[i] = 2.0 * kap * whittaker_logderiv(int(l[i]), z / kap, 2.0 * kap * a)
+            continue
         if k2[i] > 0.0:
             k = math.sqrt(k2[i])
             x = k * a
@@ -203,14 +259,15 @@ def channel_functions(l, thresh, E, a):
 # ----------------------------------------------------------------------------
 # matching -> K, then S, eigenphase sum, cross sections
 # ----------------------------------------------------------------------------
-def kmatrix(R, l, thresh, E, a):
+def kmatrix(R, l, thresh, E, a, z=0.0):
     """Open-open K-matrix from the R-matrix at energy E (b = 0 matching).
+    z is the residual charge of the target (0: neutral, item 3; > 0: item 3').
 
     Solves (I - a R Lambda) Y = -B by LU with partial pivoting; K = Y[:n_o]/c.
     Returns (K (n_o x n_o), n_o, flags, pivot ratio min|u_jj| / max|u_jj|).
     """
     n = l.shape[0]
-    f = channel_functions(l, thresh, E, a)
+    f = channel_functions(l, thresh, E, a, z)
     no = f["n_o"]
     flags = 0
     if no == 0:
@@ -265,6 +322,7 @@ def sweep(wave, energies, sel=(0,), delta=0.05, part="all", keep_R=True, keep_K=
     flags (m,) uint8, piv_ratio (m,).
     """
     l, thr, poles, W, a = wave.l, wave.thresh, wave.poles, wave.W, wave.a
+    z = float(getattr(wave, "z", 0.0))
     n = l.shape[0]
     E_all, nflags = nudge_energies(energies, poles, thr)
     idx = np.arange(E_all.shape[0]) if energy_idx is None else np.asarray(energy_idx)
@@ -286,7 +344,7 @@ def sweep(wave, energies, sel=(0,), delta=0.05, part="all", keep_R=True, keep_K=
     for t, e in enumerate(idx):
         E = E_all[e]
         R = rmatrix(W, poles, E, a, delta=delta, part=part)
-        K, no, fl, ratio = kmatrix(R, l, thr, E, a)
+        K, no, fl, ratio = kmatrix(R, l, thr, E, a, z)
         fl |= int(nflags[e])
         out["flags"][t] = fl
         out["n_open"][t] = no

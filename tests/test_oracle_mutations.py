@@ -129,8 +129,57 @@ def pin_nudge():
     return En[0] == 0.5 + 5e-10 + 1e-6 and En[1] == 0.9 and fl[0] == o.FLAG_NUDGED and fl[1] == 0
 
 
+def pin_coulomb_hard_sphere():
+    # R = 0 with z > 0: K_ii = -F_l(eta, ka) / G_l(eta, ka), eta = -z/k
+    import mpmath as mp
+    a, E, z = 12.0, 1.3, 2.0
+    wave = synth.Wave(l=np.array([0, 1, 3, 1], np.int32), thresh=np.array([0.0, 0.2, 0.5, 1.5]),
+                      poles=np.array([-1.0, 4.0]), W=np.zeros((4, 2)), a=a, z=z)
+    out = o.sweep(wave, np.array([E]))
+    ok = out["n_open"][0] == 3
+    for i in range(3):
+        k = math.sqrt(E - wave.thresh[i])
+        with mp.workdps(30):
+            r = float(mp.coulombf(int(wave.l[i]), -z / k, k * a) / mp.coulombg(int(wave.l[i]), -z / k, k * a))
+        ok &= abs(out["K"][0, i, i] + r) <= 1e-10 * max(1.0, abs(r))
+    return bool(ok)
+
+
+def pin_coulomb_closed_hydrogenic():
+    # closed channel at kappa = z/(l+1): the decaying solution is r^(l+1) e^(-kappa r), so
+    # Lambda = (l+1)/a - kappa
+    a, z, lc = 9.0, 1.5, 2
+    kap = z / (lc + 1)
+    thr = np.array([0.0, 1.0])
+    E = thr[1] - kap * kap
+    f = o.channel_functions(np.array([0, lc], np.int32), thr, E, a, z=z)
+    return abs(f["lam"][1] - ((lc + 1) / a - kap)) <= 1e-12
+
+
+def pin_coulomb_eta_zero():
+    # eta = 0 gives the Riccati-Bessel functions (scipy), and the Wronskian is 1 at eta != 0
+    from scipy.special import spherical_jn, spherical_yn
+    ok = True
+    for l, x in [(0, 2.0), (3, 7.5)]:
+        F, Fp, G, Gp = o.coulomb_open(l, 0.0, x)
+        ok &= abs(F - x * spherical_jn(l, x)) <= 1e-12
+        ok &= abs(G + x * spherical_yn(l, x)) <= 1e-12 * max(1.0, abs(x * spherical_yn(l, x)))
+        ok &= abs(Fp - (spherical_jn(l, x) + x * spherical_jn(l, x, derivative=True))) <= 1e-12
+        F, Fp, G, Gp = o.coulomb_open(l, -3.0, x)
+        ok &= abs(Fp * G - F * Gp - 1.0) <= 1e-11
+    # large rho: F ~ sin(theta), F' ~ cos(theta), theta = rho - eta ln 2 rho - l pi/2 + arg Gamma(l+1+i eta)
+    from scipy.special import loggamma
+    l, eta, rho = 1, -3.0, 4000.0
+    th = rho - eta * math.log(2 * rho) - l * math.pi / 2 + loggamma(complex(l + 1, eta)).imag
+    F, Fp, G, Gp = o.coulomb_open(l, eta, rho)
+    tol = 2.0 * (eta * eta + l * (l + 1) + 1.0) / rho
+    ok &= abs(F - math.sin(th)) <= tol and abs(Fp - math.cos(th)) <= tol and abs(Gp + math.sin(th)) <= tol
+    return bool(ok)
+
+
 PINS = [pin_breit_wigner, pin_lane_thomas, pin_hard_sphere, pin_bloch, pin_closed_channel,
-        pin_symmetry_unitarity_balance, pin_nudge]
+        pin_symmetry_unitarity_balance, pin_nudge, pin_coulomb_hard_sphere, pin_coulomb_closed_hydrogenic,
+        pin_coulomb_eta_zero]
 
 
 def run_pins():
@@ -167,6 +216,14 @@ MUTATIONS = [
     ("eigenphase sign", o.eigenphase_sum, "np.sum(np.arctan(", "-np.sum(np.arctan("),
     ("nudge downwards", o.nudge_energies, "E[e] = E[e] + NUDGE_SHIFT", "E[e] = E[e] - NUDGE_SHIFT"),
     ("open count too large", o.n_open, "thresh < E", "thresh <= E + 0.5"),
+    ("Coulomb eta sign", o.channel_functions, "-z / k, k * a", "z / k, k * a"),
+    ("Coulomb c from F", o.channel_functions, "c[i] = G / math.sqrt(k)", "c[i] = F / math.sqrt(k)"),
+    ("Whittaker argument kappa a", o.channel_functions, "2.0 * kap * a)", "kap * a)"),
+    ("Whittaker order", o.channel_functions, "z / kap, 2.0 * kap * a", "-z / kap, 2.0 * kap * a"),
+    ("Whittaker derivative sign", o.whittaker_logderiv, "(xx / 2 - k) * W0 - W1", "(xx / 2 - k) * W0 + W1"),
+    ("Coulomb derivative coefficient", o.coulomb_open, "c2 = mp.sqrt(L * L + e * e) / L",
+     "c2 = mp.sqrt(L * L + e * e) / (L + 1)"),
+    ("Coulomb derivative eta term", o.coulomb_open, "c1 = (L * L / r + e) / L", "c1 = (L * L / r - e) / L"),
 ]
 
 
