@@ -13,6 +13,7 @@ replica of the workload (weak scaling) and the value is the total number of
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -78,6 +79,7 @@ def parse():
                     help="use every stride-th energy of the mesh (0 = automatic)")
     ap.add_argument("--sel", type=int, default=1, help="number of selected initial channels")
     ap.add_argument("--chunk", type=int, default=0, help="energies per rm_run chunk (0: automatic)")
+    ap.add_argument("--z", type=float, default=0.0, help="residual target charge of every wave (0: neutral)")
     ap.add_argument("--cluster", default="", help="tensor-core cluster shape CXxCY (default: autotuned)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -94,6 +96,10 @@ def dist_env():
 
 def workload(args):
     wl = synth.config(args.config)
+    if args.z:
+        # the same workload around an ion of residual charge z (Coulomb outer region)
+        wl = synth.Workload(f"{wl.name} z={args.z:g}", [dataclasses.replace(w, z=args.z) for w in wl.waves],
+                            wl.energies, wl.delta, wl.meta)
     stride = args.stride
     if stride == 0:
         stride = 25 if args.prec == "fp64" and args.config in (3, 5) else 1
@@ -238,7 +244,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     # inputs resident in HBM
     dwaves = [synth.Wave(l=torch.from_numpy(w.l).to(dev), thresh=torch.from_numpy(w.thresh).to(dev),
-                         poles=torch.from_numpy(w.poles).to(dev), W=torch.from_numpy(w.W).to(dev), a=w.a)
+                         poles=torch.from_numpy(w.poles).to(dev), W=torch.from_numpy(w.W).to(dev), a=w.a, z=w.z)
               for w in wl.waves]
     dE = torch.from_numpy(wl.energies).to(dev)
     cluster = tuple(int(x) for x in args.cluster.split("x")) if args.cluster else None
@@ -337,7 +343,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-        hwaves = [synth.Wave(l=pin(w.l), thresh=pin(w.thresh), poles=pin(w.poles), W=pin(w.W), a=w.a)
+        hwaves = [synth.Wave(l=pin(w.l), thresh=pin(w.thresh), poles=pin(w.poles), W=pin(w.W), a=w.a, z=w.z)
                   for w in wl.waves]
         hE = pin(wl.energies)
         outs = [{k: torch.from_numpy(v).pin_memory().numpy() for k, v in
@@ -455,7 +461,7 @@ def run_variants(args):
     E = wl.energies[::stride].copy()
     w = wl.waves[0]
     dwaves = [synth.Wave(l=torch.from_numpy(x.l).to(dev), thresh=torch.from_numpy(x.thresh).to(dev),
-                         poles=torch.from_numpy(x.poles).to(dev), W=torch.from_numpy(x.W).to(dev), a=x.a)
+                         poles=torch.from_numpy(x.poles).to(dev), W=torch.from_numpy(x.W).to(dev), a=x.a, z=x.z)
               for x in wl.waves]
     dE = torch.from_numpy(E).to(dev)
     idx = np.linspace(0, E.size - 1, 6).astype(int)

@@ -74,6 +74,8 @@ typedef enum {
 #define RM_FLAG_ILLCOND 2u   /* min|pivot| / max|pivot| of the matching LU below 1e-12 */
 #define RM_FLAG_NO_OPEN 4u   /* no open channel (E below every threshold); outputs are zero */
 #define RM_FLAG_SINGULAR 8u  /* exact zero pivot; outputs are NaN */
+#define RM_FLAG_ASYM 16u     /* a Coulomb / Whittaker continued fraction did not converge within its
+                                iteration cap for some channel (z > 0 only); outputs are unreliable */
 
 #define RM_LMAX 32           /* largest supported channel angular momentum */
 #define RM_MAX_SEL 64        /* largest number of selected initial channels */
@@ -89,6 +91,13 @@ typedef struct {
   const double* thresh;  /* [n] channel thresholds e_i (Ry), sorted ascending */
   const double* pole_E;  /* [N] poles E_k (Ry), sorted ascending */
   const double* W;       /* [n*N] surface amplitudes w_ik, row-major */
+  double z;              /* residual charge of the target seen by the scattered electron
+                            (potential -2z/r, Ry units), finite and >= 0.  0: neutral target,
+                            Riccati-Bessel / k-hat outer functions; > 0: ion, Coulomb functions
+                            F_l, G_l (eta = -z/k) for open and Whittaker W_{z/kappa, l+1/2} for
+                            closed channels.  The paper's targets are ions (B II, Ca II,
+                            Fe III ...); it gives no outer-region formulas, so these are the
+                            standard ones.  Repulsive fields (z < 0) are rejected. */
 } rm_wave;
 
 typedef struct {

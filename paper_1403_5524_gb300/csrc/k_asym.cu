@@ -14,6 +14,28 @@
 // khat is run upward on the scaled sequence exp(x) khat_l:
 // g_{l+1} = g_{l-1} + ((2l+1)/x) g_l, g_{-1} = g_0 = 1; the exponential
 // cancels in the log-derivative, khat_l'/khat_l = (-g_{l-1} - (l/x) g_l)/g_l.
+//
+// Ionic targets (residual charge z > 0, potential -2z/r): open channels use
+// the Coulomb functions F_l(eta, rho), G_l(eta, rho), eta = -z/k, rho = k a,
+// with s = k^-1/2 F, c = k^-1/2 G (z = 0 gives jhat_l and -nhat_l back);
+// closed channels the decaying Whittaker function W_{z/kappa, l+1/2}(2 kappa r).
+// Coulomb functions by Barnett's arrangement of Steed's method (Barnett,
+// Feng, Steed & Goldfarb 1974): the continued fraction CF1 for F_l'/F_l at the
+// channel's l, whose partial denominators also give the sign of F_l; the
+// recurrence down to order 0 for the unnormalised F; at order 0 (outside the
+// turning point for every attractive field) the complex continued fraction
+// CF2 for p + iq = (G' + iF')/(G + iF) and the Wronskian F'G - FG' = 1 fix
+// F_0 and G_0; G runs up again to order l.  CF2 is written here through the
+// Kummer function: G + iF = const e^(i rho) rho^(l+1) U(l+1+i eta, 2l+2, -2i rho),
+// so p + iq = -i + i eta/rho - r/rho with r = U(a-1,b,x)/U(a,b,x), and r is the
+// continued fraction of the recurrence
+//   U(a-1) + (b - 2a - x) U(a) + a(a - b + 1) U(a+1) = 0
+// in a (U is its minimal solution as a -> infinity).  The same fraction at real
+// x = 2 kappa a, a = l + 1 - z/kappa, b = 2l + 2 gives the Whittaker
+// log-derivative W'/W = 1/2 - (z/kappa + r)/x, because
+// W_{k,m}(x) = e^(-x/2) x^(m+1/2) U(m - k + 1/2, 2m + 1, x).
+// Every fraction runs under an iteration cap; a channel whose fraction does
+// not converge sets RM_FLAG_ASYM on its energy.
 #include <vector>
 
 #include "rm_internal.cuh"
@@ -91,27 +113,168 @@ __device__ double khat_logderiv(int l, double x) {
   return (-gm1 - (l / x) * g) / g;
 }
 
+constexpr int CF_MAXIT = 200000;      // iteration cap of every continued fraction
+constexpr double CF_EPS = 4.5e-16;     // |delta - 1| at convergence (two ulps)
+constexpr double CF_TINY = 1e-300;
+
+// CF1: f = F_l'/F_l = S_{l+1} - R^2_{l+1} / (S_{l+1} + S_{l+2} - R^2_{l+2} / (...)),
+// S_m = m/rho + eta/m, R^2_m = 1 + eta^2/m^2 (modified Lentz).  The sign of F_l
+// is the parity of negative partial denominators (F_L > 0 for L -> infinity).
+__device__ bool coulomb_cf1(int l, double eta, double rho, double& f, double& sign) {
+  auto S = [&](int m) { return m / rho + eta / m; };
+  f = S(l + 1);
+  if (f == 0.0) f = CF_TINY;
+  double C = f, D = 0.0;
+  sign = 1.0;
+  for (int k = 1; k < CF_MAXIT; ++k) {
+    const int m = l + k;
+    const double am = -(1.0 + (eta / m) * (eta / m));
+    const double bm = S(m) + S(m + 1);
+    D = bm + am * D;
+    if (D == 0.0) D = CF_TINY;
+    C = bm + am / C;
+    if (C == 0.0) C = CF_TINY;
+    D = 1.0 / D;
+    const double delta = C * D;
+    f *= delta;
+    if (D < 0.0) sign = -sign;
+    if (fabs(delta - 1.0) < CF_EPS) return true;
+  }
+  return false;
+}
+
+// complex quotient a / b (Smith's method)
+__device__ cplx cdiv(cplx a, cplx b) {
+  if (fabs(b.re) >= fabs(b.im)) {
+    const double t = b.im / b.re, d = b.re + b.im * t;
+    return cplx{(a.re + a.im * t) / d, (a.im - a.re * t) / d};
+  }
+  const double t = b.re / b.im, d = b.im + b.re * t;
+  return cplx{(a.re * t + a.im) / d, (a.im * t - a.re) / d};
+}
+
+// r = U(a-1,b,x)/U(a,b,x) for complex a, x (b real) by the continued fraction of
+// the recurrence in a: r = (2a + x - b) - a(a-b+1) / ((2a + 2 + x - b) - ...).
+__device__ bool kummer_ratio(cplx a, double b, cplx x, cplx& r) {
+  r = cplx{2.0 * a.re + x.re - b, 2.0 * a.im + x.im};
+  if (r.re == 0.0 && r.im == 0.0) r = cplx{CF_TINY, 0.0};
+  cplx C = r, D = cplx{0.0, 0.0};
+  for (int k = 1; k < CF_MAXIT; ++k) {
+    const cplx p = cplx{a.re + (k - 1), a.im} * cplx{a.re + (k - b), a.im};
+    const cplx ak = cplx{-p.re, -p.im};
+    const cplx bk = cplx{2.0 * (a.re + k) + x.re - b, 2.0 * a.im + x.im};
+    D = bk + ak * D;
+    if (D.re == 0.0 && D.im == 0.0) D = cplx{CF_TINY, 0.0};
+    C = bk + cdiv(ak, C);
+    if (C.re == 0.0 && C.im == 0.0) C = cplx{CF_TINY, 0.0};
+    D = cdiv(cplx{1.0, 0.0}, D);
+    const cplx delta = C * D;
+    r = r * delta;
+    if (fabs(delta.re - 1.0) + fabs(delta.im) < CF_EPS) return true;
+  }
+  return false;
+}
+
+// F_l, F_l', G_l, G_l' (derivatives in rho) for eta <= 0; false if a fraction
+// did not converge.
+__device__ bool coulomb_open(int l, double eta, double rho, double& F, double& Fp, double& G, double& Gp) {
+  double f, sign;
+  bool ok = coulomb_cf1(l, eta, rho, f, sign);
+  // unnormalised F down to order 0: u_{m-1} = (S_m u_m + u_m')/R_m, u_{m-1}' = S_m u_{m-1} - R_m u_m
+  double Fu = sign, Fpu = sign * f, scale = 1.0;
+  for (int m = l; m >= 1; --m) {
+    const double S = m / rho + eta / m;
+    const double R = sqrt(1.0 + (eta / m) * (eta / m));
+    const double Fm = (S * Fu + Fpu) / R;
+    Fpu = S * Fm - R * Fu;
+    Fu = Fm;
+    if (fabs(Fu) > 1e250) {
+      Fu *= 1e-250;
+      Fpu *= 1e-250;
+      scale *= 1e-250;  // F_l = (F_0 / Fu) * sign * scale
+    }
+  }
+  const double f0 = Fpu / Fu;
+  // CF2 at order 0: p + iq = -i + i eta/rho - r/rho, r from U(1 + i eta, 2, -2i rho)
+  cplx r;
+  ok = kummer_ratio(cplx{1.0, eta}, 2.0, cplx{0.0, -2.0 * rho}, r) && ok;
+  const double p = r.re * (-1.0 / rho);
+  const double q = -1.0 + eta / rho - r.im / rho;
+  const double F0 = copysign(sqrt(q / ((f0 - p) * (f0 - p) + q * q)), Fu);
+  double Gm = (f0 - p) * F0 / q;
+  double Gpm = p * Gm - q * F0;
+  F = (F0 / Fu) * sign * scale;
+  Fp = F * f;
+  // G upward: u_{m+1} = (S_{m+1} u_m - u_m')/R_{m+1}, u_{m+1}' = R_{m+1} u_m - S_{m+1} u_{m+1}
+  for (int m = 0; m < l; ++m) {
+    const double S = (m + 1) / rho + eta / (m + 1);
+    const double R = sqrt(1.0 + (eta / (m + 1)) * (eta / (m + 1)));
+    const double G1 = (S * Gm - Gpm) / R;
+    Gpm = R * Gm - S * G1;
+    Gm = G1;
+  }
+  G = Gm;
+  Gp = Gpm;
+  return ok && isfinite(F) && isfinite(G) && q > 0.0;
+}
+
+// W'/W of W_{kp, l+1/2}(x), x > 0, by the real Kummer-ratio fraction
+__device__ bool whittaker_logderiv(int l, double kp, double x, double& d) {
+  cplx r;
+  const bool ok = kummer_ratio(cplx{l + 1.0 - kp, 0.0}, 2.0 * l + 2.0, cplx{x, 0.0}, r);
+  d = 0.5 - (kp + r.re) / x;
+  return ok && isfinite(d);
+}
+
+// Matching data of one (energy, channel): Lambda, s, s', c (s = s' = c = 0 closed).
+__device__ bool channel_data(int l, double k2, double a, double z, double& lam, double& s, double& sp,
+                             double& c) {
+  s = sp = c = 0.0;
+  if (k2 > 0.0) {
+    const double k = sqrt(k2), sk = sqrt(k);
+    if (z == 0.0) {
+      double j, jp, y, yp;
+      riccati_open(l, k * a, j, jp, y, yp);
+      s = j / sk;
+      sp = jp * sk;
+      c = -y / sk;
+      lam = k * yp / y;  // c'/c
+      return true;
+    }
+    double F, Fp, G, Gp;
+    const bool ok = coulomb_open(l, -z / k, k * a, F, Fp, G, Gp);
+    s = F / sk;
+    sp = Fp * sk;
+    c = G / sk;
+    lam = k * Gp / G;
+    return ok;
+  }
+  const double kap = sqrt(-k2);
+  if (z == 0.0) {
+    lam = kap * khat_logderiv(l, kap * a);
+    return true;
+  }
+  double d;
+  const bool ok = whittaker_logderiv(l, z / kap, 2.0 * kap * a, d);
+  lam = 2.0 * kap * d;
+  return ok;
+}
+
+// flag the energy's byte in a uint8 flag array (atomically: several channels may fail)
+__device__ void flag_energy(uint8_t* flags, int64_t e, uint8_t bit) {
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(flags + e);
+  unsigned int* word = reinterpret_cast<unsigned int*>(addr & ~uintptr_t(3));
+  atomicOr(word, (unsigned int)bit << (8 * (addr & 3)));
+}
+
 __global__ void asym_kernel(const int32_t* __restrict__ lch, const double* __restrict__ thr, int n,
-                            double a, const double* __restrict__ E, int ne,
-                            double* __restrict__ out, int64_t ld) {
+                            double a, double z, const double* __restrict__ E, int ne,
+                            double* __restrict__ out, int64_t ld, uint8_t* flags) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)ne * n) return;
   const int e = (int)(t / n), i = (int)(t % n);
-  const double k2 = E[e] - thr[i];
-  const int l = lch[i];
-  double lam, s = 0.0, sp = 0.0, c = 0.0;
-  if (k2 > 0.0) {
-    const double k = sqrt(k2), sk = sqrt(k);
-    double j, jp, y, yp;
-    riccati_open(l, k * a, j, jp, y, yp);
-    s = j / sk;
-    sp = jp * sk;
-    c = -y / sk;
-    lam = k * yp / y;  // c'/c
-  } else {
-    const double kap = sqrt(-k2);
-    lam = kap * khat_logderiv(l, kap * a);
-  }
+  double lam, s, sp, c;
+  if (!channel_data(lch[i], E[e] - thr[i], a, z, lam, s, sp, c)) flag_energy(flags, e, RM_FLAG_ASYM);
   out[0 * ld + t] = lam;
   out[1 * ld + t] = s;
   out[2 * ld + t] = sp;
@@ -123,7 +286,9 @@ struct AsymWave {
   const double* thr;
   const double* E;  // nudged mesh (base)
   double* out;      // chunk buffer [4][chunk * n]
+  uint8_t* flags;   // per-energy input flags of the solve (base)
   double a;
+  double z;
   int n;
 };
 
@@ -135,21 +300,9 @@ __global__ void asym_grouped_kernel(const AsymWave* __restrict__ waves, int64_t 
   // ld between the four quantities is chunk * n of this wave
   const int64_t ld = ld_chunk * w.n;
   const int e = (int)(t / w.n), i = (int)(t % w.n);
-  const double k2 = w.E[e_begin + e] - w.thr[i];
-  const int l = w.l[i];
-  double lam, s = 0.0, sp = 0.0, c = 0.0;
-  if (k2 > 0.0) {
-    const double k = sqrt(k2), sk = sqrt(k);
-    double j, jp, y, yp;
-    riccati_open(l, k * w.a, j, jp, y, yp);
-    s = j / sk;
-    sp = jp * sk;
-    c = -y / sk;
-    lam = k * yp / y;
-  } else {
-    const double kap = sqrt(-k2);
-    lam = kap * khat_logderiv(l, kap * w.a);
-  }
+  double lam, s, sp, c;
+  if (!channel_data(w.l[i], w.E[e_begin + e] - w.thr[i], w.a, w.z, lam, s, sp, c))
+    flag_energy(w.flags, e_begin + e, RM_FLAG_ASYM);
   w.out[0 * ld + t] = lam;
   w.out[1 * ld + t] = s;
   w.out[2 * ld + t] = sp;
@@ -163,7 +316,7 @@ cudaError_t group_setup_asym(Plan& p) {
   std::vector<AsymWave> h(p.n_waves);
   for (int g = 0; g < p.n_waves; ++g) {
     const WaveDev& w = p.waves[g];
-    h[g] = AsymWave{w.l, w.thr, w.E, G.asym[g], w.a, w.n};
+    h[g] = AsymWave{w.l, w.thr, w.E, G.asym[g], w.flags0, w.a, w.z, w.n};
   }
   cudaError_t err;
   if (!G.asym_waves && (err = cudaMalloc(&G.asym_waves, sizeof(AsymWave) * p.n_waves)) != cudaSuccess) return err;
@@ -184,8 +337,8 @@ cudaError_t launch_asym(const WaveDev& w, int64_t e0, int ne, double* asym, int 
   if (ne <= 0) return cudaSuccess;
   const int64_t total = (int64_t)ne * w.n;
   const int bs = 256;
-  asym_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(w.l, w.thr, w.n, w.a, w.E + e0, ne,
-                                                              asym, (int64_t)ld_chunk);
+  asym_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(w.l, w.thr, w.n, w.a, w.z, w.E + e0, ne,
+                                                              asym, (int64_t)ld_chunk, w.flags0 + e0);
   return cudaGetLastError();
 }
 

@@ -88,6 +88,7 @@ rm_status_t check_wave_args(const rm_wave& w, int idx) {
   if (w.n_ch < 1 || w.n_ch > 640) return fail(RM_ERR_ARG, tag + "n_ch must be in [1, 640]");
   if (w.n_poles < 1) return fail(RM_ERR_ARG, tag + "n_poles must be >= 1");
   if (!(w.a > 0.0) || !(w.a < 1e300)) return fail(RM_ERR_ARG, tag + "radius a must be finite and > 0");
+  if (!(w.z >= 0.0) || !(w.z < 1e300)) return fail(RM_ERR_ARG, tag + "charge z must be finite and >= 0");
   if (!w.l || !w.thresh || !w.pole_E || !w.W) return fail(RM_ERR_ARG, tag + "null input pointer");
   return RM_OK;
 }
@@ -621,6 +622,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       d.N = waves[g].n_poles;
       d.Npad = (d.N + 63) / 64 * 64;
       d.a = waves[g].a;
+      d.z = waves[g].z;
       n_max = d.n > n_max ? d.n : n_max;
       const int64_t np = (int64_t)d.n * (d.n + 1) / 2;
       np_max = np > np_max ? np : np_max;
@@ -760,7 +762,8 @@ rm_status_t rm_plan_load(rm_plan_t h, const rm_wave* waves, const double* energi
       if (st != RM_OK) return st;
       if (waves[g].n_ch != p->waves[g].n || waves[g].n_poles != p->waves[g].N)
         return fail(RM_ERR_ARG, "wave shape differs from the plan's");
-      if (waves[g].a != p->waves[g].a) p->waves[g].a = waves[g].a;
+      p->waves[g].a = waves[g].a;
+      p->waves[g].z = waves[g].z;
     }
     if (cudaSetDevice(p->device) != cudaSuccess) return fail(RM_ERR_CUDA, "cudaSetDevice failed");
     return prepare(p, waves, energies, mem);

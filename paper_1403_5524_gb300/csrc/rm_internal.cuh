@@ -39,7 +39,7 @@ struct SplitDev {
   float* pol = nullptr;     // [2 * Npad] poles as FP32 hi (row 0) + lo (row 1)
   double* sigma = nullptr;  // [n] power-of-two channel scales
   float* mult_p = nullptr;  // [n_p] 2^(e_p + 8)
-  double* f_p = nullptr;    // [n_p] sigma_i sigma_j 2^-e_p 2^-48 / (2a)
+  double* f_p = nullptr;    // [n_p] sigma_i sigma_j 2^-e_p 2^-16 / (2a)
   int32_t* klo = nullptr;   // [n_e] near window [klo, khi) in pole indices
   int32_t* khi = nullptr;
   double* tau = nullptr;    // [n_e] power-of-two D scale
@@ -57,6 +57,7 @@ struct WaveDev {
   int N = 0;         // poles
   int Npad = 0;      // poles rounded up for aligned tiles
   double a = 0.0;
+  double z = 0.0;    // residual target charge (0: neutral)
   int lmax = 0;
   int32_t* l = nullptr;     // [n]
   double* thr = nullptr;    // [n]

@@ -18,21 +18,23 @@ LIB_PATH = os.path.join(_HERE, "librm.so")
 RM_OK, RM_ERR_ARG, RM_ERR_ORDER, RM_ERR_NOMEM, RM_ERR_CUDA, RM_ERR_TIMEOUT, RM_ERR_STATE = range(7)
 RM_MEM_HOST, RM_MEM_DEVICE = 0, 1
 RM_PREC_FP64, RM_PREC_SPLIT_BF16, RM_PREC_SPLIT_FP16, RM_PREC_FP32_SIMT = 0, 1, 2, 3
-FLAG_NUDGED, FLAG_ILLCOND, FLAG_NO_OPEN, FLAG_SINGULAR = 1, 2, 4, 8
+FLAG_NUDGED, FLAG_ILLCOND, FLAG_NO_OPEN, FLAG_SINGULAR, FLAG_ASYM = 1, 2, 4, 8, 16
 
 PREC = {"fp64": RM_PREC_FP64, "split_bf16": RM_PREC_SPLIT_BF16, "split_fp16": RM_PREC_SPLIT_FP16,
         "fp32_simt": RM_PREC_FP32_SIMT}
 
 EXPORTS = ["rm_options_default", "rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix",
            "rm_xsec", "rm_run", "rm_results", "rm_sync", "rm_plan_info", "rm_plan_launches",
-           "rm_plan_destroy", "rm_status_str", "rm_last_error", "rm_profile_enable", "rm_profile_read"]
+           "rm_plan_destroy", "rm_status_str", "rm_last_error", "rm_profile_enable", "rm_profile_read",
+           "rm_plan_cluster"]
 
 KERNELS = {"polesum_fp64": 0, "polesum_split": 1, "near": 2, "asym": 3, "solve": 4}
 
 
 class rm_wave(C.Structure):
     _fields_ = [("n_ch", C.c_int32), ("n_poles", C.c_int32), ("a", C.c_double),
-                ("l", C.c_void_p), ("thresh", C.c_void_p), ("pole_E", C.c_void_p), ("W", C.c_void_p)]
+                ("l", C.c_void_p), ("thresh", C.c_void_p), ("pole_E", C.c_void_p), ("W", C.c_void_p),
+                ("z", C.c_double)]
 
 
 class rm_options(C.Structure):
@@ -166,6 +168,7 @@ class Plan:
             warr[g].n_ch = int(arrs[0].shape[0])
             warr[g].n_poles = int(arrs[2].shape[0])
             warr[g].a = float(w.a)
+            warr[g].z = float(getattr(w, "z", 0.0))
             warr[g].l, warr[g].thresh, warr[g].pole_E, warr[g].W = (_ptr(a) for a in arrs)
         return warr
 

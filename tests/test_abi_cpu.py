@@ -53,6 +53,7 @@ def _create(lib, waves, energies, opt=None, n_waves=None):
         warr[g].n_ch, warr[g].n_poles, warr[g].a = w.l.shape[0], w.poles.shape[0], w.a
         warr[g].l, warr[g].thresh = w.l.ctypes.data, w.thresh.ctypes.data
         warr[g].pole_E, warr[g].W = w.poles.ctypes.data, w.W.ctypes.data
+        warr[g].z = w.z
     code = lib.rm_plan_create(C.byref(h), warr, len(waves) if n_waves is None else n_waves,
                               energies.ctypes.data if energies is not None else None,
                               0 if energies is None else energies.shape[0],
@@ -68,6 +69,9 @@ def test_bad_arguments_rejected_before_device(lib):
     assert code == rm.RM_ERR_ARG and not h.value
     bad = synth.Wave(l=w.l, thresh=w.thresh, poles=w.poles, W=w.W, a=-1.0)
     assert _create(lib, [bad], wl.energies)[0] == rm.RM_ERR_ARG
+    for z in (-1.0, float("nan"), float("inf")):  # repulsive or non-finite target charge
+        badz = synth.Wave(l=w.l, thresh=w.thresh, poles=w.poles, W=w.W, a=w.a, z=z)
+        assert _create(lib, [badz], wl.energies)[0] == rm.RM_ERR_ARG
     o = rm.rm_options()
     lib.rm_options_default(C.byref(o))
     o.prec = 7
