@@ -37,6 +37,19 @@ in bohr, k^2 = E - e_i):
    (statistical weight (2J+1)/g_i taken as 1), eigenphase sum
    eta = sum_m arctan(lambda_m(K)).
 
+6. Photoionisation (a wave with a bound-free dipole vector d_k = <psi_k|D|Psi_0>
+   over the inner-region eigenstates and an initial bound-state energy E_0; the
+   paper names the module but prints no formulas, so this is the standard
+   R-matrix reading, length form): the inner-region part of the final state is
+   sum_k A_k psi_k with A_k = sum_i psi_ik(a) F_i'(a) / (E_k - E), so with
+   w_ik = sqrt(2) psi_ik(a) and the dipole vector y_i = (1/2a) sum_k w_ik d_k / (E_k - E)
+   the K-normalised amplitude of open solution m is
+   M^K_m = sqrt(2) a sum_i F'_im y_i, F'_im = s'_m d_im + Lambda_i Y_im,
+   the incoming-wave amplitudes are M^- = (I + iK)^-1 M^K, and
+   sigma_PI = (4 pi alpha / 3) omega sum_m |M^-_m|^2 (a0^2; omega = E - E_0 in Ry;
+   s, c normalised as k^-1/2 sin, cos, i.e. sqrt(pi) times per-Rydberg energy
+   normalisation; initial statistical weight 1).
+
 Energies closer than 1e-9 Ry to a pole or a threshold are moved up by 1e-6 Ry,
 once, and flagged.
 
@@ -287,6 +300,39 @@ def kmatrix(R, l, thresh, E, a, z=0.0):
     return K, no, flags, ratio
 
 
+ALPHA = 7.2973525693e-3                    # fine-structure constant (CODATA 2018)
+PI_PREFACTOR = 4.0 * math.pi * ALPHA / 3.0   # sigma_PI = PI_PREFACTOR omega sum |M^-|^2
+
+
+def dipole_vector(W, dip, poles, E, a):
+    """y_i(E) = (1/2a) sum_k w_ik d_k / (E_k - E): the pole sum of item 6."""
+    return (W @ (dip / (poles - E))) / (2.0 * a)
+
+
+def photo_amplitudes(R, y, l, thresh, E, a, z=0.0):
+    """Dipole amplitudes of the open final channels at energy E (item 6).
+
+    Solves the matching system of item 4 for Y, forms the boundary derivatives
+    F'_im = s'_m delta_im + Lambda_i Y_im of each K-normalised solution m, then
+    M^K = sqrt(2) a F'^T y and M^- = (I + iK)^-1 M^K.  Returns (M^K, M^-, K).
+    """
+    n = l.shape[0]
+    f = channel_functions(l, thresh, E, a, z)
+    no = f["n_o"]
+    if no == 0:
+        return np.zeros(0), np.zeros(0, complex), np.zeros((0, 0))
+    Mt = np.eye(n) - a * R * f["lam"][None, :]
+    B = -a * R[:, :no] * f["sp"][None, :no]
+    B[np.arange(no), np.arange(no)] += f["s"][:no]
+    Y = np.linalg.solve(Mt, -B)
+    K = Y[:no, :] / f["c"][:no, None]
+    Fp = f["lam"][:, None] * Y
+    Fp[np.arange(no), np.arange(no)] += f["sp"][:no]
+    MK = math.sqrt(2.0) * a * (Fp.T @ y)
+    Mm = np.linalg.solve(np.eye(no) + 1j * K, MK.astype(complex))
+    return MK, Mm, K
+
+
 def smatrix(K):
     """S = (I + iK)(I - iK)^-1 (= (I - iK)^-1 (I + iK) for symmetric K) and T = S - I."""
     no = K.shape[0]
@@ -341,6 +387,10 @@ def sweep(wave, energies, sel=(0,), delta=0.05, part="all", keep_R=True, keep_K=
         out["R"] = np.zeros((m, n * (n + 1) // 2))
     if keep_K:
         out["K"] = np.zeros((m, n, n))
+    dip = getattr(wave, "dip", None)
+    if dip is not None:
+        out["sig_pi"] = np.zeros(m)
+        out["sig_pi_ch"] = np.zeros((m, n))
     for t, e in enumerate(idx):
         E = E_all[e]
         R = rmatrix(W, poles, E, a, delta=delta, part=part)
@@ -355,6 +405,12 @@ def sweep(wave, energies, sel=(0,), delta=0.05, part="all", keep_R=True, keep_K=
             continue
         if keep_K:
             out["K"][t, :no, :no] = K
+        if dip is not None:
+            y = dipole_vector(W, np.asarray(dip, dtype=np.float64), poles, E, a)
+            _, Mm, _ = photo_amplitudes(R, y, l, thr, E, a, z)
+            ch = PI_PREFACTOR * (E - float(wave.e0)) * np.abs(Mm) ** 2
+            out["sig_pi_ch"][t, :no] = ch
+            out["sig_pi"][t] = float(np.sum(ch))
         S, T = smatrix(K)
         sig = xsec(T, E - thr)
         out["eta"][t] = eigenphase_sum(K)

@@ -26,7 +26,7 @@ implementation itself.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List
+from typing import Optional, List
 
 import numpy as np
 
@@ -39,6 +39,8 @@ class Wave:
     W: np.ndarray          # float64 (n, N), C-contiguous
     a: float               # R-matrix radius, bohr
     z: float = 0.0         # residual charge of the target (0 neutral, > 0 ion)
+    dip: Optional[np.ndarray] = None  # float64 (N,) bound-free dipole vector d_k, or None
+    e0: float = 0.0        # initial bound-state energy (Ry) of the photoionisation
 
     @property
     def n(self) -> int:
@@ -64,8 +66,10 @@ class Workload:
 
 def make_wave(rng: np.random.Generator, n: int, N: int, *, lmax: int = 7,
               thr_hi: float = 2.0, pole_lo: float = -5.0, pole_hi: float = 60.0,
-              a: float = 30.0, l_fixed=None, z: float = 0.0) -> Wave:
-    """Draw one wave in the documented order (thresholds, l, poles, W)."""
+              a: float = 30.0, l_fixed=None, z: float = 0.0, dipole: bool = False,
+              e0: float = -0.5) -> Wave:
+    """Draw one wave in the documented order (thresholds, l, poles, W, then the
+    dipole vector d_k ~ N(0, 1/N) when asked for)."""
     thr = np.sort(rng.uniform(0.0, thr_hi, size=n))
     if n > 0:
         thr[0] = 0.0
@@ -75,8 +79,10 @@ def make_wave(rng: np.random.Generator, n: int, N: int, *, lmax: int = 7,
         l = rng.integers(0, lmax + 1, size=n).astype(np.int32)
     poles = np.sort(rng.uniform(pole_lo, pole_hi, size=N))
     W = rng.normal(0.0, 1.0 / np.sqrt(max(N, 1)), size=(n, N))
+    dip = rng.normal(0.0, 1.0 / np.sqrt(max(N, 1)), size=N).astype(np.float64) if dipole else None
     return Wave(l=l, thresh=thr.astype(np.float64), poles=poles.astype(np.float64),
-                W=np.ascontiguousarray(W, dtype=np.float64), a=float(a), z=float(z))
+                W=np.ascontiguousarray(W, dtype=np.float64), a=float(a), z=float(z), dip=dip,
+                e0=float(e0))
 
 
 def config(idx: int, seed: int = 0) -> Workload:
@@ -122,9 +128,10 @@ def config(idx: int, seed: int = 0) -> Workload:
 
 def small(seed: int, n: int, N: int, n_e: int, *, e_lo: float = 0.01, e_hi: float = 3.0,
           lmax: int = 7, thr_hi: float = 2.0, pole_lo: float = -5.0, pole_hi: float = 40.0,
-          a: float = 25.0, delta: float = 0.05, z: float = 0.0) -> Workload:
+          a: float = 25.0, delta: float = 0.05, z: float = 0.0, dipole: bool = False) -> Workload:
     """A small seeded single-wave workload with the distributions of the named ones."""
     rng = np.random.default_rng(seed)
-    w = make_wave(rng, n, N, lmax=lmax, thr_hi=thr_hi, pole_lo=pole_lo, pole_hi=pole_hi, a=a, z=z)
+    w = make_wave(rng, n, N, lmax=lmax, thr_hi=thr_hi, pole_lo=pole_lo, pole_hi=pole_hi, a=a, z=z,
+                  dipole=dipole)
     return Workload(f"small n={n} N={N} n_e={n_e} seed={seed}", [w],
                     np.linspace(e_lo, e_hi, n_e), delta=delta)

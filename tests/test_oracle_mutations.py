@@ -177,9 +177,29 @@ def pin_coulomb_eta_zero():
     return bool(ok)
 
 
+def pin_photo():
+    # amplitudes against the brute-force inner-region solve (one closed channel), scalar
+    # incoming-wave normalisation, and a positive sigma_PI from the sweep
+    from tests.test_oracle_photo import brute_force_amplitudes, inner_problem
+    thr, E = np.array([0.0, 0.3, 2.5]), 0.8
+    l, H, O, Bv, Ek, W, v, dip, a = inner_problem(3, thr, seed=8)
+    R = o.rmatrix(W, Ek, E, a)
+    MK, Mm, K = o.photo_amplitudes(R, o.dipole_vector(W, dip, Ek, E, a), l, thr, E, a)
+    Mb, _ = brute_force_amplitudes(l, thr, H, O, Bv, v, R, E, a)
+    ok = np.abs(MK - Mb).max() <= 1e-9 * max(1.0, np.abs(Mb).max())
+    wave = synth.Wave(l=l, thresh=thr, poles=Ek, W=W, a=a, dip=dip, e0=-0.4)
+    out = o.sweep(wave, np.array([E]))
+    ok &= out["sig_pi"][0] > 0.0
+    # single channel: |M^-|^2 = (M^K)^2 / (1 + K^2)
+    W1, y1 = W[:1], o.dipole_vector(W[:1], dip, Ek, 1.7, a)
+    MK1, Mm1, K1 = o.photo_amplitudes(o.rmatrix(W1, Ek, 1.7, a), y1, l[:1], thr[:1], 1.7, a)
+    ok &= abs(abs(Mm1[0]) ** 2 - MK1[0] ** 2 / (1.0 + K1[0, 0] ** 2)) <= 1e-12 * MK1[0] ** 2
+    return bool(ok)
+
+
 PINS = [pin_breit_wigner, pin_lane_thomas, pin_hard_sphere, pin_bloch, pin_closed_channel,
         pin_symmetry_unitarity_balance, pin_nudge, pin_coulomb_hard_sphere, pin_coulomb_closed_hydrogenic,
-        pin_coulomb_eta_zero]
+        pin_coulomb_eta_zero, pin_photo]
 
 
 def run_pins():
@@ -224,6 +244,12 @@ MUTATIONS = [
     ("Coulomb derivative coefficient", o.coulomb_open, "c2 = mp.sqrt(L * L + e * e) / L",
      "c2 = mp.sqrt(L * L + e * e) / (L + 1)"),
     ("Coulomb derivative eta term", o.coulomb_open, "c1 = (L * L / r + e) / L", "c1 = (L * L / r - e) / L"),
+    ("dipole vector 1/a", o.dipole_vector, "/ (2.0 * a)", "/ a"),
+    ("dipole amplitude without sqrt 2", o.photo_amplitudes, "math.sqrt(2.0) * a * (Fp.T @ y)", "a * (Fp.T @ y)"),
+    ("boundary derivative without s'", o.photo_amplitudes, "+= f[\"sp\"][:no]", "+= 0.0 * f[\"sp\"][:no]"),
+    ("boundary derivative Lambda by column", o.photo_amplitudes, "f[\"lam\"][:, None] * Y",
+     "f[\"lam\"][None, :no] * Y"),
+    ("photon energy sign", o.sweep, "(E - float(wave.e0))", "(float(wave.e0) - E)"),
 ]
 
 
