@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--sel", type=int, default=1, help="number of selected initial channels")
     ap.add_argument("--chunk", type=int, default=0, help="energies per rm_run chunk (0: automatic)")
     ap.add_argument("--z", type=float, default=0.0, help="residual target charge of every wave (0: neutral)")
+    ap.add_argument("--dipole", action="store_true",
+                    help="photoionisation: give every wave a bound-free dipole vector (sigma_PI per energy)")
     ap.add_argument("--cluster", default="", help="tensor-core cluster shape CXxCY (default: autotuned)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -96,6 +98,15 @@ def dist_env():
 
 def workload(args):
     wl = synth.config(args.config)
+    if args.dipole:
+        # photoionisation: a seeded bound-free dipole vector d_k ~ N(0, 1/N) per wave (its own
+        # random stream, so W and the poles are unchanged) and an initial state 0.5 Ry below
+        # the first threshold
+        waves = []
+        for g, w in enumerate(wl.waves):
+            rng = np.random.default_rng([args.config, 7777, g])
+            waves.append(dataclasses.replace(w, dip=rng.normal(0.0, 1.0 / math.sqrt(w.N), w.N), e0=-0.5))
+        wl = synth.Workload(f"{wl.name} photoionisation", waves, wl.energies, wl.delta, wl.meta)
     if args.z:
         # the same workload around an ion of residual charge z (Coulomb outer region)
         wl = synth.Workload(f"{wl.name} z={args.z:g}", [dataclasses.replace(w, z=args.z) for w in wl.waves],
@@ -244,7 +255,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     # inputs resident in HBM
     dwaves = [synth.Wave(l=torch.from_numpy(w.l).to(dev), thresh=torch.from_numpy(w.thresh).to(dev),
-                         poles=torch.from_numpy(w.poles).to(dev), W=torch.from_numpy(w.W).to(dev), a=w.a, z=w.z)
+                         poles=torch.from_numpy(w.poles).to(dev), W=torch.from_numpy(w.W).to(dev), a=w.a, z=w.z,
+                         dip=None if w.dip is None else torch.from_numpy(w.dip).to(dev), e0=w.e0)
               for w in wl.waves]
     dE = torch.from_numpy(wl.energies).to(dev)
     cluster = tuple(int(x) for x in args.cluster.split("x")) if args.cluster else None
@@ -343,13 +355,17 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-        hwaves = [synth.Wave(l=pin(w.l), thresh=pin(w.thresh), poles=pin(w.poles), W=pin(w.W), a=w.a, z=w.z)
+        hwaves = [synth.Wave(l=pin(w.l), thresh=pin(w.thresh), poles=pin(w.poles), W=pin(w.W), a=w.a, z=w.z,
+                              dip=None if w.dip is None else pin(w.dip), e0=w.e0)
                   for w in wl.waves]
         hE = pin(wl.energies)
         outs = [{k: torch.from_numpy(v).pin_memory().numpy() for k, v in
                  rm.host_outputs(wl.n_e, w.n, len(sel)).items()} for w in wl.waves]
-        h2d = sum(w.l.nbytes + w.thresh.nbytes + w.poles.nbytes + w.W.nbytes for w in wl.waves) + hE.nbytes
-        d2h = sum(sum(v.nbytes for v in o.values()) for o in outs)
+        pis = [torch.zeros(wl.n_e, dtype=torch.float64).pin_memory().numpy() if w.dip is not None else None
+               for w in wl.waves]
+        h2d = sum(w.l.nbytes + w.thresh.nbytes + w.poles.nbytes + w.W.nbytes
+                  + (0 if w.dip is None else w.dip.nbytes) for w in wl.waves) + hE.nbytes
+        d2h = sum(sum(v.nbytes for v in o.values()) for o in outs) + sum(x.nbytes for x in pis if x is not None)
         e2e_steps = max(1, min(args.steps, 3))
         barrier()
         t0 = time.perf_counter()
@@ -358,6 +374,8 @@ def run_ours(args):
             plan.run()
             for g in range(len(wl.waves)):
                 plan.results(g, 0, wl.n_e, **outs[g])
+                if pis[g] is not None:
+                    plan.results_photo(g, 0, wl.n_e, sig_pi=pis[g])
         barrier()
         dt = (time.perf_counter() - t0) / e2e_steps
         if world > 1:
@@ -424,7 +442,7 @@ def accuracy(plan, wl, sel, idx, ref):
     FL_SKIP = 2 | 4 | 8  # ILLCOND | NO_OPEN | SINGULAR
     w = wl.waves[0]
     n = w.n
-    eR = eK = eS = eE = 0.0
+    eR = eK = eS = eE = ePI = 0.0
     R = np.zeros((1, n * (n + 1) // 2))
     K = np.zeros((1, n, n))
     for t, e in enumerate(idx):
@@ -446,8 +464,15 @@ def accuracy(plan, wl, sel, idx, ref):
                 eS = max(eS, float(np.abs(out["sig_sel"][0, q] - ref["sig_sel"][t, q]).max() / st))
         d = out["eigsum"][0] - ref["eta"][t]
         eE = max(eE, float(abs(np.mod(d + np.pi, 2 * np.pi) - np.pi)))
-    return {"energies_checked": int(len(idx)), "R": eR, "K": eK, "sigma": eS, "eigsum_abs": eE,
-            "norm": "max|x - x*| / max|x*| per energy (sigma: / sigma_tot of the initial channel)"}
+        if "sig_pi" in ref and ref["sig_pi"][t] > 0:
+            pi = np.zeros(1)
+            plan.photo(0, e, e + 1, sig_pi=pi)
+            ePI = max(ePI, float(abs(pi[0] - ref["sig_pi"][t]) / ref["sig_pi"][t]))
+    res = {"energies_checked": int(len(idx)), "R": eR, "K": eK, "sigma": eS, "eigsum_abs": eE,
+           "norm": "max|x - x*| / max|x*| per energy (sigma: / sigma_tot of the initial channel)"}
+    if "sig_pi" in ref:
+        res["sigma_pi"] = ePI
+    return res
 
 
 def run_variants(args):
@@ -461,7 +486,8 @@ def run_variants(args):
     E = wl.energies[::stride].copy()
     w = wl.waves[0]
     dwaves = [synth.Wave(l=torch.from_numpy(x.l).to(dev), thresh=torch.from_numpy(x.thresh).to(dev),
-                         poles=torch.from_numpy(x.poles).to(dev), W=torch.from_numpy(x.W).to(dev), a=x.a, z=x.z)
+                         poles=torch.from_numpy(x.poles).to(dev), W=torch.from_numpy(x.W).to(dev), a=x.a, z=x.z,
+                         dip=None if x.dip is None else torch.from_numpy(x.dip).to(dev), e0=x.e0)
               for x in wl.waves]
     dE = torch.from_numpy(E).to(dev)
     idx = np.linspace(0, E.size - 1, 6).astype(int)

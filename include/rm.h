@@ -98,6 +98,12 @@ typedef struct {
                             closed channels.  The paper's targets are ions (B II, Ca II,
                             Fe III ...); it gives no outer-region formulas, so these are the
                             standard ones.  Repulsive fields (z < 0) are rejected. */
+  const double* dip;     /* [N] bound-free dipole vector d_k = <psi_k|D|Psi_0> between the inner-region
+                            eigenstates of this (final) symmetry and the initial bound state, or NULL
+                            (no photoionisation).  With a dipole vector the pole sum carries it as
+                            one more row of W, giving y_i(E) = (1/2a) sum_k w_ik d_k / (E_k - E). */
+  double e0;             /* initial bound-state energy (Ry, same origin as the thresholds); the photon
+                            energy is omega = E - e0.  Ignored without dip. */
 } rm_wave;
 
 typedef struct {
@@ -174,6 +180,21 @@ rm_status_t rm_results(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, dou
                        double* sig_tot, double* sig_sel, int32_t* n_open, uint8_t* flags,
                        int32_t mem);
 
+/* Photoionisation cross sections of one wave (it must carry a dipole vector) for [e0, e1),
+   length form, standard R-matrix reading (the paper names its photoionisation module but prints
+   no formulas): from the K-normalised solutions' boundary derivatives
+   F'_im = s'_m delta_im + Lambda_i Y_im, the amplitudes M^K_m = sqrt(2) a sum_i F'_im y_i(E),
+   the incoming-wave amplitudes M^- = (I + iK)^-1 M^K, and
+   sigma_PI,m = (4 pi alpha / 3) (E - e0) |M^-_m|^2 (a0^2; initial statistical weight 1;
+   s, c = k^-1/2 sin, cos i.e. sqrt(pi) times per-Rydberg energy normalisation).
+   sig_pi[(e1-e0)] total, sig_pi_ch[(e1-e0)*n] per final channel; either may be NULL. */
+rm_status_t rm_photo(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, double* sig_pi,
+                     double* sig_pi_ch, int32_t mem);
+
+/* Photoionisation results of the last rm_run (waves with a dipole vector), as rm_photo. */
+rm_status_t rm_results_photo(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, double* sig_pi,
+                             double* sig_pi_ch, int32_t mem);
+
 /* Wait for the plan's stream; reports device-side error words. */
 rm_status_t rm_sync(rm_plan_t plan);
 
@@ -231,7 +252,7 @@ const char* rm_last_error(void);
  * ascending and finite.  The work is enqueued on cuda_stream (NULL = default
  * stream) and the call returns without waiting.
  * Sizes: n_ch is limited by the scratch (one solve workspace of about
- * 4 n_ch^2 + 2 n_ch n_sel doubles must fit); larger n_ch returns RM_ERR_ARG.
+ * 4 n_ch^2 + 2 n_ch (n_sel + 1) doubles must fit); larger n_ch returns RM_ERR_ARG.
  * Set-up: the first call on each device looks up the scratch array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the one scratch array and every call overwrites

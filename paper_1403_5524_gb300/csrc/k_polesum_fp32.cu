@@ -109,9 +109,9 @@ __global__ void __launch_bounds__(NT) polesum_fp32_kernel(
 cudaError_t launch_polesum_fp32(const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s) {
   if (ne <= 0) return cudaSuccess;
   const SplitDev& sd = w.split;
-  const int nb = (w.n + CB - 1) / CB;
+  const int nb = (w.nR + CB - 1) / CB;  // all rows of the pole-sum operand (dipole row included)
   dim3 grid(nb * (nb + 1) / 2, (ne + ET - 1) / ET);
-  polesum_fp32_kernel<<<grid, NT, 0, s>>>(sd.omega, w.n, w.Npad, w.N, sd.pol, sd.Eh + e0, sd.El + e0, sd.klo + e0,
+  polesum_fp32_kernel<<<grid, NT, 0, s>>>(sd.omega, w.nR, w.Npad, w.N, sd.pol, sd.Eh + e0, sd.El + e0, sd.klo + e0,
                                           sd.khi + e0, sd.sigma, ne, 1.0 / (2.0 * w.a), R);
   return cudaGetLastError();
 }

@@ -103,9 +103,9 @@ __global__ void __launch_bounds__(NT) polesum_fp64_kernel(
 
 cudaError_t launch_polesum_fp64(const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s) {
   if (ne <= 0) return cudaSuccess;
-  const int nb = (w.n + CB - 1) / CB;
+  const int nb = (w.nR + CB - 1) / CB;  // all rows of the pole-sum operand (dipole row included)
   dim3 grid(nb * (nb + 1) / 2, (ne + ET - 1) / ET);
-  polesum_fp64_kernel<<<grid, NT, 0, s>>>(w.W, w.n, w.Npad, w.N, w.poles, w.E + e0, ne,
+  polesum_fp64_kernel<<<grid, NT, 0, s>>>(w.W, w.nR, w.Npad, w.N, w.poles, w.E + e0, ne,
                                           1.0 / (2.0 * w.a), R);
   return cudaGetLastError();
 }

@@ -786,17 +786,18 @@ std::vector<int2> split_tiles(int n) {
 
 cudaError_t split_prepare(const Plan& p, WaveDev& w, cudaStream_t s) {
   SplitDev& sd = w.split;
-  prep_omega_kernel<<<w.n, 256, 0, s>>>(w.W, w.n, w.N, w.Npad, sd.sigma, sd.omega);
+  // every row of the pole-sum operand (the dipole row, when present, is row 0)
+  prep_omega_kernel<<<w.nR, 256, 0, s>>>(w.W, w.nR, w.N, w.Npad, sd.sigma, sd.omega);
   prep_pol_kernel<<<(w.Npad + 255) / 256, 256, 0, s>>>(w.poles, w.N, w.Npad, sd.pol);
-  const int64_t np = (int64_t)w.n * (w.n + 1) / 2;
-  prep_pairs_kernel<<<(unsigned)((np + 7) / 8), 256, 0, s>>>(sd.omega, sd.sigma, w.n, w.N, w.Npad, 1.0 / (2.0 * w.a),
+  const int64_t np = w.npR();
+  prep_pairs_kernel<<<(unsigned)((np + 7) / 8), 256, 0, s>>>(sd.omega, sd.sigma, w.nR, w.N, w.Npad, 1.0 / (2.0 * w.a),
                                                              sd.mult_p, sd.f_p);
   if (p.n_e > 0)
     prep_energy_split_kernel<<<(unsigned)((p.n_e + 255) / 256), 256, 0, s>>>(
         w.E, p.n_e, w.poles, w.N, p.delta, sd.klo, sd.khi, sd.tau, sd.mult_e, sd.Eh, sd.El);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (!encode_2d_f32(&sd.map_omega, sd.omega, (uint64_t)w.Npad, (uint64_t)(2 * w.n), KS, 16))
+  if (!encode_2d_f32(&sd.map_omega, sd.omega, (uint64_t)w.Npad, (uint64_t)(2 * w.nR), KS, 16))
     return cudaErrorInvalidValue;
   if (!encode_2d_f32(&sd.map_pol, sd.pol, (uint64_t)w.Npad, 2, KS, 2)) return cudaErrorInvalidValue;
   return cudaSuccess;
@@ -815,7 +816,7 @@ cudaError_t launch_polesum_split(const Plan& p, const WaveDev& w, int64_t e0, in
   g.Eh = sd.Eh;
   g.El = sd.El;
   g.tiles = sd.tiles;
-  g.n = w.n;
+  g.n = w.nR;
   g.N = w.N;
   g.nK = w.Npad / KS;
   g.f16 = p.prec == RM_PREC_SPLIT_FP16 ? 1 : 0;
@@ -834,7 +835,7 @@ size_t near_smem_bytes(int n) { return ((size_t)n * (NKP + 1) + NEB * NKP) * siz
 
 cudaError_t launch_near(const Plan& p, const WaveDev& w, int64_t e0, int ne, double* R, cudaStream_t s) {
   if (ne <= 0) return cudaSuccess;
-  const size_t smem = near_smem_bytes(w.n);
+  const size_t smem = near_smem_bytes(w.nR);
   cudaError_t err = cudaFuncSetAttribute(near_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int blocks = (ne + NEB - 1) / NEB;
@@ -842,7 +843,7 @@ cudaError_t launch_near(const Plan& p, const WaveDev& w, int64_t e0, int ne, dou
   if (splits < 1) splits = 1;
   if (splits > 64) splits = 64;
   dim3 grid(blocks, splits);
-  near_kernel<<<grid, NNT, smem, s>>>(w.W, w.n, w.Npad, w.poles, w.E + e0, w.split.klo + e0, w.split.khi + e0, ne,
+  near_kernel<<<grid, NNT, smem, s>>>(w.W, w.nR, w.Npad, w.poles, w.E + e0, w.split.klo + e0, w.split.khi + e0, ne,
                                       1.0 / (2.0 * w.a), splits, R);
   return cudaGetLastError();
 }
@@ -896,7 +897,7 @@ cudaError_t group_setup_split(Plan& p) {
     a.Eh = sd.Eh;
     a.El = sd.El;
     a.tiles = nullptr;
-    a.n = w.n;
+    a.n = w.nR;
     a.N = w.N;
     a.nK = w.Npad / KS;
     a.f16 = p.prec == RM_PREC_SPLIT_FP16 ? 1 : 0;
@@ -907,11 +908,11 @@ cudaError_t group_setup_split(Plan& p) {
     tw[g] = a;
     maps[2 * g] = sd.map_omega;
     maps[2 * g + 1] = sd.map_pol;
-    const std::vector<int2> wt = split_tiles(w.n);
+    const std::vector<int2> wt = split_tiles(w.nR);
     for (const int2& t : wt) tiles.push_back(make_int4(g, t.x, t.y, w.Npad / KS));
     // pad to a multiple of the cluster width with empty tiles (i-block past the last channel)
-    for (size_t q = wt.size(); q % G.tc_cx != 0; ++q) tiles.push_back(make_int4(g, (w.n + 7) / 8, 0, w.Npad / KS));
-    nw[g] = NearWave{w.W, w.poles, w.E, sd.klo, sd.khi, G.R[g], 1.0 / (2.0 * w.a), w.n, w.Npad};
+    for (size_t q = wt.size(); q % G.tc_cx != 0; ++q) tiles.push_back(make_int4(g, (w.nR + 7) / 8, 0, w.Npad / KS));
+    nw[g] = NearWave{w.W, w.poles, w.E, sd.klo, sd.khi, G.R[g], 1.0 / (2.0 * w.a), w.nR, w.Npad};
     for (int e = 0; e < G.chunk; e += NEB) jobs.push_back(make_int2(g, e));
   }
   // longest K loop first, so the last wave of CTAs holds the short tiles; the sort is
@@ -953,7 +954,7 @@ cudaError_t group_setup_split(Plan& p) {
     return err;
   if ((err = set_tc_smem()) != cudaSuccess) return err;
   return cudaFuncSetAttribute(near_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)near_smem_bytes(p.n_max));
+                              (int)near_smem_bytes(p.nR_max));
 }
 
 bool polesum_cluster_ok(int cx, int cy) {
@@ -1006,7 +1007,7 @@ cudaError_t launch_near_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t 
   if (ne <= 0) return cudaSuccess;
   const GroupDev& G = p.grp;
   dim3 grid(G.n_near_jobs, G.near_splits);
-  near_grouped_kernel<<<grid, NNT, near_smem_bytes(p.n_max), s>>>(reinterpret_cast<const NearWave*>(G.near_waves),
+  near_grouped_kernel<<<grid, NNT, near_smem_bytes(p.nR_max), s>>>(reinterpret_cast<const NearWave*>(G.near_waves),
                                                                   G.near_jobs, e0, ne, G.near_splits);
   return cudaGetLastError();
 }

@@ -9,10 +9,10 @@ __device__ inline void set_err(int32_t* err, int code) { atomicMax(err, code); }
 
 __global__ void validate_kernel(const int32_t* __restrict__ l, const double* __restrict__ thr,
                                 int n, const double* __restrict__ poles, int N,
-                                const double* __restrict__ W, int Npad,
+                                const double* __restrict__ W, int nW, int Npad,
                                 const double* __restrict__ E, int64_t n_e, int32_t* err) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * N; t += stride) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nW * N; t += stride) {
     const int i = (int)(t / N), k = (int)(t % N);
     if (!isfinite(W[(int64_t)i * Npad + k])) set_err(err, RM_ERR_ARG);
   }
@@ -72,7 +72,7 @@ __global__ void prep_kernel(const double* __restrict__ energies, int64_t n_e,
 
 cudaError_t launch_validate(const WaveDev& w, int N_real, const double* energies, int64_t n_e,
                             int32_t* err_word, cudaStream_t s) {
-  validate_kernel<<<152 * 2, 256, 0, s>>>(w.l, w.thr, w.n, w.poles, N_real, w.W, w.Npad, energies,
+  validate_kernel<<<152 * 2, 256, 0, s>>>(w.l, w.thr, w.n, w.poles, N_real, w.W, w.nR, w.Npad, energies,
                                          n_e, err_word);
   return cudaGetLastError();
 }

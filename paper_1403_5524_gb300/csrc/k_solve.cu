@@ -14,6 +14,14 @@
 // 2iK(I - iK)^-1), sigma_{sel_q -> j} = (pi / k^2) |T_{j,sel_q}|^2, and the
 // eigenphase sum -arg det(I - iK) from the pivots and the interchange count.
 //
+// Photoionisation (a wave whose pole sum carries the dipole vector as row 0,
+// so that R holds y_i = (1/2a) sum_k w_ik d_k / (E_k - E) ahead of the channel
+// block): the boundary derivatives of the K-normalised solutions are
+// F'_im = s'_m delta_im + Lambda_i Y_im, the amplitudes
+// M^K_m = sqrt(2) a sum_i F'_im y_i, and M^K is one more right-hand side of
+// the complex LU: |((I - iK)^-1 M^K)_m| = |M^-_m| with M^- = (I + iK)^-1 M^K
+// (K real symmetric), sigma_PI,m = (4 pi alpha / 3) (E - E_0) |M^-_m|^2.
+//
 // The blocked LU keeps a 16-column panel in shared memory, factors it with
 // partial pivoting, and updates the columns to its right in 64-column tiles
 // (row interchanges, triangular solve with the unit-lower panel block, then
@@ -329,7 +337,11 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
 struct SolveArgs {
   int n, n_sel;
   double a;
-  const double* R;  // [ne * np]
+  const double* R;  // [ne * npR]: per energy [dipole row (y at 1..n)], then the n x n channel block
+  int64_t npR;      // packed entries per energy
+  int64_t roff;     // offset of the channel block (0 without a dipole row)
+  int dip;          // 1: photoionisation amplitudes from y
+  double e0;        // initial bound-state energy (Ry)
   const double* asym;
   int64_t ld_asym;  // stride between lam, s, sp, c blocks
   const double* E;  // [ne]
@@ -363,12 +375,12 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   double* tile_d = reinterpret_cast<double*>(tile_b);
   double* A = g.slot + (int64_t)blockIdx.x * g.slot_doubles;
   cplx* C = reinterpret_cast<cplx*>(A + (int64_t)n * g.ldR);
-  const int64_t np = (int64_t)n * (n + 1) / 2;
   const int t = threadIdx.x;
 
   const int no = g.n_open_in[e];
   uint8_t fl = g.flags_in[e];
-  const double* Re = g.R + (int64_t)e * np;
+  const double* Re = g.R + (int64_t)e * g.npR + g.roff;
+  const double* ye = g.R + (int64_t)e * g.npR + 1;  // dipole vector y_i (rows with a dipole)
   const double* lam = g.asym + 0 * g.ld_asym + (int64_t)e * n;
   const double* s = g.asym + 1 * g.ld_asym + (int64_t)e * n;
   const double* sp = g.asym + 2 * g.ld_asym + (int64_t)e * n;
@@ -388,6 +400,9 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     if (g.out.sig_sel)
       for (int64_t idx = t; idx < (int64_t)g.n_sel * n; idx += NT)
         g.out.sig_sel[(int64_t)e * g.n_sel * n + idx] = 0.0;
+    if (g.out.pi_tot && t == 0) g.out.pi_tot[e] = 0.0;
+    if (g.out.pi_ch)
+      for (int j = t; j < n; j += NT) g.out.pi_ch[(int64_t)e * n + j] = 0.0;
     __syncthreads();
     return;
   }
@@ -437,18 +452,31 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     __syncthreads();
     return;
   }
+  // ---------------------------------------------------- dipole amplitudes
+  const bool photo = g.dip && (g.out.pi_tot || g.out.pi_ch);
+  double* MK = tile_d;  // the tile area is free between the two LUs
+  if (photo) {
+    for (int m = t; m < no; m += NT) {
+      double acc = sp[m] * ye[m];
+      for (int i = 0; i < n; ++i) acc = fma(lam[i] * A[(int64_t)i * g.ldR + n + m], ye[i], acc);
+      MK[m] = M_SQRT2 * g.a * acc;
+    }
+    __syncthreads();  // the complex build below reads every M^K_i (photo is uniform in the block)
+  }
   // --------------------------------------------------------------- S-step
   const int r = g.n_sel;
-  const int mc = no + r;
+  const int mc = no + r + (photo ? 1 : 0);
   for (int64_t idx = t; idx < (int64_t)no * mc; idx += NT) {
     const int i = (int)(idx / mc), j = (int)(idx % mc);
     cplx v;
     if (j < no) {
       const double kij = A[(int64_t)i * g.ldR + n + j] * rc[i];
       v = cplx{(i == j) ? 1.0 : 0.0, -kij};
-    } else {
+    } else if (j < no + r) {
       const int sq = g.sel[j - no];
       v = cplx{(sq < no) ? A[(int64_t)i * g.ldR + n + sq] * rc[i] : 0.0, 0.0};
+    } else {
+      v = cplx{MK[i], 0.0};
     }
     C[(int64_t)i * g.ldC + j] = v;
   }
@@ -492,6 +520,31 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     }
     __syncthreads();
   }
+  if (photo) {
+    // sigma_PI,j = (4 pi alpha / 3) omega |X_j|^2, X = (I - iK)^-1 M^K
+    const double pref = (4.0 * M_PI * 7.2973525693e-3 / 3.0) * (g.E[e] - g.e0);
+    double part = 0.0;
+    for (int j = t; j < n; j += NT) {
+      double v = 0.0;
+      if (j < no) {
+        const cplx x = C[(int64_t)j * g.ldC + no + r];
+        v = pref * (x.re * x.re + x.im * x.im);
+      }
+      if (s_singular) v = NAN;
+      if (g.out.pi_ch) g.out.pi_ch[(int64_t)e * n + j] = v;
+      part += v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    if ((t & 31) == 0) red.v[t >> 5] = part;
+    __syncthreads();
+    if (t == 0 && g.out.pi_tot) {
+      double tot = 0.0;
+      for (int w = 0; w < NWARP; ++w) tot += red.v[w];
+      g.out.pi_tot[e] = tot;
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
@@ -529,6 +582,8 @@ __global__ void __launch_bounds__(NT, 2) solve_grouped_kernel(const SolveArgs* _
     if (g.out.sig_sel) g.out.sig_sel += e_begin * g.n_sel * g.n;
     if (g.out.flags) g.out.flags += e_begin;
     if (g.out.n_open) g.out.n_open += e_begin;
+    if (g.out.pi_tot) g.out.pi_tot += e_begin;
+    if (g.out.pi_ch) g.out.pi_ch += e_begin * g.n;
     g.ne = ne;
     solve_energy(g, un.y, smem_raw, red, s_acc);
   }
@@ -568,6 +623,10 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   g.n_sel = p.n_sel;
   g.a = w.a;
   g.R = R;
+  g.npR = w.npR();
+  g.roff = w.roff();
+  g.dip = w.dip ? 1 : 0;
+  g.e0 = w.e0;
   g.asym = asym;
   g.ld_asym = ld_chunk;
   g.E = w.E + e0;
@@ -579,7 +638,7 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   g.slot = p.slot;
   g.slot_doubles = p.slot_doubles;
   g.ldR = 2 * p.n_max;
-  g.ldC = p.n_max + p.n_sel;
+  g.ldC = p.n_max + p.n_sel + 1;  // + the dipole right-hand side
   g.out = out;
   const size_t smem = solve_smem_bytes(p.n_max);
   cudaError_t err = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -599,6 +658,10 @@ cudaError_t group_setup_solve(Plan& p) {
     a.n_sel = p.n_sel;
     a.a = w.a;
     a.R = G.R[g];
+    a.npR = w.npR();
+    a.roff = w.roff();
+    a.dip = w.dip ? 1 : 0;
+    a.e0 = w.e0;
     a.asym = G.asym[g];
     a.ld_asym = (int64_t)G.chunk * w.n;
     a.E = w.E;
@@ -610,12 +673,14 @@ cudaError_t group_setup_solve(Plan& p) {
     a.slot = p.slot;
     a.slot_doubles = p.slot_doubles;
     a.ldR = 2 * p.n_max;
-    a.ldC = p.n_max + p.n_sel;
+    a.ldC = p.n_max + p.n_sel + 1;
     a.out = SolveOut();
     a.out.eta = w.eta;
     a.out.sig_tot = w.sig_tot;
     a.out.sig_sel = w.sig_sel;
     a.out.flags = w.flags;
+    a.out.pi_tot = w.pi_tot;
+    a.out.pi_ch = w.pi_ch;
     a.out.do_xsec = true;
     h[g] = a;
   }

@@ -55,6 +55,7 @@ void free_plan(Plan* p) {
   for (auto& w : p->waves) {
     dfree(w.l); dfree(w.thr); dfree(w.poles); dfree(w.W); dfree(w.E); dfree(w.flags0);
     dfree(w.n_open); dfree(w.eta); dfree(w.sig_tot); dfree(w.sig_sel); dfree(w.flags);
+    dfree(w.pi_tot); dfree(w.pi_ch);
     SplitDev& sd = w.split;
     dfree(sd.omega); dfree(sd.pol); dfree(sd.sigma); dfree(sd.mult_p); dfree(sd.f_p); dfree(sd.klo);
     dfree(sd.khi); dfree(sd.tau); dfree(sd.mult_e); dfree(sd.Eh); dfree(sd.El); dfree(sd.tiles);
@@ -90,6 +91,7 @@ rm_status_t check_wave_args(const rm_wave& w, int idx) {
   if (!(w.a > 0.0) || !(w.a < 1e300)) return fail(RM_ERR_ARG, tag + "radius a must be finite and > 0");
   if (!(w.z >= 0.0) || !(w.z < 1e300)) return fail(RM_ERR_ARG, tag + "charge z must be finite and >= 0");
   if (!w.l || !w.thresh || !w.pole_E || !w.W) return fail(RM_ERR_ARG, tag + "null input pointer");
+  if (w.dip && !(w.e0 > -1e300 && w.e0 < 1e300)) return fail(RM_ERR_ARG, tag + "e0 must be finite");
   return RM_OK;
 }
 
@@ -100,9 +102,12 @@ rm_status_t upload_wave(Plan* p, WaveDev& d, const rm_wave& w, int32_t mem) {
   RM_CUDA(cudaMemcpyAsync(d.l, w.l, sizeof(int32_t) * d.n, k, s), "copy l");
   RM_CUDA(cudaMemcpyAsync(d.thr, w.thresh, sizeof(double) * d.n, k, s), "copy thresholds");
   RM_CUDA(cudaMemcpyAsync(d.poles, w.pole_E, sizeof(double) * d.N, k, s), "copy poles");
-  RM_CUDA(cudaMemsetAsync(d.W, 0, sizeof(double) * (size_t)d.n * d.Npad, s), "clear W");
-  RM_CUDA(cudaMemcpy2DAsync(d.W, sizeof(double) * d.Npad, w.W, sizeof(double) * d.N,
+  // pole-sum operand: [dipole row,] then the n channel rows, each padded to Npad
+  RM_CUDA(cudaMemsetAsync(d.W, 0, sizeof(double) * (size_t)d.nR * d.Npad, s), "clear W");
+  if (d.dip) RM_CUDA(cudaMemcpyAsync(d.W, w.dip, sizeof(double) * d.N, k, s), "copy dipole vector");
+  RM_CUDA(cudaMemcpy2DAsync(d.W + (d.dip ? d.Npad : 0), sizeof(double) * d.Npad, w.W, sizeof(double) * d.N,
                             sizeof(double) * d.N, d.n, k, s), "copy W");
+  d.e0 = w.e0;
   if (mem == RM_MEM_HOST) {
     int32_t lmax = 0;
     for (int i = 0; i < d.n; ++i) lmax = w.l[i] > lmax ? w.l[i] : lmax;
@@ -264,9 +269,14 @@ rm_status_t run_range(Plan* p, int32_t wave, int64_t e0, int64_t e1, const Range
   for (int64_t c0 = e0; c0 < e1; c0 += p->chunk) {
     const int ne = (int)((e1 - c0) < p->chunk ? (e1 - c0) : p->chunk);
     const int64_t off = c0 - e0;
-    double* R = o.R ? o.R + off * np : p->Rbuf;
+    // with a dipole row the pole sum's rows are (dipole, channels): compute into the
+    // workspace and hand out the channel block
+    double* R = (o.R && !w.dip) ? o.R + off * np : p->Rbuf;
     rm_status_t st = polesum_chunk(p, w, c0, ne, R);
     if (st != RM_OK) return st;
+    if (o.R && w.dip)
+      RM_CUDA(cudaMemcpy2DAsync(o.R + off * np, sizeof(double) * np, R + w.roff(), sizeof(double) * w.npR(),
+                                sizeof(double) * np, ne, cudaMemcpyDeviceToDevice, p->stream), "channel block of R");
     if (!o.need_solve) continue;
     const int ld = p->chunk * p->n_max;
     {
@@ -280,6 +290,8 @@ rm_status_t run_range(Plan* p, int32_t wave, int64_t e0, int64_t e1, const Range
     if (so.sig_sel) so.sig_sel += off * p->n_sel * w.n;
     if (so.flags) so.flags += off;
     if (so.n_open) so.n_open += off;
+    if (so.pi_tot) so.pi_tot += off;
+    if (so.pi_ch) so.pi_ch += off * w.n;
     {
       Prof pr(p, RM_KERNEL_SOLVE);
       RM_CUDA(launch_solve(*p, w, c0, ne, R, p->asym, ld, so, p->stream), "solve kernel");
@@ -396,7 +408,7 @@ rm_status_t build_graph(Plan* p) {
 std::string tune_key(const Plan* p) {
   std::string k = "rm2 prec=" + std::to_string(p->prec) + " ne=" + std::to_string(p->n_e) +
                   " sel=" + std::to_string(p->n_sel);
-  for (const auto& w : p->waves) k += " " + std::to_string(w.n) + "x" + std::to_string(w.N);
+  for (const auto& w : p->waves) k += " " + std::to_string(w.nR) + "x" + std::to_string(w.N);
   return k;
 }
 
@@ -613,7 +625,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     std::memcpy(p->sel, sel, sizeof(sel));
     p->sm_count = prop.multiProcessorCount;
     p->waves.resize(n_waves);
-    int n_max = 0;
+    int n_max = 0, nR_max = 0;
     int64_t np_max = 0;
     rm_status_t st = RM_OK;
     for (int g = 0; g < n_waves && st == RM_OK; ++g) {
@@ -623,13 +635,17 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       d.Npad = (d.N + 63) / 64 * 64;
       d.a = waves[g].a;
       d.z = waves[g].z;
+      d.dip = waves[g].dip != nullptr;
+      d.e0 = waves[g].e0;
+      d.nR = d.n + (d.dip ? 1 : 0);
       n_max = d.n > n_max ? d.n : n_max;
-      const int64_t np = (int64_t)d.n * (d.n + 1) / 2;
+      nR_max = d.nR > nR_max ? d.nR : nR_max;
+      const int64_t np = d.npR();
       np_max = np > np_max ? np : np_max;
       if ((st = dalloc(p, &d.l, d.n)) != RM_OK) break;
       if ((st = dalloc(p, &d.thr, d.n)) != RM_OK) break;
       if ((st = dalloc(p, &d.poles, d.Npad)) != RM_OK) break;
-      if ((st = dalloc(p, &d.W, (int64_t)d.n * d.Npad)) != RM_OK) break;
+      if ((st = dalloc(p, &d.W, (int64_t)d.nR * d.Npad)) != RM_OK) break;
       if ((st = dalloc(p, &d.E, n_e)) != RM_OK) break;
       if ((st = dalloc(p, &d.flags0, n_e)) != RM_OK) break;
       if ((st = dalloc(p, &d.n_open, n_e)) != RM_OK) break;
@@ -637,11 +653,13 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if ((st = dalloc(p, &d.sig_tot, n_e * n_sel)) != RM_OK) break;
       if ((st = dalloc(p, &d.sig_sel, n_e * n_sel * d.n)) != RM_OK) break;
       if ((st = dalloc(p, &d.flags, n_e)) != RM_OK) break;
+      if (d.dip && (st = dalloc(p, &d.pi_tot, n_e)) != RM_OK) break;
+      if (d.dip && (st = dalloc(p, &d.pi_ch, n_e * d.n)) != RM_OK) break;
       if (is_split_like(o.prec)) {
         SplitDev& sd = d.split;
-        if ((st = dalloc(p, &sd.omega, 2ll * d.n * d.Npad)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.omega, 2ll * d.nR * d.Npad)) != RM_OK) break;
         if ((st = dalloc(p, &sd.pol, 2ll * d.Npad)) != RM_OK) break;
-        if ((st = dalloc(p, &sd.sigma, d.n)) != RM_OK) break;
+        if ((st = dalloc(p, &sd.sigma, d.nR)) != RM_OK) break;
         if ((st = dalloc(p, &sd.mult_p, np)) != RM_OK) break;
         if ((st = dalloc(p, &sd.f_p, np)) != RM_OK) break;
         if ((st = dalloc(p, &sd.klo, n_e)) != RM_OK) break;
@@ -650,7 +668,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
         if ((st = dalloc(p, &sd.mult_e, n_e)) != RM_OK) break;
         if ((st = dalloc(p, &sd.Eh, n_e)) != RM_OK) break;
         if ((st = dalloc(p, &sd.El, n_e)) != RM_OK) break;
-        std::vector<int2> tl = split_tiles(d.n);
+        std::vector<int2> tl = split_tiles(d.nR);
         sd.n_tiles = (int)tl.size();
         if ((st = dalloc(p, &sd.tiles, sd.n_tiles)) != RM_OK) break;
         if (cudaMemcpy(sd.tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -660,6 +678,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       }
     }
     p->n_max = n_max;
+    p->nR_max = nR_max;
     if (st == RM_OK) {
       int chunk = o.chunk;
       if (chunk == 0) {
@@ -672,7 +691,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if (chunk < 1) chunk = 1;
       p->chunk = chunk;
       p->solve_slots = p->sm_count * solve_blocks_per_sm(n_max);
-      p->slot_doubles = solve_slot_doubles(n_max, n_sel);
+      p->slot_doubles = solve_slot_doubles(n_max, n_sel + 1);  // + the dipole right-hand side
       if (st == RM_OK) st = dalloc(p, &p->energies, n_e);
       if (st == RM_OK) st = dalloc(p, &p->sel_dev, n_sel);
       if (st == RM_OK) st = dalloc(p, &p->Rbuf, (int64_t)chunk * np_max);
@@ -683,7 +702,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       // fits min(24 GiB, a third of free device memory): one launch per kernel
       // and sweep, no chunk tails; otherwise chunks (autotuned when asked).
       int64_t per_e = 0;
-      for (const auto& w : p->waves) per_e += (int64_t)w.n * (w.n + 1) / 2 + 4ll * w.n;
+      for (const auto& w : p->waves) per_e += w.npR() + 4ll * w.n;
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 2ull << 30; }
       int64_t budget = (int64_t)(free_b / 3);
@@ -698,7 +717,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       p->grp.asym.assign(n_waves, nullptr);
       for (int g = 0; g < n_waves && st == RM_OK; ++g) {
         const WaveDev& d = p->waves[g];
-        st = dalloc(p, &p->grp.R[g], cmax * ((int64_t)d.n * (d.n + 1) / 2));
+        st = dalloc(p, &p->grp.R[g], cmax * d.npR());
         if (st == RM_OK) st = dalloc(p, &p->grp.asym[g], 4ll * cmax * d.n);
       }
     }
@@ -710,7 +729,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       st = fail(RM_ERR_ARG, "n_ch too large for the solve kernel's shared memory");
     if (st == RM_OK && is_split_like(o.prec) &&
         (polesum_tc_smem_bytes() > (size_t)prop.sharedMemPerBlockOptin ||
-         near_smem_bytes(n_max) > (size_t)prop.sharedMemPerBlockOptin))
+         near_smem_bytes(nR_max) > (size_t)prop.sharedMemPerBlockOptin))
       st = fail(RM_ERR_ARG, "split-precision kernels do not fit this device's shared memory");
     if (st == RM_OK && is_split_like(o.prec)) {
       // explicit cluster shape (a missing dimension is 1); automatic: the first
@@ -760,8 +779,9 @@ rm_status_t rm_plan_load(rm_plan_t h, const rm_wave* waves, const double* energi
     for (int g = 0; g < p->n_waves; ++g) {
       rm_status_t st = check_wave_args(waves[g], g);
       if (st != RM_OK) return st;
-      if (waves[g].n_ch != p->waves[g].n || waves[g].n_poles != p->waves[g].N)
-        return fail(RM_ERR_ARG, "wave shape differs from the plan's");
+      if (waves[g].n_ch != p->waves[g].n || waves[g].n_poles != p->waves[g].N ||
+          (waves[g].dip != nullptr) != p->waves[g].dip)
+        return fail(RM_ERR_ARG, "wave shape (or dipole presence) differs from the plan's");
       p->waves[g].a = waves[g].a;
       p->waves[g].z = waves[g].z;
     }
@@ -790,8 +810,9 @@ rm_status_t rm_rmatrix(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double
       RangeOut o;  // into Rbuf
       st = run_range(p, wave, c0, c1, o);
       if (st != RM_OK) return st;
-      RM_CUDA(cudaMemcpyAsync(R_packed + (c0 - e0) * np, p->Rbuf, sizeof(double) * (size_t)((c1 - c0) * np),
-                              cudaMemcpyDeviceToHost, p->stream), "copy R");
+      RM_CUDA(cudaMemcpy2DAsync(R_packed + (c0 - e0) * np, sizeof(double) * np, p->Rbuf + w.roff(),
+                                sizeof(double) * w.npR(), sizeof(double) * np, c1 - c0, cudaMemcpyDeviceToHost,
+                                p->stream), "copy R");
       RM_CUDA(cudaStreamSynchronize(p->stream), "rm_rmatrix");
     }
     return check_err_word(p);
@@ -880,6 +901,63 @@ rm_status_t rm_run(rm_plan_t h) {
       p->launches += p->grp.graph_kernels;
     }
     p->ran = true;
+    return RM_OK;
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
+rm_status_t rm_photo(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* sig_pi, double* sig_pi_ch,
+                     int32_t mem) {
+  try {
+    Plan* p = as_plan(h);
+    rm_status_t st = check_range(p, wave, e0, e1);
+    if (st != RM_OK) return st;
+    if (!valid_mem(mem)) return fail(RM_ERR_ARG, "bad memory space");
+    const WaveDev& w = p->waves[wave];
+    if (!w.dip) return fail(RM_ERR_ARG, "wave has no dipole vector");
+    const int64_t ne = e1 - e0;
+    Scratch s1, s2;
+    RangeOut o;
+    o.need_solve = true;
+    o.so.do_xsec = true;
+    if ((st = out_buf(p, sig_pi, ne, mem, s1, &o.so.pi_tot)) != RM_OK) return st;
+    if ((st = out_buf(p, sig_pi_ch, ne * w.n, mem, s2, &o.so.pi_ch)) != RM_OK) return st;
+    if ((st = run_range(p, wave, e0, e1, o)) != RM_OK) return st;
+    if ((st = copy_back(p, sig_pi, o.so.pi_tot, ne, mem)) != RM_OK) return st;
+    if ((st = copy_back(p, sig_pi_ch, o.so.pi_ch, ne * w.n, mem)) != RM_OK) return st;
+    if (mem == RM_MEM_HOST) {
+      RM_CUDA(cudaStreamSynchronize(p->stream), "rm_photo");
+      return check_err_word(p);
+    }
+    return RM_OK;
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
+rm_status_t rm_results_photo(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* sig_pi,
+                             double* sig_pi_ch, int32_t mem) {
+  try {
+    Plan* p = as_plan(h);
+    rm_status_t st = check_range(p, wave, e0, e1);
+    if (st != RM_OK) return st;
+    if (!valid_mem(mem)) return fail(RM_ERR_ARG, "bad memory space");
+    if (!p->ran) return fail(RM_ERR_STATE, "rm_results_photo before rm_run");
+    const WaveDev& w = p->waves[wave];
+    if (!w.dip) return fail(RM_ERR_ARG, "wave has no dipole vector");
+    const int64_t ne = e1 - e0;
+    const cudaMemcpyKind k = kind_out(mem);
+    if (ne > 0) {
+      if (sig_pi) RM_CUDA(cudaMemcpyAsync(sig_pi, w.pi_tot + e0, sizeof(double) * ne, k, p->stream), "copy sig_pi");
+      if (sig_pi_ch)
+        RM_CUDA(cudaMemcpyAsync(sig_pi_ch, w.pi_ch + e0 * w.n, sizeof(double) * ne * w.n, k, p->stream),
+                "copy sig_pi_ch");
+    }
+    if (mem == RM_MEM_HOST) {
+      RM_CUDA(cudaStreamSynchronize(p->stream), "rm_results_photo");
+      return check_err_word(p);
+    }
     return RM_OK;
   } catch (...) {
     return fail(RM_ERR_NOMEM, "unexpected host exception");

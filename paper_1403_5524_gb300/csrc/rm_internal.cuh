@@ -54,6 +54,9 @@ struct SplitDev {
 
 struct WaveDev {
   int n = 0;         // channels
+  int nR = 0;        // rows of the pole-sum operand: n, or n + 1 with the dipole vector as row 0
+  bool dip = false;  // photoionisation: row 0 of W is the dipole vector d_k
+  double e0 = 0.0;   // initial bound-state energy (Ry)
   int N = 0;         // poles
   int Npad = 0;      // poles rounded up for aligned tiles
   double a = 0.0;
@@ -71,7 +74,13 @@ struct WaveDev {
   double* sig_tot = nullptr;  // [n_e * n_sel]
   double* sig_sel = nullptr;  // [n_e * n_sel * n]
   uint8_t* flags = nullptr;   // [n_e]
+  double* pi_tot = nullptr;   // [n_e] photoionisation (waves with a dipole vector)
+  double* pi_ch = nullptr;    // [n_e * n]
   SplitDev split;
+  // packed entries of one energy's pole sum (nR x nR), and where the n x n
+  // channel block starts in them (after the dipole row's nR entries)
+  int64_t npR() const { return (int64_t)nR * (nR + 1) / 2; }
+  int64_t roff() const { return dip ? (int64_t)nR : 0; }
 };
 
 // Grouped (all waves in one launch per kernel) run of the sweep, captured in
@@ -113,6 +122,7 @@ struct Plan {
   int32_t* sel_dev = nullptr;
   int chunk = 0;
   int n_max = 0;
+  int nR_max = 0;   // largest pole-sum row count (n_ch + 1 with a dipole vector)
   int sm_count = 0;
   double* energies = nullptr;  // [n_e] raw mesh (device)
   std::vector<WaveDev> waves;
@@ -157,6 +167,8 @@ struct SolveOut {
   double* sig_sel = nullptr;  // optional [ne * n_sel * n]
   uint8_t* flags = nullptr;   // optional [ne]
   int32_t* n_open = nullptr;  // optional [ne]
+  double* pi_tot = nullptr;   // optional [ne] photoionisation (waves with a dipole vector)
+  double* pi_ch = nullptr;    // optional [ne * n]
   bool do_xsec = true;
 };
 cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, const double* R,

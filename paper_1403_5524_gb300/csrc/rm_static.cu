@@ -89,7 +89,7 @@ extern "C" rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_c
   // data, solve slots.  Chunk and slot counts shrink to fit; sizes that leave
   // no room for one slot are rejected.
   const int n = n_ch;
-  const int64_t slot_d = solve_slot_doubles(n, n_sel);
+  const int64_t slot_d = solve_slot_doubles(n, n_sel + 1);  // the solve's layout reserves a dipole column
   const size_t slot_b = (size_t)slot_d * sizeof(double);
   const size_t fixed = align256(sizeof(int32_t) * RM_MAX_SEL);
   int chunk = 256;
@@ -137,6 +137,7 @@ extern "C" rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_c
   p.slot_doubles = slot_d;
   WaveDev w;
   w.n = n;
+  w.nR = n;  // no dipole row: R is the caller's n x n packed block
   w.N = n_poles;
   w.a = a;
   w.l = const_cast<int32_t*>(l);

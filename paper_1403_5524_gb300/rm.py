@@ -26,7 +26,7 @@ PREC = {"fp64": RM_PREC_FP64, "split_bf16": RM_PREC_SPLIT_BF16, "split_fp16": RM
 EXPORTS = ["rm_options_default", "rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix",
            "rm_xsec", "rm_run", "rm_results", "rm_sync", "rm_plan_info", "rm_plan_launches",
            "rm_plan_destroy", "rm_status_str", "rm_last_error", "rm_profile_enable", "rm_profile_read",
-           "rm_plan_cluster"]
+           "rm_plan_cluster", "rm_photo", "rm_results_photo"]
 
 KERNELS = {"polesum_fp64": 0, "polesum_split": 1, "near": 2, "asym": 3, "solve": 4}
 
@@ -34,7 +34,7 @@ KERNELS = {"polesum_fp64": 0, "polesum_split": 1, "near": 2, "asym": 3, "solve":
 class rm_wave(C.Structure):
     _fields_ = [("n_ch", C.c_int32), ("n_poles", C.c_int32), ("a", C.c_double),
                 ("l", C.c_void_p), ("thresh", C.c_void_p), ("pole_E", C.c_void_p), ("W", C.c_void_p),
-                ("z", C.c_double)]
+                ("z", C.c_double), ("dip", C.c_void_p), ("e0", C.c_double)]
 
 
 class rm_options(C.Structure):
@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH):
     lib.rm_plan_info.argtypes = [P, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
                                  C.POINTER(i32), C.POINTER(i64)]
     lib.rm_plan_cluster.argtypes = [P, C.POINTER(i32), C.POINTER(i32)]
+    lib.rm_photo.argtypes = [P, i32, i64, i64, P, P, i32]
+    lib.rm_results_photo.argtypes = [P, i32, i64, i64, P, P, i32]
     lib.rm_plan_launches.argtypes = [P]
     lib.rm_plan_launches.restype = i64
     lib.rm_plan_destroy.argtypes = [P]
@@ -87,7 +89,7 @@ def load_library(path: str = LIB_PATH):
     lib.rm_last_error.restype = C.c_char_p
     for name in ["rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix", "rm_xsec", "rm_run",
                  "rm_results", "rm_sync", "rm_plan_info", "rm_plan_destroy", "rm_profile_enable",
-                 "rm_profile_read", "rm_plan_cluster"]:
+                 "rm_profile_read", "rm_plan_cluster", "rm_photo", "rm_results_photo"]:
         getattr(lib, name).restype = C.c_int32
     _lib = lib
     return lib
@@ -170,6 +172,13 @@ class Plan:
             warr[g].a = float(w.a)
             warr[g].z = float(getattr(w, "z", 0.0))
             warr[g].l, warr[g].thresh, warr[g].pole_E, warr[g].W = (_ptr(a) for a in arrs)
+            dip = getattr(w, "dip", None)
+            if dip is not None:
+                if isinstance(dip, np.ndarray):
+                    dip = np.ascontiguousarray(dip, dtype="float64")
+                self._keep.append(dip)
+                warr[g].dip = _ptr(dip)
+                warr[g].e0 = float(getattr(w, "e0", 0.0))
         return warr
 
     def load(self, waves, energies):
@@ -231,6 +240,15 @@ class Plan:
     def results(self, wave, e0, e1, eigsum=None, sig_tot=None, sig_sel=None, n_open=None, flags=None):
         _check(self.lib.rm_results(self.h, wave, e0, e1, _ptr(eigsum), _ptr(sig_tot), _ptr(sig_sel),
                                    _ptr(n_open), _ptr(flags), self._mem(eigsum, sig_tot, sig_sel, n_open, flags)))
+
+    def photo(self, wave, e0, e1, sig_pi=None, sig_pi_ch=None):
+        """Photoionisation cross sections of a wave with a dipole vector, energies [e0, e1)."""
+        _check(self.lib.rm_photo(self.h, wave, e0, e1, _ptr(sig_pi), _ptr(sig_pi_ch), self._mem(sig_pi, sig_pi_ch)))
+
+    def results_photo(self, wave, e0, e1, sig_pi=None, sig_pi_ch=None):
+        """Photoionisation results of the last run()."""
+        _check(self.lib.rm_results_photo(self.h, wave, e0, e1, _ptr(sig_pi), _ptr(sig_pi_ch),
+                                         self._mem(sig_pi, sig_pi_ch)))
 
     def sync(self):
         _check(self.lib.rm_sync(self.h))
