@@ -50,6 +50,15 @@ in bohr, k^2 = E - e_i):
    s, c normalised as k^-1/2 sin, cos, i.e. sqrt(pi) times per-Rydberg energy
    normalisation; initial statistical weight 1).
 
+7. Post-processing to compare with experiment (the paper convolves its cross
+   sections with a Gaussian of the experiment's FWHM and averages them over
+   initial levels with statistical weights, e.g. 2/3 ground + 1/3 metastable):
+   sigma_avg(E) = sum_s f_s int sigma_s(E') G(E - E') dE' / int G(E - E') dE',
+   G a normalised Gaussian of full width at half maximum F (standard deviation
+   F / (2 sqrt(2 ln 2))); on the mesh the integrals are trapezoid sums over the
+   mesh, and dividing by the kernel's own sum keeps a constant a constant at
+   the mesh ends.
+
 Energies closer than 1e-9 Ry to a pole or a threshold are moved up by 1e-6 Ry,
 once, and flagged.
 
@@ -425,3 +434,37 @@ def wrap_angle(x):
     """Wrap to (-pi, pi]."""
     y = np.mod(np.asarray(x) + np.pi, 2.0 * np.pi) - np.pi
     return np.where(y == -np.pi, np.pi, y)
+
+
+def trapezoid_weights(E):
+    """Trapezoid-rule weights of a sorted mesh: (E_{e+1} - E_{e-1}) / 2, half intervals at the ends."""
+    E = np.asarray(E, dtype=np.float64)
+    w = np.zeros(E.size)
+    if E.size > 1:
+        d = np.diff(E)
+        w[:-1] += 0.5 * d
+        w[1:] += 0.5 * d
+    else:
+        w[:] = 1.0
+    return w
+
+
+def convolve_average(E, sigma, weights, fwhm):
+    """Item 7: sum_s f_s (G * sigma_s)(E_e) on the mesh, with sigma [n_series, n_e].
+
+    fwhm = 0 returns the weighted sum of the series unconvolved.
+    """
+    E = np.asarray(E, dtype=np.float64)
+    sigma = np.atleast_2d(np.asarray(sigma, dtype=np.float64))
+    f = np.asarray(weights, dtype=np.float64)
+    mixed = f @ sigma
+    if fwhm == 0.0:
+        return mixed
+    sd = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    tw = trapezoid_weights(E)
+    out = np.zeros(E.size)
+    for e in range(E.size):
+        g = np.exp(-0.5 * ((E[e] - E) / sd) ** 2) * tw
+        out[e] = np.dot(g, mixed) / np.sum(g)
+    return out
+

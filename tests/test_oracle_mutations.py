@@ -197,9 +197,22 @@ def pin_photo():
     return bool(ok)
 
 
+def pin_convolution():
+    # Gaussian * Gaussian on a non-uniform mesh: widths add in quadrature; weights are linear
+    u = np.linspace(0.0, 1.0, 3001)
+    E = 2.0 * u ** 2
+    g = lambda x, mu, sd: np.exp(-0.5 * ((x - mu) / sd) ** 2) / (sd * math.sqrt(2 * math.pi))
+    s1, fwhm = 0.03, 0.05
+    s2 = fwhm / (2 * math.sqrt(2 * math.log(2)))
+    both = o.convolve_average(E, np.vstack([g(E, 1.0, s1), g(E, 1.0, s1)]), [0.25, 0.75], fwhm)
+    inner = (E > 0.6) & (E < 1.4)
+    want = g(E, 1.0, math.hypot(s1, s2))
+    return bool(np.abs(both[inner] - want[inner]).max() <= 1e-4 * want.max())
+
+
 PINS = [pin_breit_wigner, pin_lane_thomas, pin_hard_sphere, pin_bloch, pin_closed_channel,
         pin_symmetry_unitarity_balance, pin_nudge, pin_coulomb_hard_sphere, pin_coulomb_closed_hydrogenic,
-        pin_coulomb_eta_zero, pin_photo]
+        pin_coulomb_eta_zero, pin_photo, pin_convolution]
 
 
 def run_pins():
@@ -250,6 +263,10 @@ MUTATIONS = [
     ("boundary derivative Lambda by column", o.photo_amplitudes, "f[\"lam\"][:, None] * Y",
      "f[\"lam\"][None, :no] * Y"),
     ("photon energy sign", o.sweep, "(E - float(wave.e0))", "(float(wave.e0) - E)"),
+    ("FWHM taken as the standard deviation", o.convolve_average,
+     "sd = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))", "sd = fwhm"),
+    ("convolution without mesh weights", o.convolve_average, ") ** 2) * tw", ") ** 2) * 1.0"),
+    ("statistical weights ignored", o.convolve_average, "mixed = f @ sigma", "mixed = sigma.sum(axis=0)"),
 ]
 
 
