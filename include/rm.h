@@ -195,6 +195,23 @@ rm_status_t rm_photo(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, doubl
 rm_status_t rm_results_photo(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, double* sig_pi,
                              double* sig_pi_ch, int32_t mem);
 
+/* Post-processing (no plan needed).  The paper compares its cross sections with experiment after
+   convolving them with a Gaussian of the experiment's full width at half maximum and averaging
+   them over initial levels with statistical weights (2/3 ground + 1/3 metastable, fine-structure
+   levels ...).  For a sorted mesh energies[n_e] and n_series cross-section series
+   sigma[n_series * n_e] (series-major) on it:
+     out[e] = sum_e' G(E_e - E_e') tw_e' m_e' / sum_e' G(E_e - E_e') tw_e',
+     m_e' = sum_s f_s sigma[s * n_e + e'],
+   G a Gaussian of full width at half maximum fwhm (same unit as the energies), tw the trapezoid
+   weights of the mesh, the kernel truncated at 8 standard deviations; dividing by the kernel's
+   own sum keeps a constant a constant at the mesh ends.  fwhm = 0 gives the weighted sum alone.
+   weights: host array f[n_series] (NULL = 1/n_series each); 1 <= n_series <= 16, fwhm finite
+   and >= 0.  energies, sigma and out are in memory space mem; the mesh must be sorted ascending
+   (checked for host pointers only).  Device pointers: enqueued on cuda_stream (NULL = default)
+   without waiting; host pointers: the call allocates device buffers and returns when done. */
+rm_status_t rm_convolve(const double* energies, int64_t n_e, const double* sigma, int32_t n_series,
+                        const double* weights, double fwhm, double* out, int32_t mem, void* cuda_stream);
+
 /* Wait for the plan's stream; reports device-side error words. */
 rm_status_t rm_sync(rm_plan_t plan);
 

@@ -964,6 +964,52 @@ rm_status_t rm_results_photo(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, 
   }
 }
 
+rm_status_t rm_convolve(const double* energies, int64_t n_e, const double* sigma, int32_t n_series,
+                        const double* weights, double fwhm, double* out, int32_t mem, void* cuda_stream) {
+  try {
+    if (n_e < 0 || (n_e > 0 && (!energies || !sigma || !out)) || !valid_mem(mem))
+      return fail(RM_ERR_ARG, "bad arguments");
+    if (n_series < 1 || n_series > convolve_max_series()) return fail(RM_ERR_ARG, "n_series must be in [1, 16]");
+    if (!(fwhm >= 0.0) || !(fwhm < 1e300)) return fail(RM_ERR_ARG, "fwhm must be finite and >= 0");
+    std::vector<double> f(n_series, 1.0 / n_series);
+    if (weights)
+      for (int s = 0; s < n_series; ++s) {
+        if (!(weights[s] > -1e300 && weights[s] < 1e300)) return fail(RM_ERR_ARG, "weights must be finite");
+        f[s] = weights[s];
+      }
+    if (n_e == 0) return RM_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if (mem == RM_MEM_DEVICE) {
+      RM_CUDA(launch_convolve(energies, n_e, sigma, n_series, f.data(), fwhm, out, s), "convolution kernel");
+      return RM_OK;
+    }
+    for (int64_t e = 0; e + 1 < n_e; ++e)
+      if (!(energies[e] <= energies[e + 1])) return fail(RM_ERR_ORDER, "energies are not sorted ascending");
+    double *dE = nullptr, *dS = nullptr, *dO = nullptr;
+    auto release = [&]() { dfree(dE); dfree(dS); dfree(dO); };
+    if (cudaMalloc(&dE, sizeof(double) * n_e) != cudaSuccess || cudaMalloc(&dS, sizeof(double) * n_e * n_series) != cudaSuccess ||
+        cudaMalloc(&dO, sizeof(double) * n_e) != cudaSuccess) {
+      cudaGetLastError();
+      release();
+      return fail(RM_ERR_NOMEM, "device buffers for the convolution");
+    }
+    cudaError_t err = cudaMemcpyAsync(dE, energies, sizeof(double) * n_e, cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(dS, sigma, sizeof(double) * n_e * n_series, cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) err = launch_convolve(dE, n_e, dS, n_series, f.data(), fwhm, dO, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(out, dO, sizeof(double) * n_e, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    release();
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RM_ERR_CUDA, std::string("convolution: ") + cudaGetErrorString(err));
+    }
+    return RM_OK;
+  } catch (...) {
+    return fail(RM_ERR_NOMEM, "unexpected host exception");
+  }
+}
+
 rm_status_t rm_results(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* eigsum, double* sig_tot,
                        double* sig_sel, int32_t* n_open, uint8_t* flags, int32_t mem) {
   try {

@@ -177,6 +177,11 @@ size_t solve_smem_bytes(int n_max);
 int solve_blocks_per_sm(int n_max);
 int64_t solve_slot_doubles(int n_max, int n_sel);
 
+// Gaussian convolution / statistical averaging of cross sections (post-processing)
+cudaError_t launch_convolve(const double* E, int64_t n_e, const double* sigma, int n_series, const double* f,
+                            double fwhm, double* out, cudaStream_t s);
+int convolve_max_series();
+
 // split-precision pole sum
 std::vector<int2> split_tiles(int n);
 cudaError_t split_prepare(const Plan& p, WaveDev& w, cudaStream_t s);

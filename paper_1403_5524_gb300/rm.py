@@ -26,7 +26,7 @@ PREC = {"fp64": RM_PREC_FP64, "split_bf16": RM_PREC_SPLIT_BF16, "split_fp16": RM
 EXPORTS = ["rm_options_default", "rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix",
            "rm_xsec", "rm_run", "rm_results", "rm_sync", "rm_plan_info", "rm_plan_launches",
            "rm_plan_destroy", "rm_status_str", "rm_last_error", "rm_profile_enable", "rm_profile_read",
-           "rm_plan_cluster", "rm_photo", "rm_results_photo"]
+           "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve"]
 
 KERNELS = {"polesum_fp64": 0, "polesum_split": 1, "near": 2, "asym": 3, "solve": 4}
 
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH):
     lib.rm_plan_cluster.argtypes = [P, C.POINTER(i32), C.POINTER(i32)]
     lib.rm_photo.argtypes = [P, i32, i64, i64, P, P, i32]
     lib.rm_results_photo.argtypes = [P, i32, i64, i64, P, P, i32]
+    lib.rm_convolve.argtypes = [P, i64, P, i32, P, dbl, P, i32, P]
     lib.rm_plan_launches.argtypes = [P]
     lib.rm_plan_launches.restype = i64
     lib.rm_plan_destroy.argtypes = [P]
@@ -89,7 +90,7 @@ def load_library(path: str = LIB_PATH):
     lib.rm_last_error.restype = C.c_char_p
     for name in ["rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix", "rm_xsec", "rm_run",
                  "rm_results", "rm_sync", "rm_plan_info", "rm_plan_destroy", "rm_profile_enable",
-                 "rm_profile_read", "rm_plan_cluster", "rm_photo", "rm_results_photo"]:
+                 "rm_profile_read", "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve"]:
         getattr(lib, name).restype = C.c_int32
     _lib = lib
     return lib
@@ -114,6 +115,29 @@ def _ptr(x):
 
 def _is_dev(x):
     return x is not None and not isinstance(x, np.ndarray) and x.is_cuda
+
+
+def convolve(energies, sigma, fwhm: float, weights: Optional[Sequence[float]] = None, out=None, stream=None):
+    """Gaussian convolution (full width fwhm) and statistical average of cross-section series.
+
+    ``sigma`` is (n_series, n_e) or (n_e,); NumPy (host) or CUDA torch tensors (device) like
+    ``energies``; ``weights`` the statistical weights (default: equal).  Returns ``out``.
+    """
+    lib = load_library()
+    dev = _is_dev(energies)
+    n_e = int(energies.shape[0])
+    n_series = 1 if len(sigma.shape) == 1 else int(sigma.shape[0])
+    if out is None:
+        if dev:
+            import torch
+            out = torch.empty(n_e, dtype=torch.float64, device=energies.device)
+        else:
+            out = np.zeros(n_e)
+    w = None if weights is None else np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    stream_ptr = None if stream is None else int(stream.cuda_stream)
+    _check(lib.rm_convolve(_ptr(energies), n_e, _ptr(sigma), n_series, None if w is None else w.ctypes.data,
+                           float(fwhm), _ptr(out), RM_MEM_DEVICE if dev else RM_MEM_HOST, stream_ptr))
+    return out
 
 
 class Plan:

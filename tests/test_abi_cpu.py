@@ -105,3 +105,18 @@ def test_null_plan_calls(lib):
     assert lib.rm_sync(None) == rm.RM_ERR_ARG
     assert lib.rm_plan_destroy(None) == rm.RM_OK
     assert lib.rm_plan_launches(None) == -1
+
+
+def test_convolve_arguments_checked_on_host(lib):
+    E = np.linspace(0.0, 1.0, 11)
+    sig = np.ones((2, 11))
+    out = np.zeros(11)
+    call = lambda E_, ns, fw, w=None: lib.rm_convolve(E_.ctypes.data, E_.shape[0], sig.ctypes.data, ns,
+                                                      None if w is None else w.ctypes.data, fw, out.ctypes.data,
+                                                      rm.RM_MEM_HOST, None)
+    assert call(E, 0, 0.1) == rm.RM_ERR_ARG
+    assert call(E, 17, 0.1) == rm.RM_ERR_ARG
+    assert call(E, 2, -1.0) == rm.RM_ERR_ARG
+    assert call(E, 2, float("nan")) == rm.RM_ERR_ARG
+    assert call(E, 2, 0.1, np.array([0.5, float("inf")])) == rm.RM_ERR_ARG
+    assert call(E[::-1].copy(), 2, 0.1) == rm.RM_ERR_ORDER
