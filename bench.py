@@ -122,8 +122,10 @@ def workload(args):
 def algorithmic_flops(wl, n_open_by_wave, n_sel):
     """Per-step FLOP counts of the method (not counting slice products).
 
-    pole sum 2 n_p N per energy; matching LU (2/3) n^3 + 2 n^2 n_o;
-    S-step (8/3) n_o^3 + 8 n_o^2 r (real flops of the complex LU and solve).
+    pole sum 2 n_p N per energy; matching LU (2/3) n^3 + 2 n^2 n_o; S-step
+    (4/3) n_o^3 + 8 n_o^2 r: real flops of the complex-symmetric LDL^T of I - iK
+    (n_o^3 / 6 complex multiply-adds) and its solves -- the factorisation the
+    solve kernel performs (a general complex LU would be (8/3) n_o^3).
     """
     pole = 0.0
     solve = 0.0
@@ -132,7 +134,7 @@ def algorithmic_flops(wl, n_open_by_wave, n_sel):
         npair = n * (n + 1) / 2
         pole += 2.0 * npair * w.N * wl.n_e
         no = no.astype(np.float64)
-        solve += float(np.sum((2.0 / 3.0) * n ** 3 + 2.0 * n * n * no + (8.0 / 3.0) * no ** 3
+        solve += float(np.sum((2.0 / 3.0) * n ** 3 + 2.0 * n * n * no + (4.0 / 3.0) * no ** 3
                               + 8.0 * no * no * n_sel))
     return pole, solve
 

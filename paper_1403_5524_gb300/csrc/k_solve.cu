@@ -9,10 +9,11 @@
 // which leaves Y = (I - a R Lambda)^-1 (-B) in the right-hand columns;
 // K_jm = Y_jm / c_j for open j, m.
 //
-// S-step: A = I - iK (n_o x n_o complex) with right-hand sides K[:, sel_q];
-// the same LU gives X = A^-1 K[:, sel], T[:, sel_q] = 2i X[:, q] (T = S - I =
+// S-step: A = I - iK (n_o x n_o, complex symmetric) with right-hand sides
+// K[:, sel_q]; its LDL^T factorisation (no interchanges needed, see ldl_solve)
+// gives X = A^-1 K[:, sel], T[:, sel_q] = 2i X[:, q] (T = S - I =
 // 2iK(I - iK)^-1), sigma_{sel_q -> j} = (pi / k^2) |T_{j,sel_q}|^2, and the
-// eigenphase sum -arg det(I - iK) from the pivots and the interchange count.
+// eigenphase sum -arg det(I - iK) = -sum_j arg d_j.
 //
 // Photoionisation (a wave whose pole sum carries the dipole vector as row 0,
 // so that R holds y_i = (1/2a) sum_k w_ik d_k / (E_k - E) ahead of the channel
@@ -334,6 +335,161 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
   }
 }
 
+// LDL^T factorisation without pivoting of a complex symmetric matrix A (n x n,
+// row-major, ld; only its lower triangle is read and kept up to date), the
+// same elimination applied to the right-hand-side columns [n, m), then
+// x = L^-T D^-1 L^-1 b on those columns.  Used for A = I - iK: every Schur
+// complement of I - iK keeps a real part >= I (the real part of
+// K21 (I - iK11)^-1 K12 is K21 (I + K11^2)^-1 K12 >= 0), so every pivot has
+// |d| >= Re d >= 1 and the elimination needs no interchanges; it costs half
+// the flops of LU and skips the pivot searches.  d_j is left on the diagonal.
+// Blocked like lu_solve: an NB-column panel factored in shared memory, then
+// the columns to its right in TC-column tiles, where a matrix column col takes
+// the tile column d_j L[col][kb+j] straight from the panel and updates rows
+// >= col only, and a right-hand-side column takes L11^-1 A12 as in lu_solve.
+template <typename T>
+__device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* tile, T* tmp, T* tri,
+                          LUStat& st) {
+  using O = Ops<T>;
+  constexpr int NB = Blk<T>::NB;
+  const int t = threadIdx.x;
+  st.pmin = INFINITY;
+  st.pmax = 0.0;
+  st.swaps = 0;
+  st.singular = false;
+  // ------------------------------------------------------------ factorisation
+  for (int kb = 0; kb < n; kb += NB) {
+    const int nb = min(NB, n - kb);
+    const int rows = n - kb;
+    // panel rows kb.., columns kb..kb+nb; in the diagonal block the upper half comes from the
+    // (current) lower half by symmetry
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      T v = O::zero();
+      if (c < nb) v = (r >= c) ? A[(int64_t)(kb + r) * ld + kb + c] : A[(int64_t)(kb + c) * ld + kb + r];
+      panel[idx] = v;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      const T piv = panel[j * NB + j];
+      const double pm = O::mag(piv);
+      if (t == 0) {
+        st.pmin = fmin(st.pmin, pm);
+        st.pmax = fmax(st.pmax, pm);
+        if (pm == 0.0) st.singular = true;
+      }
+      const T pinv = (pm == 0.0) ? O::zero() : O::inv(piv);
+      for (int r = j + 1 + t; r < rows; r += NT) {
+        const T lr = O::mul(panel[r * NB + j], pinv);
+        panel[r * NB + j] = lr;
+        for (int c = j + 1; c < nb; ++c) panel[r * NB + c] = O::fms(panel[r * NB + c], lr, panel[j * NB + c]);
+      }
+      __syncthreads();
+    }
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      if (c < nb && r >= c) A[(int64_t)(kb + r) * ld + kb + c] = panel[idx];
+    }
+    // inverse of the unit-lower diagonal block (for the right-hand sides), column t by thread t
+    if (t < NB) {
+      for (int i = 0; i < NB; ++i) tri[i * NB + t] = (i == t) ? O::one() : O::zero();
+      if (t < nb) {
+        for (int i = t + 1; i < nb; ++i) {
+          T acc = O::zero();
+          for (int k = t; k < i; ++k) acc = O::fms(acc, panel[i * NB + k], tri[k * NB + t]);
+          tri[i * NB + t] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    for (int c0 = kb + nb; c0 < m; c0 += TC) {
+      // tile column: d_j L[col][kb+j] for matrix columns, L11^-1 A12 for right-hand sides
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        tmp[idx] = (j < nb && col >= n && col < m) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
+      }
+      __syncthreads();
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        if (col >= m) continue;
+        T u;
+        if (col < n) {
+          u = (j < nb) ? O::mul(panel[j * NB + j], panel[(col - kb) * NB + j]) : O::zero();
+        } else {
+          u = tmp[j * TC + c];
+          for (int i = 0; i < j; ++i) u = O::fma_acc(u, tri[j * NB + i], tmp[i * TC + c]);
+          if (j < nb) A[(int64_t)(kb + j) * ld + col] = u;
+        }
+        tile[idx] = u;
+      }
+      __syncthreads();
+      const int cwp = tile_width_pow2(m - c0);
+      const int tc = t % cwp, tr = t / cwp;
+      const int col = c0 + tc;
+      if (col < m) {
+        const int rs = (col < n) ? max(kb + nb, col) : kb + nb;  // lower triangle only
+        rank_update<T>(A, ld, col, rs + tr, n, panel - (int64_t)kb * NB, tile + tc, nb, NT / cwp);
+      }
+      __syncthreads();
+    }
+  }
+  // -------------------------------------------- D^-1, then back substitution
+  for (int64_t idx = t; idx < (int64_t)n * (m - n); idx += NT) {
+    const int i = (int)(idx / (m - n)), col = n + (int)(idx % (m - n));
+    const T d = A[(int64_t)i * ld + i];
+    A[(int64_t)i * ld + col] = (O::mag(d) == 0.0) ? O::zero() : O::mul(A[(int64_t)i * ld + col], O::inv(d));
+  }
+  __syncthreads();
+  const int kb_last = ((n - 1) / NB) * NB;
+  for (int kb = kb_last; kb >= 0; kb -= NB) {
+    const int nb = min(NB, n - kb);
+    const int rows = kb + nb;  // (L^T)[0 .. kb+nb)[kb .. kb+nb) = L[kb+c][r]
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      T v = O::zero();
+      if (c < nb) {
+        if (r < kb + c) v = A[(int64_t)(kb + c) * ld + r];
+        else if (r == kb + c) v = O::one();
+      }
+      panel[idx] = v;
+    }
+    __syncthreads();
+    // inverse of the unit-upper diagonal block, column t by thread t
+    if (t < NB) {
+      for (int i = 0; i < NB; ++i) tri[i * NB + t] = (i == t) ? O::one() : O::zero();
+      if (t < nb) {
+        const T* U = panel + (int64_t)kb * NB;
+        for (int i = t - 1; i >= 0; --i) {
+          T acc = O::zero();
+          for (int k = i + 1; k <= t; ++k) acc = O::fms(acc, U[i * NB + k], tri[k * NB + t]);
+          tri[i * NB + t] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    for (int c0 = n; c0 < m; c0 += TC) {
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        tmp[idx] = (j < nb && col < m) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
+      }
+      __syncthreads();
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        if (col >= m) continue;
+        T y = O::zero();
+        for (int i = j; i < nb; ++i) y = O::fma_acc(y, tri[j * NB + i], tmp[i * TC + c]);
+        tile[idx] = y;
+        if (j < nb) A[(int64_t)(kb + j) * ld + col] = y;
+      }
+      __syncthreads();
+      const int cwp = tile_width_pow2(m - c0);
+      const int tc = t % cwp, tr = t / cwp;
+      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, tr, kb, panel, tile + tc, nb, NT / cwp);
+      __syncthreads();
+    }
+  }
+}
+
 struct SolveArgs {
   int n, n_sel;
   double a;
@@ -470,6 +626,7 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     const int i = (int)(idx / mc), j = (int)(idx % mc);
     cplx v;
     if (j < no) {
+      if (j > i) continue;  // the LDL^T reads the lower triangle only
       const double kij = A[(int64_t)i * g.ldR + n + j] * rc[i];
       v = cplx{(i == j) ? 1.0 : 0.0, -kij};
     } else if (j < no + r) {
@@ -481,14 +638,13 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     C[(int64_t)i * g.ldC + j] = v;
   }
   __syncthreads();
-  lu_solve<cplx>(C, no, mc, g.ldC, panel_c, tile_c, tmp_c, tri_c, ipiv, &red, st);
+  ldl_solve<cplx>(C, no, mc, g.ldC, panel_c, tile_c, tmp_c, tri_c, st);
   if (t == 0 && g.out.eta) {
-    double ph = 0.0;
+    double ph = 0.0;  // det(I - iK) = prod d_j (no interchanges)
     for (int j = 0; j < no; ++j) {
       const cplx d = C[(int64_t)j * g.ldC + j];
       ph += atan2(d.im, d.re);
     }
-    ph += M_PI * (double)(st.swaps & 1);
     double eta = -ph;
     eta = eta - 2.0 * M_PI * floor((eta + M_PI) / (2.0 * M_PI));  // [-pi, pi)
     if (eta == -M_PI) eta = M_PI;
