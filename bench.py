@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--sel", type=int, default=1, help="number of selected initial channels")
     ap.add_argument("--chunk", type=int, default=0, help="energies per rm_run chunk (0: automatic)")
     ap.add_argument("--z", type=float, default=0.0, help="residual target charge of every wave (0: neutral)")
+    ap.add_argument("--solve", default="fp64", choices=["fp64", "mixed"],
+                    help="matching solve: FP64, or FP32 LU + double-float iterative refinement")
     ap.add_argument("--dipole", action="store_true",
                     help="photoionisation: give every wave a bound-free dipole vector (sigma_PI per energy)")
     ap.add_argument("--cluster", default="", help="tensor-core cluster shape CXxCY (default: autotuned)")
@@ -263,7 +265,7 @@ def run_ours(args):
     dE = torch.from_numpy(wl.energies).to(dev)
     cluster = tuple(int(x) for x in args.cluster.split("x")) if args.cluster else None
     plan = rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream, autotune=True,
-                   chunk=args.chunk, cluster=cluster)
+                   chunk=args.chunk, cluster=cluster, solve=args.solve)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
     def barrier():
@@ -352,6 +354,15 @@ def run_ours(args):
                    "algorithmic_tflops": pole_flops * args.steps / (kern["polesum_split"]["ms_total"]
                                                                     + kern.get("near", {}).get("ms_total", 0.0)) / 1e9,
                    "note": f"{SPLIT_PRODUCTS} BF16 products per far term; algorithmic = 2 n_p N n_e of Eq. 1-2"}
+
+    # mixed solve: energies whose refinement fell back to FP64 (flag 32) in the last run
+    fallback = None
+    if args.solve == "mixed":
+        fallback = 0
+        for g, w in enumerate(wl.waves):
+            fl = np.zeros(wl.n_e, np.uint8)
+            plan.results(g, 0, wl.n_e, flags=fl)
+            fallback += int(np.count_nonzero(fl & 32))
 
     # post-processing: Gaussian convolution of the sweep's sigma_tot at the experiments' widths
     # (4 meV and 124 meV FWHM), on the device, outside the timed step
@@ -448,7 +459,8 @@ def run_ours(args):
                 "data": "synthetic (seeded, workload distributions of the paper's problem class)",
                 "config": {"workload": wl.name, "prec": args.prec, "mesh_stride": stride,
                            "energy_chunk": plan.info(0)["chunk"],
-                           "tc_cluster": "%dx%d" % plan.cluster(),
+                           "tc_cluster": "%dx%d" % plan.cluster(), "solve": args.solve,
+                           "fp64_fallback_energies": fallback,
                            "energies_per_step": wl.n_e, "waves": len(wl.waves),
                            "n_ch": [w.n for w in wl.waves][:4], "n_poles": [w.N for w in wl.waves][:4],
                            "n_sel": len(sel), "l2": "flushed (512 MB write) between timed steps",

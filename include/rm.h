@@ -76,9 +76,18 @@ typedef enum {
 #define RM_FLAG_SINGULAR 8u  /* exact zero pivot; outputs are NaN */
 #define RM_FLAG_ASYM 16u     /* a Coulomb / Whittaker continued fraction did not converge within its
                                 iteration cap for some channel (z > 0 only); outputs are unreliable */
+#define RM_FLAG_FP64 32u     /* solve_prec = RM_SOLVE_MIXED: the FP32 refinement did not converge (or hit a
+                                zero pivot) and the matching system was solved in FP64 instead */
 
 #define RM_LMAX 32           /* largest supported channel angular momentum */
 #define RM_MAX_SEL 64        /* largest number of selected initial channels */
+
+/* Precision of the matching (K-matrix) solve.  MIXED: LU in FP32, then iterative refinement
+   with residuals r = -B - M Y in double-float (FP32 hi + lo, error-free products and sums, about
+   48 bits) and FP32 correction solves until the last correction is below 1e-11 of Y; an energy
+   whose refinement stops contracting is solved again in FP64 (RM_FLAG_FP64).  The S-step stays
+   FP64 (its eigenphase sum needs FP64 pivots). */
+typedef enum { RM_SOLVE_FP64 = 0, RM_SOLVE_MIXED = 1 } rm_solve_precision_t;
 
 typedef struct rm_plan_s* rm_plan_t;
 
@@ -127,6 +136,7 @@ typedef struct {
                               the P slices): 1, 2 or 4; 0 = automatic.  At most 8 CTAs per
                               cluster; a shape the device cannot co-schedule is rejected with
                               RM_ERR_ARG. */
+  int32_t solve_prec;      /* rm_solve_precision_t of the matching solve (default FP64) */
 } rm_options;
 
 /* Fill *opt with defaults: FP64, delta 0.05, sel {0}, host inputs, auto chunk. */

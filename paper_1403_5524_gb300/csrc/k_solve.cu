@@ -60,6 +60,17 @@ struct Ops<double> {
 };
 
 template <>
+struct Ops<float> {
+  __device__ static float zero() { return 0.0f; }
+  __device__ static float one() { return 1.0f; }
+  __device__ static double mag(float x) { return fabsf(x); }
+  __device__ static float inv(float x) { return 1.0f / x; }
+  __device__ static float mul(float a, float b) { return a * b; }
+  __device__ static float fms(float acc, float a, float b) { return fmaf(-a, b, acc); }
+  __device__ static float fma_acc(float acc, float a, float b) { return fmaf(a, b, acc); }
+};
+
+template <>
 struct Ops<cplx> {
   __device__ static cplx zero() { return cplx{0.0, 0.0}; }
   __device__ static cplx one() { return cplx{1.0, 0.0}; }
@@ -91,8 +102,9 @@ struct Blk {
 };
 
 constexpr int TILE_BYTES = Blk<double>::NB * TC * 8;  // NB x TC elements, either type
-constexpr int TRI_BYTES = Blk<double>::NB * Blk<double>::NB * 8;  // the larger of the two
+constexpr int TRI_BYTES = Blk<float>::NB * Blk<float>::NB * 4;  // the largest of the three types
 static_assert(Blk<cplx>::NB * TC * (int)sizeof(cplx) == TILE_BYTES, "tile bytes");
+static_assert(Blk<float>::NB * TC * (int)sizeof(float) == TILE_BYTES, "tile bytes");
 
 // smallest power of two >= min(TC, w), at least 1
 __device__ __forceinline__ int tile_width_pow2(int w) {
@@ -490,6 +502,216 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
   }
 }
 
+// ------------------------------------------------------------------------
+// Mixed-precision matching solve: FP32 LU of [M | -B], then iterative
+// refinement with residuals r = -B - M Y computed in double-float (FP32 hi +
+// lo, error-free products and sums: about 48 bits) and corrections solved
+// with the FP32 factors.  GB300 retires 64 FP32 FMAs for every FP64 FMA, so a
+// double-float multiply-add (about 11 FP32 operations) costs about a sixth of
+// an FP64 one, and the FP64 pipe is left to the complex S-step.
+
+// s + e = a + b exactly
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Apply the stored LU factors (row interchanges ipiv, unit-lower L, upper U, in A) to the
+// right-hand-side columns [n, m): forward elimination by panels, then back substitution.
+template <typename T>
+__device__ void lu_resolve(T* __restrict__ A, int n, int m, int ld, T* panel, T* tile, T* tmp, T* tri,
+                           const int* ipiv) {
+  using O = Ops<T>;
+  constexpr int NB = Blk<T>::NB;
+  const int t = threadIdx.x;
+  for (int kb = 0; kb < n; kb += NB) {
+    const int nb = min(NB, n - kb);
+    const int rows = n - kb;
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      panel[idx] = (c < nb) ? A[(int64_t)(kb + r) * ld + kb + c] : O::zero();
+    }
+    for (int col = n + t; col < m; col += NT) {
+      for (int j = 0; j < nb; ++j) {
+        const int r1 = kb + j, r2 = ipiv[kb + j];
+        if (r1 != r2) {
+          const T a1 = A[(int64_t)r1 * ld + col];
+          A[(int64_t)r1 * ld + col] = A[(int64_t)r2 * ld + col];
+          A[(int64_t)r2 * ld + col] = a1;
+        }
+      }
+    }
+    __syncthreads();
+    if (t < NB) {
+      for (int i = 0; i < NB; ++i) tri[i * NB + t] = (i == t) ? O::one() : O::zero();
+      if (t < nb) {
+        for (int i = t + 1; i < nb; ++i) {
+          T acc = O::zero();
+          for (int k = t; k < i; ++k) acc = O::fms(acc, panel[i * NB + k], tri[k * NB + t]);
+          tri[i * NB + t] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    for (int c0 = n; c0 < m; c0 += TC) {
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        tmp[idx] = (j < nb && col < m) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
+      }
+      __syncthreads();
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        if (col >= m) continue;
+        T u = tmp[j * TC + c];
+        for (int i = 0; i < j; ++i) u = O::fma_acc(u, tri[j * NB + i], tmp[i * TC + c]);
+        tile[idx] = u;
+        if (j < nb) A[(int64_t)(kb + j) * ld + col] = u;
+      }
+      __syncthreads();
+      const int cwp = tile_width_pow2(m - c0);
+      const int tc = t % cwp, tr = t / cwp;
+      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, kb + nb + tr, n, panel - (int64_t)kb * NB, tile + tc, nb, NT / cwp);
+      __syncthreads();
+    }
+  }
+  const int kb_last = ((n - 1) / NB) * NB;
+  for (int kb = kb_last; kb >= 0; kb -= NB) {
+    const int nb = min(NB, n - kb);
+    const int rows = kb + nb;
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      panel[idx] = (c < nb) ? A[(int64_t)r * ld + kb + c] : O::zero();
+    }
+    __syncthreads();
+    if (t < NB) {
+      for (int i = 0; i < NB; ++i) tri[i * NB + t] = O::zero();
+      if (t < nb) {
+        const T* U = panel + (int64_t)kb * NB;
+        const double dm = O::mag(U[t * NB + t]);
+        tri[t * NB + t] = (dm == 0.0) ? O::zero() : O::inv(U[t * NB + t]);
+        for (int i = t - 1; i >= 0; --i) {
+          T acc = O::zero();
+          for (int k = i + 1; k <= t; ++k) acc = O::fms(acc, U[i * NB + k], tri[k * NB + t]);
+          const double di = O::mag(U[i * NB + i]);
+          tri[i * NB + t] = (di == 0.0) ? O::zero() : O::mul(acc, O::inv(U[i * NB + i]));
+        }
+      }
+    }
+    __syncthreads();
+    for (int c0 = n; c0 < m; c0 += TC) {
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        tmp[idx] = (j < nb && col < m) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
+      }
+      __syncthreads();
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        if (col >= m) continue;
+        T y = O::zero();
+        for (int i = j; i < nb; ++i) y = O::fma_acc(y, tri[j * NB + i], tmp[i * TC + c]);
+        tile[idx] = y;
+        if (j < nb) A[(int64_t)(kb + j) * ld + col] = y;
+      }
+      __syncthreads();
+      const int cwp = tile_width_pow2(m - c0);
+      const int tc = t % cwp, tr = t / cwp;
+      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, tr, kb, panel, tile + tc, nb, NT / cwp);
+      __syncthreads();
+    }
+  }
+}
+
+// r = b - M y in double-float for the n x no block, b = A64[:, n + c] (FP64), M = Mh + Ml
+// (n x n, ld ldm), y = Yh + Yl (n x no, ld ldy); r rounded to FP32 into R[i * ldr + c].
+// 64 x 64 output tiles, 4 x 4 per thread, k-steps of 16 staged through 16 KB of shared memory.
+__device__ void residual_df(const double* __restrict__ A64, int ldR, int n, int no, const float* __restrict__ Mh,
+                            const float* __restrict__ Ml, int ldm, const float* __restrict__ Yh,
+                            const float* __restrict__ Yl, int ldy, float* __restrict__ R, int ldr,
+                            float* sM, float* sY) {
+  constexpr int TT = 64, KR = 16;
+  const int t = threadIdx.x;
+  const int tx = t % 16, ty = t / 16;  // outputs rows ty*4.., cols tx*4..
+  float* sMh = sM;                     // [TT][KR]
+  float* sMl = sM + TT * KR;
+  float* sYh = sY;                     // [KR][TT]
+  float* sYl = sY + KR * TT;
+  for (int i0 = 0; i0 < n; i0 += TT) {
+    for (int c0 = 0; c0 < no; c0 += TT) {
+      float sh[4][4], sl[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = i0 + ty * 4 + a, c = c0 + tx * 4 + b;
+          const double v = (i < n && c < no) ? A64[(int64_t)i * ldR + n + c] : 0.0;
+          const float h = (float)v;
+          sh[a][b] = h;
+          sl[a][b] = (float)(v - (double)h);
+        }
+      // each thread stages 4 elements of each operand per k-step; the next k-step's values are
+      // loaded into registers before the current one is computed (latency hidden)
+      float pm[4][2], py[4][2];
+      auto fetch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int idx = t + q * NT;
+          const int r = idx / KR, k = idx % KR, i = i0 + r, j = k0 + k;
+          const bool okm = i < n && j < n;
+          pm[q][0] = okm ? Mh[(int64_t)i * ldm + j] : 0.0f;
+          pm[q][1] = okm ? Ml[(int64_t)i * ldm + j] : 0.0f;
+          const int ky = idx / TT, c = idx % TT, jy = k0 + ky, cc = c0 + c;
+          const bool oky = jy < n && cc < no;
+          py[q][0] = oky ? Yh[(int64_t)jy * ldy + cc] : 0.0f;
+          py[q][1] = oky ? Yl[(int64_t)jy * ldy + cc] : 0.0f;
+        }
+      };
+      fetch(0);
+      for (int k0 = 0; k0 < n; k0 += KR) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int idx = t + q * NT;
+          sMh[idx] = pm[q][0];
+          sMl[idx] = pm[q][1];
+          sYh[idx] = py[q][0];
+          sYl[idx] = py[q][1];
+        }
+        __syncthreads();
+        if (k0 + KR < n) fetch(k0 + KR);
+#pragma unroll 4
+        for (int k = 0; k < KR; ++k) {
+          const float4 yh = *reinterpret_cast<const float4*>(sYh + k * TT + tx * 4);
+          const float4 yl = *reinterpret_cast<const float4*>(sYl + k * TT + tx * 4);
+          const float yhv[4] = {yh.x, yh.y, yh.z, yh.w}, ylv[4] = {yl.x, yl.y, yl.z, yl.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const float mh = sMh[(ty * 4 + a) * KR + k], ml = sMl[(ty * 4 + a) * KR + k];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const float p = __fmul_rn(mh, yhv[b]);
+              float e = __fmaf_rn(mh, yhv[b], -p);
+              e = __fmaf_rn(mh, ylv[b], __fmaf_rn(ml, yhv[b], e));
+              float s, err;
+              df_two_sum(sh[a][b], -p, s, err);
+              sh[a][b] = s;
+              sl[a][b] = __fsub_rn(__fadd_rn(sl[a][b], err), e);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = i0 + ty * 4 + a, c = c0 + tx * 4 + b;
+          if (i < n && c < no) R[(int64_t)i * ldr + n + c] = __fadd_rn(sh[a][b], sl[a][b]);
+        }
+    }
+  }
+  __syncthreads();
+}
+
 struct SolveArgs {
   int n, n_sel;
   double a;
@@ -498,6 +720,8 @@ struct SolveArgs {
   int64_t roff;     // offset of the channel block (0 without a dipole row)
   int dip;          // 1: photoionisation amplitudes from y
   double e0;        // initial bound-state energy (Ry)
+  int mixed;        // 1: matching solve in FP32 + double-float iterative refinement
+  int64_t mix_off;  // doubles from a slot's start to its mixed-precision area
   const double* asym;
   int64_t ld_asym;  // stride between lam, s, sp, c blocks
   const double* E;  // [ne]
@@ -513,8 +737,104 @@ struct SolveArgs {
   SolveOut out;
 };
 
+// The matching system [M | -B] of solve_energy by FP32 LU and double-float
+// iterative refinement; on success the FP64 right-hand-side columns of A hold
+// Y.  Returns false (A untouched) when the FP32 factorisation hits a zero
+// pivot or the corrections stop contracting, and the caller solves in FP64.
+__device__ bool mixed_matching(const SolveArgs& g, double* A, int n, int m, int no, unsigned char* panel_b,
+                               unsigned char* tile_b, unsigned char* tmp_b, unsigned char* tri_b, int* ipiv,
+                               Red& red, LUStat& st) {
+  const int t = threadIdx.x;
+  const int nmax = g.ldR / 2;
+  float* A32 = reinterpret_cast<float*>(A + g.mix_off);
+  float* Mh = A32 + (int64_t)nmax * g.ldR;
+  float* Ml = Mh + (int64_t)nmax * nmax;
+  float* Yh = Ml + (int64_t)nmax * nmax;
+  float* Yl = Yh + (int64_t)nmax * nmax;
+  for (int64_t idx = t; idx < (int64_t)n * m; idx += NT) {
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    const double v = A[(int64_t)i * g.ldR + j];
+    const float f = (float)v;
+    A32[(int64_t)i * g.ldR + j] = f;
+    if (j < n) {
+      Mh[(int64_t)i * nmax + j] = f;
+      Ml[(int64_t)i * nmax + j] = (float)(v - (double)f);
+    }
+  }
+  __syncthreads();
+  lu_solve<float>(A32, n, m, g.ldR, reinterpret_cast<float*>(panel_b), reinterpret_cast<float*>(tile_b),
+                  reinterpret_cast<float*>(tmp_b), reinterpret_cast<float*>(tri_b), ipiv, &red, st);
+  __shared__ int s_fail;
+  if (t == 0) s_fail = st.singular ? 1 : 0;
+  __syncthreads();
+  if (s_fail) return false;
+  for (int64_t idx = t; idx < (int64_t)n * no; idx += NT) {
+    const int i = (int)(idx / no), c = (int)(idx % no);
+    Yh[(int64_t)i * nmax + c] = A32[(int64_t)i * g.ldR + n + c];
+    Yl[(int64_t)i * nmax + c] = 0.0f;
+  }
+  __syncthreads();
+  float prev = INFINITY;
+  bool conv = false;
+  for (int it = 0; it < 5 && !conv; ++it) {
+    residual_df(A, g.ldR, n, no, Mh, Ml, nmax, Yh, Yl, nmax, A32, g.ldR, reinterpret_cast<float*>(tile_b),
+                reinterpret_cast<float*>(tmp_b));
+    lu_resolve<float>(A32, n, m, g.ldR, reinterpret_cast<float*>(panel_b), reinterpret_cast<float*>(tile_b),
+                      reinterpret_cast<float*>(tmp_b), reinterpret_cast<float*>(tri_b), ipiv);
+    float dmax = 0.0f, ymax = 0.0f;
+    for (int64_t idx = t; idx < (int64_t)n * no; idx += NT) {
+      const int i = (int)(idx / no), c = (int)(idx % no);
+      const int64_t q = (int64_t)i * nmax + c;
+      const float d = A32[(int64_t)i * g.ldR + n + c];
+      float s, e;
+      df_two_sum(Yh[q], d, s, e);
+      Yh[q] = s;
+      Yl[q] = __fadd_rn(Yl[q], e);
+      dmax = fmaxf(dmax, fabsf(d));
+      ymax = fmaxf(ymax, fabsf(s));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, off));
+      ymax = fmaxf(ymax, __shfl_down_sync(0xffffffffu, ymax, off));
+    }
+    if ((t & 31) == 0) {
+      red.v[t >> 5] = dmax;
+      red.i[t >> 5] = __float_as_int(ymax);
+    }
+    __syncthreads();
+    if (t == 0) {
+      float dm = 0.0f, ym = 0.0f;
+      for (int w = 0; w < NWARP; ++w) {
+        dm = fmaxf(dm, (float)red.v[w]);
+        ym = fmaxf(ym, __int_as_float(red.i[w]));
+      }
+      // converged: the last correction is below 1e-11 of the solution (a looser stop, 1e-8, let
+      // single cross sections drift by 5e-8: elements of Y are more sensitive than its norm);
+      // failed: the corrections stopped contracting
+      red.piv = (dm <= 1e-11f * ym) ? 1 : ((dm < 0.5f * prev && isfinite(dm)) ? 0 : -1);
+      red.v[0] = dm;
+    }
+    __syncthreads();
+    const int verdict = red.piv;
+    prev = (float)red.v[0];
+    __syncthreads();
+    if (verdict < 0) return false;
+    conv = verdict > 0;
+  }
+  if (!conv) return false;
+  for (int64_t idx = t; idx < (int64_t)n * no; idx += NT) {
+    const int i = (int)(idx / no), c = (int)(idx % no);
+    const int64_t q = (int64_t)i * nmax + c;
+    A[(int64_t)i * g.ldR + n + c] = (double)Yh[q] + (double)Yl[q];
+  }
+  __syncthreads();
+  return true;
+}
+
 // One energy e of the argument block: build the matching system from R and the
 // asymptotic data, LU -> K, then (optionally) the complex S-step.
+template <bool MIXED>
 __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw, Red& red, double& s_acc) {
   const int n = g.n;
   // shared by both LUs: panel n x 128 B, tile and tmp 8 KB each, tri 2 KB, ipiv
@@ -579,8 +899,14 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   }
   __syncthreads();
   LUStat st;
-  lu_solve<double>(A, n, m, g.ldR, panel_d, tile_d, reinterpret_cast<double*>(tmp_c),
-                   reinterpret_cast<double*>(tri_c), ipiv, &red, st);
+  bool solved = false;
+  if constexpr (MIXED) {
+    solved = mixed_matching(g, A, n, m, no, panel_b, tile_b, tmp_b, tri_b, ipiv, red, st);
+    if (!solved) fl |= RM_FLAG_FP64;
+  }
+  if (!solved)
+    lu_solve<double>(A, n, m, g.ldR, panel_d, tile_d, reinterpret_cast<double*>(tmp_c),
+                     reinterpret_cast<double*>(tri_c), ipiv, &red, st);
   __shared__ int s_singular;
   __shared__ double s_ratio;
   if (t == 0) {
@@ -703,16 +1029,18 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   }
 }
 
+template <bool MIXED>
 __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Red red;
   __shared__ double s_acc;
-  for (int e = blockIdx.x; e < g.ne; e += gridDim.x) solve_energy(g, e, smem_raw, red, s_acc);
+  for (int e = blockIdx.x; e < g.ne; e += gridDim.x) solve_energy<MIXED>(g, e, smem_raw, red, s_acc);
 }
 
 // All waves of a plan: persistent CTAs claim (wave, chunk energy) units from a
 // list sorted by decreasing cost through an atomic counter.  Per-wave
 // arguments hold base pointers; the chunk offset e_begin is applied here.
+template <bool MIXED>
 __global__ void __launch_bounds__(NT, 2) solve_grouped_kernel(const SolveArgs* __restrict__ waves,
                                                               const int2* __restrict__ units, int n_units,
                                                               int64_t e_begin, int ne, int* counter) {
@@ -741,7 +1069,7 @@ __global__ void __launch_bounds__(NT, 2) solve_grouped_kernel(const SolveArgs* _
     if (g.out.pi_tot) g.out.pi_tot += e_begin;
     if (g.out.pi_ch) g.out.pi_ch += e_begin * g.n;
     g.ne = ne;
-    solve_energy(g, un.y, smem_raw, red, s_acc);
+    solve_energy<MIXED>(g, un.y, smem_raw, red, s_acc);
   }
 }
 
@@ -756,18 +1084,27 @@ size_t solve_smem_bytes(int n_max) {
 int solve_blocks_per_sm(int n_max) {
   const int smem = (int)solve_smem_bytes(n_max);
   int b = 0;
-  if (cudaFuncSetAttribute(solve_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, solve_grouped_kernel, NT, smem) != cudaSuccess) {
+  if (cudaFuncSetAttribute(solve_grouped_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(solve_grouped_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, solve_grouped_kernel<false>, NT, smem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
   return b < 1 ? 1 : (b > 2 ? 2 : b);
 }
 
-int64_t solve_slot_doubles(int n_max, int n_sel) {
+// slot layout: real augmented matrix n_max x 2 n_max, complex n_max x (n_max + n_sel), then
+// (mixed precision only) FP32 copy of the augmented matrix, M hi / lo, Y hi / lo: 3 n_max^2 doubles
+int64_t solve_mix_offset(int n_max, int n_sel) {
   const int64_t ldR = 2 * (int64_t)n_max;
   const int64_t ldC = (int64_t)n_max + n_sel;
-  int64_t d = (int64_t)n_max * ldR + 2 * (int64_t)n_max * ldC;
+  return ((int64_t)n_max * ldR + 2 * (int64_t)n_max * ldC + 31) / 32 * 32;
+}
+
+int64_t solve_slot_doubles(int n_max, int n_sel, bool mixed) {
+  const int64_t d = solve_mix_offset(n_max, n_sel) + (mixed ? 3 * (int64_t)n_max * n_max : 0);
   return (d + 31) / 32 * 32;
 }
 
@@ -783,6 +1120,8 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   g.roff = w.roff();
   g.dip = w.dip ? 1 : 0;
   g.e0 = w.e0;
+  g.mixed = p.solve_mixed;
+  g.mix_off = solve_mix_offset(p.n_max, p.n_sel + 1);
   g.asym = asym;
   g.ld_asym = ld_chunk;
   g.E = w.E + e0;
@@ -797,10 +1136,11 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   g.ldC = p.n_max + p.n_sel + 1;  // + the dipole right-hand side
   g.out = out;
   const size_t smem = solve_smem_bytes(p.n_max);
-  cudaError_t err = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = p.solve_mixed ? solve_kernel<true> : solve_kernel<false>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int grid = min(ne, p.solve_slots);
-  solve_kernel<<<grid, NT, smem, s>>>(g);
+  kern<<<grid, NT, smem, s>>>(g);
   return cudaGetLastError();
 }
 
@@ -818,6 +1158,8 @@ cudaError_t group_setup_solve(Plan& p) {
     a.roff = w.roff();
     a.dip = w.dip ? 1 : 0;
     a.e0 = w.e0;
+    a.mixed = p.solve_mixed;
+    a.mix_off = solve_mix_offset(p.n_max, p.n_sel + 1);
     a.asym = G.asym[g];
     a.ld_asym = (int64_t)G.chunk * w.n;
     a.E = w.E;
@@ -867,7 +1209,10 @@ cudaError_t group_setup_solve(Plan& p) {
     return err;
   if ((err = cudaMemcpy(G.units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
     return err;
-  return cudaFuncSetAttribute(solve_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e2 = cudaFuncSetAttribute(solve_grouped_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)solve_smem_bytes(p.n_max));
+  if (e2 != cudaSuccess) return e2;
+  return cudaFuncSetAttribute(solve_grouped_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)solve_smem_bytes(p.n_max));
 }
 
@@ -876,7 +1221,8 @@ cudaError_t launch_solve_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t
   cudaError_t err = cudaMemsetAsync(G.counter, 0, sizeof(int), s);
   if (err != cudaSuccess) return err;
   const int grid = std::min(p.solve_slots, p.n_waves * ne);
-  solve_grouped_kernel<<<grid, NT, solve_smem_bytes(p.n_max), s>>>(
+  auto kern = p.solve_mixed ? solve_grouped_kernel<true> : solve_grouped_kernel<false>;
+  kern<<<grid, NT, solve_smem_bytes(p.n_max), s>>>(
       reinterpret_cast<const SolveArgs*>(G.solve_waves), G.units, G.n_units, e0, ne, G.counter);
   return cudaGetLastError();
 }

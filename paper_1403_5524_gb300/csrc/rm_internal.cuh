@@ -123,6 +123,7 @@ struct Plan {
   int chunk = 0;
   int n_max = 0;
   int nR_max = 0;   // largest pole-sum row count (n_ch + 1 with a dipole vector)
+  int solve_mixed = 0;  // matching solve in FP32 + double-float iterative refinement
   int sm_count = 0;
   double* energies = nullptr;  // [n_e] raw mesh (device)
   std::vector<WaveDev> waves;
@@ -175,7 +176,8 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
                          const double* asym, int ld_chunk, const SolveOut& out, cudaStream_t s);
 size_t solve_smem_bytes(int n_max);
 int solve_blocks_per_sm(int n_max);
-int64_t solve_slot_doubles(int n_max, int n_sel);
+int64_t solve_slot_doubles(int n_max, int n_sel, bool mixed);
+int64_t solve_mix_offset(int n_max, int n_sel);
 
 // Gaussian convolution / statistical averaging of cross sections (post-processing)
 cudaError_t launch_convolve(const double* E, int64_t n_e, const double* sigma, int n_series, const double* f,

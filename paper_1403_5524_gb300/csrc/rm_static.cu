@@ -89,7 +89,7 @@ extern "C" rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_c
   // data, solve slots.  Chunk and slot counts shrink to fit; sizes that leave
   // no room for one slot are rejected.
   const int n = n_ch;
-  const int64_t slot_d = solve_slot_doubles(n, n_sel + 1);  // the solve's layout reserves a dipole column
+  const int64_t slot_d = solve_slot_doubles(n, n_sel + 1, false);  // the solve's layout reserves a dipole column
   const size_t slot_b = (size_t)slot_d * sizeof(double);
   const size_t fixed = align256(sizeof(int32_t) * RM_MAX_SEL);
   int chunk = 256;

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "librm.so")
 RM_OK, RM_ERR_ARG, RM_ERR_ORDER, RM_ERR_NOMEM, RM_ERR_CUDA, RM_ERR_TIMEOUT, RM_ERR_STATE = range(7)
 RM_MEM_HOST, RM_MEM_DEVICE = 0, 1
 RM_PREC_FP64, RM_PREC_SPLIT_BF16, RM_PREC_SPLIT_FP16, RM_PREC_FP32_SIMT = 0, 1, 2, 3
-FLAG_NUDGED, FLAG_ILLCOND, FLAG_NO_OPEN, FLAG_SINGULAR, FLAG_ASYM = 1, 2, 4, 8, 16
+FLAG_NUDGED, FLAG_ILLCOND, FLAG_NO_OPEN, FLAG_SINGULAR, FLAG_ASYM, FLAG_FP64 = 1, 2, 4, 8, 16, 32
+SOLVE = {"fp64": 0, "mixed": 1}
 
 PREC = {"fp64": RM_PREC_FP64, "split_bf16": RM_PREC_SPLIT_BF16, "split_fp16": RM_PREC_SPLIT_FP16,
         "fp32_simt": RM_PREC_FP32_SIMT}
@@ -41,7 +42,7 @@ class rm_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("delta", C.c_double), ("slices", C.c_int32),
                 ("sel_init", C.c_void_p), ("n_sel", C.c_int32), ("mem", C.c_int32),
                 ("chunk", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p),
-                ("cluster_x", C.c_int32), ("cluster_y", C.c_int32)]
+                ("cluster_x", C.c_int32), ("cluster_y", C.c_int32), ("solve_prec", C.c_int32)]
 
 
 class RMError(RuntimeError):
@@ -150,7 +151,7 @@ class Plan:
     def __init__(self, waves: Sequence, energies, prec: str = "fp64", delta: float = 0.05,
                  sel: Sequence[int] = (0,), chunk: int = 0, slices: int = 0, stream=None,
                  autotune: bool = False, tune_cache: Optional[str] = None,
-                 cluster: Optional[Sequence[int]] = None):
+                 cluster: Optional[Sequence[int]] = None, solve: str = "fp64"):
         self.lib = load_library()
         self._keep = []
         self.mem = RM_MEM_DEVICE if _is_dev(energies) else RM_MEM_HOST
@@ -170,6 +171,7 @@ class Plan:
         opt.tune_cache = self._tune_cache
         if cluster is not None:
             opt.cluster_x, opt.cluster_y = int(cluster[0]), int(cluster[1])
+        opt.solve_prec = SOLVE[solve]
         h = C.c_void_p()
         self.n_e = int(energies.shape[0])
         self.n_waves = len(waves)
