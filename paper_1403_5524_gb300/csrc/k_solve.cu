@@ -435,12 +435,29 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
         tile[idx] = u;
       }
       __syncthreads();
+      // matrix columns [c0, cm) of this tile: the rows below its diagonal block as one rectangle
+      // (every lane of a warp runs the same rows), the block's lower triangle element by element;
+      // right-hand-side columns: all rows below the panel
+      const int cm = min(c0 + TC, n);
       const int cwp = tile_width_pow2(m - c0);
       const int tc = t % cwp, tr = t / cwp;
       const int col = c0 + tc;
       if (col < m) {
-        const int rs = (col < n) ? max(kb + nb, col) : kb + nb;  // lower triangle only
+        const int rs = (col < n) ? max(kb + nb, cm) : kb + nb;
         rank_update<T>(A, ld, col, rs + tr, n, panel - (int64_t)kb * NB, tile + tc, nb, NT / cwp);
+      }
+      const int w = cm - c0;
+      for (int q = t; q < w * (w + 1) / 2; q += NT) {
+        int rr = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+        while (rr * (rr + 1) / 2 > q) --rr;
+        while ((rr + 1) * (rr + 2) / 2 <= q) ++rr;
+        const int cc = q - rr * (rr + 1) / 2;  // cc <= rr
+        const int r = c0 + rr;
+        T v = A[(int64_t)r * ld + c0 + cc];
+        const T* l = panel + (int64_t)(r - kb) * NB;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) v = O::fms(v, l[j], tile[j * TC + cc]);
+        A[(int64_t)r * ld + c0 + cc] = v;
       }
       __syncthreads();
     }
