@@ -366,6 +366,12 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       klo = g.klo[ge];
       khi = g.khi[ge];
     }
+    // swizzled slice offsets of this thread's elements, the same in every k-step
+    uint32_t offA[TA], offB[TB];
+#pragma unroll
+    for (int t = 0; t < TA; ++t) offA[t] = swz(ai * 16 + jbase + 2 * t, 2 * kpa);
+#pragma unroll
+    for (int t = 0; t < TB; ++t) offB[t] = swz(rb, 2 * (kpb + 4 * (kq0 + t)));
     const uint32_t trow = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(32 * (w >> 2));
     float Vh[32], Vl[32];  // running sums of this thread's 32 accumulator cells
 #pragma unroll
@@ -396,7 +402,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       const int ka = 2 * kpa;
       const float2 wih = *reinterpret_cast<const float2*>(WI + (2 * ai) * KS + ka);
       const float2 wil = *reinterpret_cast<const float2*>(WI + (2 * ai + 1) * KS + ka);
-#pragma unroll 1
+#pragma unroll
       for (int t = 0; t < TA; ++t) {
         const int jj = jbase + 2 * t;
         const int k = ka;
@@ -408,13 +414,15 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         float s0[4], s1[4];
         slice4(__fmul_rn(ph0, mp[t]), __fmul_rn(pl0, mp[t]), s0);
         slice4(__fmul_rn(ph1, mp[t]), __fmul_rn(pl1, mp[t]), s1);
-        const uint32_t off = swz(ai * 16 + jj, k);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + off) = pack_slice(s0[u], s1[u], f16);
+          *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + offA[t]) = pack_slice(s0[u], s1[u], f16);
       }
       const int k0 = j * KS;
-#pragma unroll 1
+      // the whole k-step lies outside this energy's near window (and inside the real poles):
+      // no per-element test
+      const bool all_far = (k0 + KS <= klo || k0 >= khi) && k0 + KS <= g.N;
+#pragma unroll
       for (int t = 0; t < TB; ++t) {
         const int k = 2 * (kpb + 4 * (kq0 + t));
         const int kg = k0 + k;
@@ -423,16 +431,15 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         float rh0, rl0, rh1, rl1;
         df_recip_diff(ph.x, pl.x, eh, el, rh0, rl0);
         df_recip_diff(ph.y, pl.y, eh, el, rh1, rl1);
-        const bool far0 = (kg < klo || kg >= khi) && kg < g.N;
-        const bool far1 = (kg + 1 < klo || kg + 1 >= khi) && kg + 1 < g.N;
+        const bool far0 = all_far || ((kg < klo || kg >= khi) && kg < g.N);
+        const bool far1 = all_far || ((kg + 1 < klo || kg + 1 >= khi) && kg + 1 < g.N);
         const float m0 = far0 ? me : 0.0f, m1 = far1 ? me : 0.0f;
         float s0[4], s1[4];
         slice4(__fmul_rn(rh0, m0), __fmul_rn(rl0, m0), s0);
         slice4(__fmul_rn(rh1, m1), __fmul_rn(rl1, m1), s1);
-        const uint32_t off = swz(rb, k);
 #pragma unroll
         for (int v = 0; v < 4; ++v)
-          *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + off) = pack_slice(s0[v], s1[v], f16);
+          *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + offB[t]) = pack_slice(s0[v], s1[v], f16);
       }
       // the MMAs (and, in clusters, the bulk copies) read these slices through the async proxy
       fence_proxy_async_smem();
