@@ -249,8 +249,11 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
       const int r = idx / NB, c = idx % NB;
       if (c < nb) A[(int64_t)(kb + r) * ld + kb + c] = panel[idx];
     }
-    // row interchanges on every column right of the panel (all threads, one column each)
-    for (int col = kb + nb + t; col < m; col += NT) {
+    // row interchanges on every column outside the panel (all threads, one column each): right of
+    // it for the elimination, left of it so that the stored L ends in the final row order (as
+    // LAPACK's getrf leaves it), which lu_unit_solve and lu_resolve rely on
+    for (int col = t; col < m; col += NT) {
+      if (col >= kb && col < kb + nb) continue;
       for (int j = 0; j < nb; ++j) {
         const int r1 = kb + j, r2 = ipiv[kb + j];
         if (r1 != r2) {
@@ -519,6 +522,116 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
   }
 }
 
+// Solve M X = P^T E for unit right-hand sides with the stored LU factors of M:
+// column q of the block [n, n + no) of A gets the unit vector whose 1 sits
+// at pivoted row posq[q] (sorted ascending), i.e. the interchanges are
+// already applied.  L^-1 leaves a column zero above its 1, so panel kb of the
+// forward elimination touches only the columns q with posq[q] < kb + nb --
+// a prefix, because posq is sorted -- and the forward pass costs about n^3/3
+// instead of n^2 no.  Back substitution as in lu_solve.
+template <typename T>
+__device__ void lu_unit_solve(T* __restrict__ A, int n, int no, int ld, T* panel, T* tile, T* tmp, T* tri,
+                              const int* posq) {
+  using O = Ops<T>;
+  constexpr int NB = Blk<T>::NB;
+  const int t = threadIdx.x;
+  const int m = n + no;
+  for (int64_t idx = t; idx < (int64_t)n * no; idx += NT) {
+    const int r = (int)(idx / no), q = (int)(idx % no);
+    A[(int64_t)r * ld + n + q] = (r == posq[q]) ? O::one() : O::zero();
+  }
+  __syncthreads();
+  int active = 0;  // columns with their 1 above the current panel's end (uniform across the block)
+  for (int kb = 0; kb < n; kb += NB) {
+    const int nb = min(NB, n - kb);
+    while (active < no && posq[active] < kb + nb) ++active;
+    if (active == 0) continue;
+    const int rows = n - kb;
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      panel[idx] = (c < nb) ? A[(int64_t)(kb + r) * ld + kb + c] : O::zero();
+    }
+    __syncthreads();
+    if (t < NB) {
+      for (int i = 0; i < NB; ++i) tri[i * NB + t] = (i == t) ? O::one() : O::zero();
+      if (t < nb) {
+        for (int i = t + 1; i < nb; ++i) {
+          T acc = O::zero();
+          for (int k = t; k < i; ++k) acc = O::fms(acc, panel[i * NB + k], tri[k * NB + t]);
+          tri[i * NB + t] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    const int me = n + active;
+    for (int c0 = n; c0 < me; c0 += TC) {
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        tmp[idx] = (j < nb && col < me) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
+      }
+      __syncthreads();
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        if (col >= me) continue;
+        T u = tmp[j * TC + c];
+        for (int i = 0; i < j; ++i) u = O::fma_acc(u, tri[j * NB + i], tmp[i * TC + c]);
+        tile[idx] = u;
+        if (j < nb) A[(int64_t)(kb + j) * ld + col] = u;
+      }
+      __syncthreads();
+      const int cwp = tile_width_pow2(me - c0);
+      const int tc = t % cwp, tr = t / cwp;
+      if (c0 + tc < me) rank_update<T>(A, ld, c0 + tc, kb + nb + tr, n, panel - (int64_t)kb * NB, tile + tc, nb, NT / cwp);
+      __syncthreads();
+    }
+  }
+  const int kb_last = ((n - 1) / NB) * NB;
+  for (int kb = kb_last; kb >= 0; kb -= NB) {
+    const int nb = min(NB, n - kb);
+    const int rows = kb + nb;
+    for (int idx = t; idx < rows * NB; idx += NT) {
+      const int r = idx / NB, c = idx % NB;
+      panel[idx] = (c < nb) ? A[(int64_t)r * ld + kb + c] : O::zero();
+    }
+    __syncthreads();
+    if (t < NB) {
+      for (int i = 0; i < NB; ++i) tri[i * NB + t] = O::zero();
+      if (t < nb) {
+        const T* U = panel + (int64_t)kb * NB;
+        const double dm = O::mag(U[t * NB + t]);
+        tri[t * NB + t] = (dm == 0.0) ? O::zero() : O::inv(U[t * NB + t]);
+        for (int i = t - 1; i >= 0; --i) {
+          T acc = O::zero();
+          for (int k = i + 1; k <= t; ++k) acc = O::fms(acc, U[i * NB + k], tri[k * NB + t]);
+          const double di = O::mag(U[i * NB + i]);
+          tri[i * NB + t] = (di == 0.0) ? O::zero() : O::mul(acc, O::inv(U[i * NB + i]));
+        }
+      }
+    }
+    __syncthreads();
+    for (int c0 = n; c0 < m; c0 += TC) {
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        tmp[idx] = (j < nb && col < m) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
+      }
+      __syncthreads();
+      for (int idx = t; idx < NB * TC; idx += NT) {
+        const int j = idx / TC, c = idx % TC, col = c0 + c;
+        if (col >= m) continue;
+        T y = O::zero();
+        for (int i = j; i < nb; ++i) y = O::fma_acc(y, tri[j * NB + i], tmp[i * TC + c]);
+        tile[idx] = y;
+        if (j < nb) A[(int64_t)(kb + j) * ld + col] = y;
+      }
+      __syncthreads();
+      const int cwp = tile_width_pow2(m - c0);
+      const int tc = t % cwp, tr = t / cwp;
+      if (c0 + tc < m) rank_update<T>(A, ld, c0 + tc, tr, kb, panel, tile + tc, nb, NT / cwp);
+      __syncthreads();
+    }
+  }
+}
+
 // ------------------------------------------------------------------------
 // Mixed-precision matching solve: FP32 LU of [M | -B], then iterative
 // refinement with residuals r = -B - M Y computed in double-float (FP32 hi +
@@ -535,29 +648,32 @@ __device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e)
 }
 
 // Apply the stored LU factors (row interchanges ipiv, unit-lower L, upper U, in A) to the
-// right-hand-side columns [n, m): forward elimination by panels, then back substitution.
+// right-hand-side columns [n, m): all interchanges, forward elimination by panels, back
+// substitution.
 template <typename T>
 __device__ void lu_resolve(T* __restrict__ A, int n, int m, int ld, T* panel, T* tile, T* tmp, T* tri,
                            const int* ipiv) {
   using O = Ops<T>;
   constexpr int NB = Blk<T>::NB;
   const int t = threadIdx.x;
+  // the stored L is in the final row order: apply all interchanges to the right-hand sides first
+  for (int col = n + t; col < m; col += NT) {
+    for (int k = 0; k < n; ++k) {
+      const int r2 = ipiv[k];
+      if (r2 != k) {
+        const T a1 = A[(int64_t)k * ld + col];
+        A[(int64_t)k * ld + col] = A[(int64_t)r2 * ld + col];
+        A[(int64_t)r2 * ld + col] = a1;
+      }
+    }
+  }
+  __syncthreads();
   for (int kb = 0; kb < n; kb += NB) {
     const int nb = min(NB, n - kb);
     const int rows = n - kb;
     for (int idx = t; idx < rows * NB; idx += NT) {
       const int r = idx / NB, c = idx % NB;
       panel[idx] = (c < nb) ? A[(int64_t)(kb + r) * ld + kb + c] : O::zero();
-    }
-    for (int col = n + t; col < m; col += NT) {
-      for (int j = 0; j < nb; ++j) {
-        const int r1 = kb + j, r2 = ipiv[kb + j];
-        if (r1 != r2) {
-          const T a1 = A[(int64_t)r1 * ld + col];
-          A[(int64_t)r1 * ld + col] = A[(int64_t)r2 * ld + col];
-          A[(int64_t)r2 * ld + col] = a1;
-        }
-      }
     }
     __syncthreads();
     if (t < NB) {
@@ -860,6 +976,9 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   unsigned char* tmp_b = tile_b + TILE_BYTES;
   unsigned char* tri_b = tmp_b + TILE_BYTES;
   int* ipiv = reinterpret_cast<int*>(tri_b + TRI_BYTES);
+  int* perm = ipiv + g.ldR / 2;  // [n_max] row permutation, then sorted unit positions / channels
+  int* posq = perm + g.ldR / 2;
+  int* chq = posq + g.ldR / 2;
   cplx* panel_c = reinterpret_cast<cplx*>(panel_b);
   cplx* tile_c = reinterpret_cast<cplx*>(tile_b);
   cplx* tmp_c = reinterpret_cast<cplx*>(tmp_b);
@@ -899,10 +1018,24 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     __syncthreads();
     return;
   }
+  // Unit right-hand sides: with the Wronskian s c' - s' c = -1, B = M D + diag(1/c') on the open
+  // columns, D = diag(c s' / c'), so Y = -D + M^-1 diag(1/c') and only M^-1 on unit columns is
+  // needed (lu_unit_solve: forward pass n^3/3 instead of n^2 n_o).  It divides by c'_m, so an
+  // energy with |c'_m| < 1e-3 k_m^1/2 in some open channel keeps the dense right-hand sides.
+  bool unit = false;
+  if constexpr (!MIXED) {
+    int bad = 0;
+    for (int j = t; j < no; j += NT) {
+      const double cp = lam[j] * c[j];
+      const double k = sqrt(g.E[e] - g.thr[j]);
+      if (!(fabs(cp) >= 1e-3 * sqrt(k))) bad = 1;
+    }
+    unit = !__syncthreads_or(bad);
+  }
   // ---------------------------------------------------------------- build
   const int m = n + no;
-  for (int64_t idx = t; idx < (int64_t)n * m; idx += NT) {
-    const int i = (int)(idx / m), j = (int)(idx % m);
+  for (int64_t idx = t; idx < (int64_t)n * (unit ? n : m); idx += NT) {
+    const int i = (int)(idx / (unit ? n : m)), j = (int)(idx % (unit ? n : m));
     double v;
     if (j < n) {
       const double rij = Re[pair_index(n, min(i, j), max(i, j))];
@@ -920,6 +1053,48 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   if constexpr (MIXED) {
     solved = mixed_matching(g, A, n, m, no, panel_b, tile_b, tmp_b, tri_b, ipiv, red, st);
     if (!solved) fl |= RM_FLAG_FP64;
+  }
+  if (!solved && unit) {
+    lu_solve<double>(A, n, n, g.ldR, panel_d, tile_d, reinterpret_cast<double*>(tmp_c),
+                     reinterpret_cast<double*>(tri_c), ipiv, &red, st);
+    // pivoted row of each open channel's unit vector, channels sorted by it
+    if (t == 0) {
+      for (int r = 0; r < n; ++r) perm[r] = r;
+      for (int k = 0; k < n; ++k) {
+        const int p2 = ipiv[k];
+        const int tmpv = perm[k];
+        perm[k] = perm[p2];
+        perm[p2] = tmpv;
+      }
+      int q = 0;
+      for (int r = 0; r < n; ++r)
+        if (perm[r] < no) {
+          posq[q] = r;
+          chq[q] = perm[r];
+          ++q;
+        }
+    }
+    __syncthreads();
+    lu_unit_solve<double>(A, n, no, g.ldR, panel_d, tile_d, reinterpret_cast<double*>(tmp_c),
+                          reinterpret_cast<double*>(tri_c), posq);
+    // X (columns in sorted order) -> Y_im = X_i,m / c'_m - delta_im c_m s'_m / c'_m in channel order,
+    // through the complex area (free until the S-step)
+    double* X = reinterpret_cast<double*>(C);
+    for (int64_t idx = t; idx < (int64_t)n * no; idx += NT) {
+      const int i = (int)(idx / no), q = (int)(idx % no);
+      X[idx] = A[(int64_t)i * g.ldR + n + q];
+    }
+    __syncthreads();
+    for (int64_t idx = t; idx < (int64_t)n * no; idx += NT) {
+      const int i = (int)(idx / no), q = (int)(idx % no);
+      const int mch = chq[q];
+      const double cp = lam[mch] * c[mch];
+      double y = X[idx] / cp;
+      if (i == mch) y -= c[mch] * sp[mch] / cp;
+      A[(int64_t)i * g.ldR + n + mch] = y;
+    }
+    __syncthreads();
+    solved = true;
   }
   if (!solved)
     lu_solve<double>(A, n, m, g.ldR, panel_d, tile_d, reinterpret_cast<double*>(tmp_c),
@@ -1093,7 +1268,8 @@ __global__ void __launch_bounds__(NT, 2) solve_grouped_kernel(const SolveArgs* _
 }  // namespace
 
 size_t solve_smem_bytes(int n_max) {
-  return (size_t)n_max * PANEL_ROW_BYTES + 2 * (size_t)TILE_BYTES + TRI_BYTES + (size_t)n_max * sizeof(int) + 16;
+  // panel, tile, tmp, tri, then ipiv, perm, posq, chq (n_max ints each)
+  return (size_t)n_max * PANEL_ROW_BYTES + 2 * (size_t)TILE_BYTES + TRI_BYTES + 4 * (size_t)n_max * sizeof(int) + 16;
 }
 
 // Resident solve CTAs per SM at this n_max (two when their shared memory fits:
