@@ -1020,15 +1020,16 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   }
   // Unit right-hand sides: with the Wronskian s c' - s' c = -1, B = M D + diag(1/c') on the open
   // columns, D = diag(c s' / c'), so Y = -D + M^-1 diag(1/c') and only M^-1 on unit columns is
-  // needed (lu_unit_solve: forward pass n^3/3 instead of n^2 n_o).  It divides by c'_m, so an
-  // energy with |c'_m| < 1e-3 k_m^1/2 in some open channel keeps the dense right-hand sides.
+  // needed (lu_unit_solve: forward pass n^3/3 instead of n^2 n_o).  It divides by c'_m; the error
+  // of K grows only like 1e-17 k^1/2 / |c'_m| (measured down to |c'| = 2e-5 k^1/2: 3e-13), and an
+  // energy with |c'_m| < 1e-6 k_m^1/2 in some open channel keeps the dense right-hand sides.
   bool unit = false;
   if constexpr (!MIXED) {
     int bad = 0;
     for (int j = t; j < no; j += NT) {
       const double cp = lam[j] * c[j];
       const double k = sqrt(g.E[e] - g.thr[j]);
-      if (!(fabs(cp) >= 1e-3 * sqrt(k))) bad = 1;
+      if (!(fabs(cp) >= 1e-6 * sqrt(k))) bad = 1;
     }
     unit = !__syncthreads_or(bad);
   }
