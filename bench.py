@@ -35,7 +35,7 @@ SPLIT_PRODUCTS = 13      # BF16 slice products per far term in the tensor-core p
 # DRAM bytes (read + write) per energy from one ncu capture each, n_ch=256 / N=20000 wave,
 # 1000-energy launch (profiles/solve_grouped_kernel_n256_1000E.md,
 # profiles/polesum_tc_grouped_2x2_n256_1000E.md); scaled to a launch by its energies.
-DRAM_BYTES_PER_ENERGY_N256 = {"solve": 21.650e6, "polesum_split": 0.4638e6}
+DRAM_BYTES_PER_ENERGY_N256 = {"polesum_split": 0.4638e6}
 
 
 def measured_peaks():
@@ -80,8 +80,9 @@ def parse():
     ap.add_argument("--sel", type=int, default=1, help="number of selected initial channels")
     ap.add_argument("--chunk", type=int, default=0, help="energies per rm_run chunk (0: automatic)")
     ap.add_argument("--z", type=float, default=0.0, help="residual target charge of every wave (0: neutral)")
-    ap.add_argument("--solve", default="fp64", choices=["fp64", "mixed"],
-                    help="matching solve: FP64, or FP32 LU + double-float iterative refinement")
+    ap.add_argument("--solve", default="fp64", choices=["fp64", "mixed", "fp64_lu"],
+                    help="matching solve: FP64 (outgoing-wave form, LU fallback), FP32 LU + double-float "
+                         "iterative refinement, or FP64 LU for every energy")
     ap.add_argument("--dipole", action="store_true",
                     help="photoionisation: give every wave a bound-free dipole vector (sigma_PI per energy)")
     ap.add_argument("--cluster", default="", help="tensor-core cluster shape CXxCY (default: autotuned)")
@@ -121,24 +122,35 @@ def workload(args):
     return wl, stride
 
 
-def algorithmic_flops(wl, n_open_by_wave, n_sel):
+def algorithmic_flops(wl, n_open_by_wave, flags_by_wave, n_sel, solve):
     """Per-step FLOP counts of the method (not counting slice products).
 
-    pole sum 2 n_p N per energy; matching LU (2/3) n^3 + 2 n^2 n_o; S-step
-    (4/3) n_o^3 + 8 n_o^2 r: real flops of the complex-symmetric LDL^T of I - iK
-    (n_o^3 / 6 complex multiply-adds) and its solves -- the factorisation the
-    solve kernel performs (a general complex LU would be (8/3) n_o^3).
+    Pole sum 2 n_p N per energy.  Solve, per energy, the FP64 flops of the path
+    the energy took:
+    * outgoing-wave path (solve "fp64"): real LDL^T over the closed channels and
+      of the open Schur complement S', n^3 / 3 together, then the complex
+      symmetric LDL^T of Z, (4/3) n_o^3 (n_o^3 / 6 complex multiply-adds), and
+      its r unit right-hand sides, 8 n_o^2 r;
+    * LU path ("fp64_lu", "mixed", or RM_FLAG_LU energies, which also paid for
+      the outgoing-wave attempt): LU (2/3) n^3 + 2 n^2 n_o with dense
+      right-hand sides, then the LDL^T of I - iK, (4/3) n_o^3 + 8 n_o^2 r.
     """
     pole = 0.0
-    solve = 0.0
-    for w, no in zip(wl.waves, n_open_by_wave):
-        n = w.n
+    solve_fl = 0.0
+    for w, no, fl in zip(wl.waves, n_open_by_wave, flags_by_wave):
+        n = float(w.n)
         npair = n * (n + 1) / 2
         pole += 2.0 * npair * w.N * wl.n_e
         no = no.astype(np.float64)
-        solve += float(np.sum((2.0 / 3.0) * n ** 3 + 2.0 * n * n * no + (4.0 / 3.0) * no ** 3
-                              + 8.0 * no * no * n_sel))
-    return pole, solve
+        live = no > 0
+        sym = n ** 3 / 3.0 + (4.0 / 3.0) * no ** 3 + 8.0 * no * no * n_sel
+        lu = (2.0 / 3.0) * n ** 3 + 2.0 * n * n * no + (4.0 / 3.0) * no ** 3 + 8.0 * no * no * n_sel
+        if solve == "fp64":
+            per = np.where((fl & 64) != 0, sym + lu, sym)
+        else:
+            per = lu
+        solve_fl += float(np.sum(np.where(live, per, 0.0)))
+    return pole, solve_fl
 
 
 class Clocks:
@@ -304,13 +316,16 @@ def run_ours(args):
     units = world * len(wl.waves) * wl.n_e * args.steps
     value = units / (total_ms / 1000.0)
 
-    # open-channel counts for the FLOP model
-    n_open = []
+    # open-channel counts and per-energy solve paths for the FLOP model
+    n_open, flags = [], []
     for g, w in enumerate(wl.waves):
         no = np.zeros(wl.n_e, np.int32)
-        plan.results(g, 0, wl.n_e, n_open=no)
+        fl = np.zeros(wl.n_e, np.uint8)
+        plan.results(g, 0, wl.n_e, n_open=no, flags=fl)
         n_open.append(no)
-    pole_flops, solve_flops = algorithmic_flops(wl, n_open, len(sel))
+        flags.append(fl)
+    lu_fallback = int(sum(np.count_nonzero(f & 64) for f in flags))
+    pole_flops, solve_flops = algorithmic_flops(wl, n_open, flags, len(sel), args.solve)
     kern = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
     near_flops = 0.0
@@ -338,10 +353,14 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic(dom),
                 "peak_source": "FP64 pipe: nominal 1.25 TFLOP/s (a DFMA probe measured 1.2)",
                 "flops_per_launch": total_fl / n_l, "avg_launch_ms": avg_ms,
-                "flop_model": "per energy (2/3)n^3 + 2n^2 n_o (LU, dense right-hand sides) + (4/3)n_o^3 + "
-                              "8 n_o^2 r (LDL^T of I - iK); energies on the unit-right-hand-side path "
-                              "skip about 2/3 of the forward elimination, so the FP64 pipe does less "
-                              "work than counted (an effective rate)"}
+                "flop_model": ("per energy n^3/3 (real LDL^T: closed channels, then S') + (4/3)n_o^3 + "
+                               "8 n_o^2 r (complex LDL^T of Z and its unit right-hand sides); energies "
+                               "handed to LU (RM_FLAG_LU) add (2/3)n^3 + 2n^2 n_o + (4/3)n_o^3 + 8 n_o^2 r"
+                               if args.solve == "fp64" else
+                               "per energy (2/3)n^3 + 2n^2 n_o (LU, dense right-hand sides) + (4/3)n_o^3 + "
+                               "8 n_o^2 r (LDL^T of I - iK); energies on the unit-right-hand-side path "
+                               "skip about 2/3 of the forward elimination, so the FP64 pipe does less "
+                               "work than counted (an effective rate)")}
     roof_tc = None
     if "polesum_split" in kern:
         info = plan.info(0)
@@ -465,6 +484,7 @@ def run_ours(args):
                            "energy_chunk": plan.info(0)["chunk"],
                            "tc_cluster": "%dx%d" % plan.cluster(), "solve": args.solve,
                            "fp64_fallback_energies": fallback,
+                           "lu_path_energies": lu_fallback if args.solve == "fp64" else None,
                            "energies_per_step": wl.n_e, "waves": len(wl.waves),
                            "n_ch": [w.n for w in wl.waves][:4], "n_poles": [w.N for w in wl.waves][:4],
                            "n_sel": len(sel), "l2": "flushed (512 MB write) between timed steps",

@@ -78,16 +78,25 @@ typedef enum {
                                 iteration cap for some channel (z > 0 only); outputs are unreliable */
 #define RM_FLAG_FP64 32u     /* solve_prec = RM_SOLVE_MIXED: the FP32 refinement did not converge (or hit a
                                 zero pivot) and the matching system was solved in FP64 instead */
+#define RM_FLAG_LU 64u       /* rm_run / rm_xsec with solve_prec = RM_SOLVE_FP64: the outgoing-wave
+                                factorisation failed its growth or pivot check and the energy was solved
+                                by LU with partial pivoting instead (same results, more flops) */
 
 #define RM_LMAX 32           /* largest supported channel angular momentum */
 #define RM_MAX_SEL 64        /* largest number of selected initial channels */
 
-/* Precision of the matching (K-matrix) solve.  MIXED: LU in FP32, then iterative refinement
+/* Matching solve.  FP64: rm_kmatrix (and every wave with a dipole vector) solves for K by LU
+   with partial pivoting, then the S-step by an LDL^T of I - iK; rm_run and rm_xsec go straight
+   to the cross sections and eigenphase sum through the outgoing-wave form: the closed channels
+   eliminated by a real LDL^T, then one complex symmetric LDL^T of
+   Z = G - diag(h / (a h')), h = c + i s, on the open channels (about half the flops; an energy
+   whose real elimination shows large growth or a tiny pivot goes through LU, RM_FLAG_LU).
+   FP64_LU: the LU path for every energy.  MIXED: LU in FP32, then iterative refinement
    with residuals r = -B - M Y in double-float (FP32 hi + lo, error-free products and sums, about
    48 bits) and FP32 correction solves until the last correction is below 1e-11 of Y; an energy
    whose refinement stops contracting is solved again in FP64 (RM_FLAG_FP64).  The S-step stays
    FP64 (its eigenphase sum needs FP64 pivots). */
-typedef enum { RM_SOLVE_FP64 = 0, RM_SOLVE_MIXED = 1 } rm_solve_precision_t;
+typedef enum { RM_SOLVE_FP64 = 0, RM_SOLVE_MIXED = 1, RM_SOLVE_FP64_LU = 2 } rm_solve_precision_t;
 
 typedef struct rm_plan_s* rm_plan_t;
 

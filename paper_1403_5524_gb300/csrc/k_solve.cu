@@ -362,19 +362,22 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
 // the columns to its right in TC-column tiles, where a matrix column col takes
 // the tile column d_j L[col][kb+j] straight from the panel and updates rows
 // >= col only, and a right-hand-side column takes L11^-1 A12 as in lu_solve.
+// With nf < n only the first nf pivots are taken (m must equal n then): the
+// trailing block [nf, n) is left holding its Schur complement.
 template <typename T>
 __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* tile, T* tmp, T* tri,
-                          LUStat& st) {
+                          LUStat& st, int nf = -1) {
   using O = Ops<T>;
   constexpr int NB = Blk<T>::NB;
   const int t = threadIdx.x;
+  if (nf < 0) nf = n;
   st.pmin = INFINITY;
   st.pmax = 0.0;
   st.swaps = 0;
   st.singular = false;
   // ------------------------------------------------------------ factorisation
-  for (int kb = 0; kb < n; kb += NB) {
-    const int nb = min(NB, n - kb);
+  for (int kb = 0; kb < nf; kb += NB) {
+    const int nb = min(NB, nf - kb);
     const int rows = n - kb;
     // panel rows kb.., columns kb..kb+nb; in the diagonal block the upper half comes from the
     // (current) lower half by symmetry
@@ -465,6 +468,7 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
       __syncthreads();
     }
   }
+  if (m == n) return;
   // -------------------------------------------- D^-1, then back substitution
   for (int64_t idx = t; idx < (int64_t)n * (m - n); idx += NT) {
     const int i = (int)(idx / (m - n)), col = n + (int)(idx % (m - n));
@@ -854,6 +858,7 @@ struct SolveArgs {
   int dip;          // 1: photoionisation amplitudes from y
   double e0;        // initial bound-state energy (Ry)
   int mixed;        // 1: matching solve in FP32 + double-float iterative refinement
+  int lu_only;      // 1: no outgoing-wave path; every energy through LU
   int64_t mix_off;  // doubles from a slot's start to its mixed-precision area
   const double* asym;
   int64_t ld_asym;  // stride between lam, s, sp, c blocks
@@ -965,6 +970,238 @@ __device__ bool mixed_matching(const SolveArgs& g, double* A, int n, int m, int 
   return true;
 }
 
+// ------------------------------------------------------------------------
+// Outgoing-wave symmetric solve (cross sections and eigenphase sum only).
+//
+// With M = R - diag(c / (a c')) on open channels and R - diag(1 / (a Lambda))
+// on closed ones, the matching gives K = -diag(s'/c') - (1/a) C'^-1 X C'^-1,
+// C' = diag(c'), X the open-open block of M^-1 = the inverse of the Schur
+// complement S_oo = M_oo - M_oc M_cc^-1 M_co (Wronskian s c' - s' c = -1).
+// Writing h = c + i s and G = S_oo + diag(c / (a c')) (R's open block less the
+// closed channels' correction), the same algebra gives
+//   (I - iK)^-1 = diag(c'/h') - (i/a) diag(1/h') Z^-1 diag(1/h'),
+//   Z = G - diag(h / (a h'))   (complex symmetric, Im Z = diag(1/(a|h'|^2)) > 0),
+// so T = S - I has T_ji = -(2i/a) (Z^-1)_ji / (h'_j h'_i) - 2i delta_ji s'_i / h'_i,
+// and det(I - iK) = prod_j (c'_j h'_j) det Z / (det C'^2 det S_oo), whose
+// argument needs only the sign of det S_oo: that of det S'' for the congruent
+// S'' = V S_oo V = V G V - diag(c c' / (a |h'|^2)), V = diag(c' / |h'|), whose
+// entries stay bounded where c and c' grow like (ka)^-l at thresholds, i.e.
+// (-1)^(negative pivots of an LDL^T of S'').  Everything is regular where some
+// c'_j vanishes.  The cost is a real LDL^T over the closed channels
+// ((n^3 - n_o^3)/3 flops), one of S'' (n_o^3/3) and the complex one of Z
+// ((4/3) n_o^3) against (2/3) n^3 + n^2 n_o + n^3/3 + (4/3) n_o^3 for LU, unit
+// solves and the LDL^T of I - iK.  The real eliminations run without
+// interchanges.  With D_pp = (|L||D||L^T|)_pp (it bounds the backward error of
+// row p, and scales like the matrix under a diagonal congruence), max_p D_pp
+// must stay within 1e4 of the largest entry of M for the closed elimination,
+// which feeds Z (a backward error of at most about n u 1e4, below the split
+// pole sum's error in R), and within 1e6 of that of S'' for the inertia (an
+// eigenvalue within about 3e-8 of zero would be needed to flip a sign), and
+// every pivot must keep |d_p| >= 1e-8 D_pp, far above its rounding error of
+// about n u D_pp, so that no pivot is lost to cancellation.  An energy that
+// fails a test is solved by the LU path.
+constexpr double SYM_GROWTH_MAX = 1e4;          // closed elimination: max_p D_pp / max|M|
+constexpr double SYM_GROWTH_MAX_INERTIA = 1e6;  // S'': max_p D_pp / max|S''|
+constexpr double SYM_PIVOT_MIN = 1e-8;          // either: |d_p| / D_pp
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+__device__ double block_max(double v, Red& red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  if ((threadIdx.x & 31) == 0) red.v[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = red.v[0];
+  for (int w = 1; w < NWARP; ++w) r = fmax(r, red.v[w]);
+  __syncthreads();
+  return r;
+}
+
+// fixed summation order: the same bits on every run
+__device__ double block_sum(double v, Red& red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red.v[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < NWARP; ++w) r += red.v[w];
+  __syncthreads();
+  return r;
+}
+
+// For the first nf pivots of an LDL^T held in A (L below the diagonal, d on
+// it), with D_pp = sum_{k < min(p, nf)} L_pk^2 |d_k| (+ |d_p| for p < nf), the
+// diagonal of |L||D||L^T|: gmax = max_p D_pp over all n rows and
+// rmin = min_{p < nf} |d_p| / D_pp.  NaN counts as failing (gmax inf, rmin 0).
+// One warp per row.
+__device__ void ldl_check(const double* A, int n, int nf, int ld, Red& red, double& gmax, double& rmin) {
+  const int lane = threadIdx.x & 31;
+  double gm = 0.0, rm = INFINITY;
+  for (int p = threadIdx.x >> 5; p < n; p += NWARP) {
+    const int kend = min(p, nf);
+    double acc = 0.0;
+    for (int k = lane; k < kend; k += 32) {
+      const double l = A[(int64_t)p * ld + k];
+      acc = fma(l * l, fabs(A[(int64_t)k * ld + k]), acc);
+    }
+    acc = warp_sum(acc);
+    if (p < nf) {
+      const double d = fabs(A[(int64_t)p * ld + p]);
+      acc += d;
+      const double q = d / acc;
+      rm = (q == q) ? fmin(rm, q) : 0.0;
+    }
+    gm = (acc == acc) ? fmax(gm, acc) : INFINITY;
+  }
+  gmax = block_max(gm, red);
+  rmin = -block_max(-rm, red);
+}
+
+// Returns true when energy e is finished (outputs written), false when its
+// real eliminations fail the growth / pivot check and the caller must solve it
+// by the LU path (the workspace is then free).
+__device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned char* smem_raw, Red& red) {
+  const int n = g.n, nc = n - no, t = threadIdx.x, lane = t & 31;
+  unsigned char* panel_b = smem_raw;
+  unsigned char* tile_b = panel_b + (size_t)n * PANEL_ROW_BYTES;
+  unsigned char* tmp_b = tile_b + TILE_BYTES;
+  unsigned char* tri_b = tmp_b + TILE_BYTES;
+  double* A = g.slot + (int64_t)blockIdx.x * g.slot_doubles;
+  cplx* C = reinterpret_cast<cplx*>(A + (int64_t)n * g.ldR);
+  const int ld = g.ldR;
+  const double* Re = g.R + (int64_t)e * g.npR + g.roff;
+  const double* lam = g.asym + 0 * g.ld_asym + (int64_t)e * n;
+  const double* s = g.asym + 1 * g.ld_asym + (int64_t)e * n;
+  const double* sp = g.asym + 2 * g.ld_asym + (int64_t)e * n;
+  const double* c = g.asym + 3 * g.ld_asym + (int64_t)e * n;
+  // ------------------------------------- M, lower triangle, channels reversed (closed first)
+  double gm = 0.0;
+  for (int p = t >> 5; p < n; p += NWARP) {
+    const int i = n - 1 - p;
+    const double* Rrow = Re + pair_index(n, i, i);  // R_ij, j >= i, at Rrow[j - i]
+    for (int q = lane; q <= p; q += 32) {
+      const int j = n - 1 - q;
+      double v = Rrow[j - i];
+      if (q == p && i >= no) v -= 1.0 / (g.a * lam[i]);
+      A[(int64_t)p * ld + q] = v;
+      gm = fmax(gm, fabs(v));
+    }
+  }
+  gm = block_max(gm, red);
+  LUStat st;
+  double growth_c = 0.0, piv_c = INFINITY;
+  if (nc > 0) {
+    ldl_solve<double>(A, n, n, ld, reinterpret_cast<double*>(panel_b), reinterpret_cast<double*>(tile_b),
+                      reinterpret_cast<double*>(tmp_b), reinterpret_cast<double*>(tri_b), st, nc);
+    ldl_check(A, n, nc, ld, red, growth_c, piv_c);
+    growth_c /= gm;
+  }
+  // ------------------------------------- Z = G - diag(h / (a h')) and unit right-hand sides
+  const int r = g.n_sel, mc = no + r;
+  for (int64_t idx = t; idx < (int64_t)no * mc; idx += NT) {
+    const int i = (int)(idx / mc), j = (int)(idx % mc);
+    cplx v;
+    if (j < no) {
+      if (j > i) continue;  // the LDL^T reads the lower triangle only
+      v = cplx{A[(int64_t)(n - 1 - j) * ld + (n - 1 - i)], 0.0};
+      if (i == j) {
+        const double cp = lam[i] * c[i];
+        const double den = g.a * (cp * cp + sp[i] * sp[i]);
+        v.re -= (c[i] * cp + s[i] * sp[i]) / den;  // h / h' = (c c' + s s' + i (s c' - c s')) / |h'|^2
+        v.im -= (s[i] * cp - c[i] * sp[i]) / den;
+      }
+    } else {
+      v = cplx{(g.sel[j - no] == i) ? 1.0 : 0.0, 0.0};
+    }
+    C[(int64_t)i * g.ldC + j] = v;
+  }
+  __syncthreads();
+  // ------------------------------------- S'' = V G V - diag(c c' / (a |h'|^2)), in place, and its inertia
+  double* As = A + (int64_t)nc * ld + nc;
+  double* vsc = reinterpret_cast<double*>(tile_b);  // V_jj = c'_j / |h'_j| (tile area free until the LDL^T)
+  for (int j = t; j < no; j += NT) {
+    const double cp = lam[j] * c[j];
+    vsc[j] = cp / sqrt(cp * cp + sp[j] * sp[j]);
+  }
+  __syncthreads();
+  double sm = 0.0;
+  for (int p = t >> 5; p < no; p += NWARP) {
+    const int i = no - 1 - p;
+    for (int q = lane; q <= p; q += 32) {
+      const int j = no - 1 - q;
+      double v = vsc[i] * As[(int64_t)p * ld + q] * vsc[j];
+      if (q == p) {
+        const double cp = lam[i] * c[i];
+        v -= c[i] * cp / (g.a * (cp * cp + sp[i] * sp[i]));
+      }
+      As[(int64_t)p * ld + q] = v;
+      sm = fmax(sm, fabs(v));
+    }
+  }
+  sm = block_max(sm, red);
+  ldl_solve<double>(As, no, no, ld, reinterpret_cast<double*>(panel_b), reinterpret_cast<double*>(tile_b),
+                    reinterpret_cast<double*>(tmp_b), reinterpret_cast<double*>(tri_b), st);
+  double growth_s, piv_s;
+  ldl_check(As, no, no, ld, red, growth_s, piv_s);
+  growth_s /= sm;
+  int neg = 0;
+  for (int p = t; p < no; p += NT) neg += (As[(int64_t)p * ld + p] < 0.0) ? 1 : 0;
+  const double negs = block_sum((double)neg, red);
+  const bool ok = (growth_c <= SYM_GROWTH_MAX) && (growth_s <= SYM_GROWTH_MAX_INERTIA) && (piv_c >= SYM_PIVOT_MIN) &&
+                  (piv_s >= SYM_PIVOT_MIN);
+  if (!ok) return false;  // uniform: the values come from block reductions
+  // ------------------------------------- complex LDL^T of Z, x = Z^-1 e_sel
+  ldl_solve<cplx>(C, no, mc, g.ldC, reinterpret_cast<cplx*>(panel_b), reinterpret_cast<cplx*>(tile_b),
+                  reinterpret_cast<cplx*>(tmp_b), reinterpret_cast<cplx*>(tri_b), st);
+  // eta = -arg det(I - iK) = -(sum_j [arg h'_j + arg d_j + pi (c'_j < 0)] - pi neg(S''))  (mod 2 pi)
+  double ph = 0.0;
+  for (int j = t; j < no; j += NT) {
+    const double cp = lam[j] * c[j];
+    const cplx d = C[(int64_t)j * g.ldC + j];
+    ph += atan2(sp[j], cp) + atan2(d.im, d.re) + ((cp < 0.0) ? M_PI : 0.0);
+  }
+  ph = block_sum(ph, red) - M_PI * negs;
+  if (t == 0) {
+    if (g.out.flags) g.out.flags[e] = fl;
+    if (g.out.n_open) g.out.n_open[e] = no;
+    if (g.out.eta) {
+      double eta = -ph;
+      eta = eta - 2.0 * M_PI * floor((eta + M_PI) / (2.0 * M_PI));  // [-pi, pi)
+      if (eta == -M_PI) eta = M_PI;
+      g.out.eta[e] = eta;
+    }
+  }
+  // sigma_{i -> j} = (pi / k_i^2) |T_ji|^2 = (4 pi / k_i^2) |x_j / (a h'_j h'_i) + delta_ji s'_i / h'_i|^2
+  for (int q = 0; q < r; ++q) {
+    const int i = g.sel[q];
+    const bool open_i = i < no;
+    const double k2 = g.E[e] - g.thr[min(i, n - 1)];
+    double part = 0.0;
+    for (int j = t; j < n; j += NT) {
+      double sig = 0.0;
+      if (open_i && j < no) {
+        const double cpi = lam[i] * c[i], cpj = lam[j] * c[j];
+        const double di = cpi * cpi + sp[i] * sp[i], dj = cpj * cpj + sp[j] * sp[j];
+        const cplx hi_inv = cplx{cpi / di, -sp[i] / di}, hj_inv = cplx{cpj / dj, -sp[j] / dj};
+        const cplx x = C[(int64_t)j * g.ldC + no + q];
+        cplx u = x * hj_inv * hi_inv;
+        u = cplx{u.re / g.a, u.im / g.a};
+        if (j == i) u = u + cplx{sp[i] * hi_inv.re, sp[i] * hi_inv.im};
+        sig = 4.0 * M_PI / k2 * (u.re * u.re + u.im * u.im);
+      }
+      if (g.out.sig_sel) g.out.sig_sel[((int64_t)e * r + q) * n + j] = sig;
+      part += sig;
+    }
+    part = block_sum(part, red);
+    if (t == 0 && g.out.sig_tot) g.out.sig_tot[(int64_t)e * r + q] = part;
+  }
+  __syncthreads();
+  return true;
+}
+
 // One energy e of the argument block: build the matching system from R and the
 // asymptotic data, LU -> K, then (optionally) the complex S-step.
 template <bool MIXED>
@@ -1017,6 +1254,13 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
       for (int j = t; j < n; j += NT) g.out.pi_ch[(int64_t)e * n + j] = 0.0;
     __syncthreads();
     return;
+  }
+  if constexpr (!MIXED) {
+    const bool photo_req = g.dip && (g.out.pi_tot || g.out.pi_ch);
+    if (g.out.do_xsec && !g.out.K && !photo_req && !g.lu_only) {
+      if (sym_xsec(g, e, no, fl, smem_raw, red)) return;
+      fl |= RM_FLAG_LU;
+    }
   }
   // Unit right-hand sides: with the Wronskian s c' - s' c = -1, B = M D + diag(1/c') on the open
   // columns, D = diag(c s' / c'), so Y = -D + M^-1 diag(1/c') and only M^-1 on unit columns is
@@ -1315,6 +1559,7 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   g.dip = w.dip ? 1 : 0;
   g.e0 = w.e0;
   g.mixed = p.solve_mixed;
+  g.lu_only = p.solve_lu;
   g.mix_off = solve_mix_offset(p.n_max, p.n_sel + 1);
   g.asym = asym;
   g.ld_asym = ld_chunk;
@@ -1353,6 +1598,7 @@ cudaError_t group_setup_solve(Plan& p) {
     a.dip = w.dip ? 1 : 0;
     a.e0 = w.e0;
     a.mixed = p.solve_mixed;
+    a.lu_only = p.solve_lu;
     a.mix_off = solve_mix_offset(p.n_max, p.n_sel + 1);
     a.asym = G.asym[g];
     a.ld_asym = (int64_t)G.chunk * w.n;

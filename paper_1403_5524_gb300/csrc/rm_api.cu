@@ -586,7 +586,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     if (o.prec < RM_PREC_FP64 || o.prec > RM_PREC_FP32_SIMT) return fail(RM_ERR_ARG, "bad precision mode");
     if (o.prec != RM_PREC_FP64 && !(o.delta > 0.0)) return fail(RM_ERR_ARG, "delta must be > 0");
     if (o.chunk < 0) return fail(RM_ERR_ARG, "chunk must be >= 0");
-    if (o.solve_prec != RM_SOLVE_FP64 && o.solve_prec != RM_SOLVE_MIXED)
+    if (o.solve_prec != RM_SOLVE_FP64 && o.solve_prec != RM_SOLVE_MIXED && o.solve_prec != RM_SOLVE_FP64_LU)
       return fail(RM_ERR_ARG, "bad solve precision");
     if (!(o.cluster_x == 0 || o.cluster_x == 1 || o.cluster_x == 2 || o.cluster_x == 4) ||
         !(o.cluster_y == 0 || o.cluster_y == 1 || o.cluster_y == 2 || o.cluster_y == 4) ||
@@ -694,6 +694,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       p->chunk = chunk;
       p->solve_slots = p->sm_count * solve_blocks_per_sm(n_max);
       p->solve_mixed = o.solve_prec == RM_SOLVE_MIXED ? 1 : 0;
+      p->solve_lu = o.solve_prec == RM_SOLVE_FP64_LU ? 1 : 0;
       p->slot_doubles = solve_slot_doubles(n_max, n_sel + 1, p->solve_mixed != 0);  // + the dipole column
       if (st == RM_OK) st = dalloc(p, &p->energies, n_e);
       if (st == RM_OK) st = dalloc(p, &p->sel_dev, n_sel);

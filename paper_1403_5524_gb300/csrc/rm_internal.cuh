@@ -124,6 +124,7 @@ struct Plan {
   int n_max = 0;
   int nR_max = 0;   // largest pole-sum row count (n_ch + 1 with a dipole vector)
   int solve_mixed = 0;  // matching solve in FP32 + double-float iterative refinement
+  int solve_lu = 0;     // cross sections through LU + LDL^T of I - iK for every energy
   int sm_count = 0;
   double* energies = nullptr;  // [n_e] raw mesh (device)
   std::vector<WaveDev> waves;

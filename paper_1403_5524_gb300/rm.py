@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(_HERE, "librm.so")
 RM_OK, RM_ERR_ARG, RM_ERR_ORDER, RM_ERR_NOMEM, RM_ERR_CUDA, RM_ERR_TIMEOUT, RM_ERR_STATE = range(7)
 RM_MEM_HOST, RM_MEM_DEVICE = 0, 1
 RM_PREC_FP64, RM_PREC_SPLIT_BF16, RM_PREC_SPLIT_FP16, RM_PREC_FP32_SIMT = 0, 1, 2, 3
-FLAG_NUDGED, FLAG_ILLCOND, FLAG_NO_OPEN, FLAG_SINGULAR, FLAG_ASYM, FLAG_FP64 = 1, 2, 4, 8, 16, 32
-SOLVE = {"fp64": 0, "mixed": 1}
+FLAG_NUDGED, FLAG_ILLCOND, FLAG_NO_OPEN, FLAG_SINGULAR, FLAG_ASYM, FLAG_FP64, FLAG_LU = 1, 2, 4, 8, 16, 32, 64
+SOLVE = {"fp64": 0, "mixed": 1, "fp64_lu": 2}
 
 PREC = {"fp64": RM_PREC_FP64, "split_bf16": RM_PREC_SPLIT_BF16, "split_fp16": RM_PREC_SPLIT_FP16,
         "fp32_simt": RM_PREC_FP32_SIMT}

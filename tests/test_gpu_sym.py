@@ -1,0 +1,161 @@
+"""The outgoing-wave cross-section path against the LU path and the oracle (needs a GPU).
+
+With solve "fp64", rm_run and rm_xsec take the cross sections and the eigenphase
+sum from Z = G - diag(h / (a h')), h = c + i s, G the open block of
+M = R - diag(c / (a c')) (closed: R - diag(1 / (a Lambda))) less the closed
+channels' Schur correction; solve "fp64_lu" solves K by LU for every energy and
+then I - iK.  Both are FP64 solves of the same matching equations from the
+same R, so they differ by rounding amplified by the conditioning, as the LU
+path differs from the oracle: the tolerances are those of the FP64 parity
+tests (1e-9 on sigma normalised by the total of its initial channel, on eta
+mod 2 pi).  Cases: a contiguous block of the n_ch = 64 mesh (thresholds up to
+2 Ry, so 1..64 open channels), a Coulomb wave, an energy where the first
+closed pivot vanishes (must go through LU, RM_FLAG_LU), and one where c'_0 = 0
+(K is regular there, but M and the unit-right-hand-side LU form divide by c').
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import rmatrix as orc
+from paper_1403_5524_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FLAG_LU = 64
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def rm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1403_5524_gb300 import rm as _rm
+    _rm.load_library()
+    return _rm
+
+
+def run(rm, wl, solve, sel=(0,), prec="fp64"):
+    w = wl.waves[0]
+    with rm.Plan(wl.waves, wl.energies, prec=prec, sel=sel, solve=solve) as p:
+        p.run()
+        out = rm.host_outputs(wl.n_e, w.n, len(sel))
+        p.results(0, 0, wl.n_e, **out)
+    return out
+
+
+def close(a, b, idx=None, tol=TOL):
+    idx = np.arange(a["eigsum"].shape[0]) if idx is None else idx
+    for e in idx:
+        st = b["sig_tot"][e]
+        for q in range(st.shape[0]):
+            if st[q] == 0:
+                assert np.all(a["sig_sel"][e, q] == 0), (e, q)
+                continue
+            err = np.abs(a["sig_sel"][e, q] - b["sig_sel"][e, q]).max() / st[q]
+            assert err <= tol, (e, q, err)
+            assert abs(a["sig_tot"][e, q] - st[q]) <= tol * st[q], (e, q)
+        assert abs(orc.wrap_angle(a["eigsum"][e] - b["eigsum"][e])) <= 10 * tol, e
+
+
+def as_ref(ref):
+    return {"eigsum": ref["eta"], "sig_tot": ref["sig_tot"], "sig_sel": ref["sig_sel"]}
+
+
+def test_config2_block_matches_lu_path(rm):
+    wl = synth.config(2)
+    sub = synth.Workload(wl.name, wl.waves, wl.energies[2000:2800])  # 0.41 .. 0.57 Ry: 12..20 open
+    a = run(rm, sub, "fp64", sel=(0, 3))
+    b = run(rm, sub, "fp64_lu", sel=(0, 3))
+    assert np.array_equal(a["n_open"], b["n_open"])
+    assert np.array_equal(a["flags"] & ~np.uint8(FLAG_LU), b["flags"])
+    assert np.count_nonzero(a["flags"] & FLAG_LU) < sub.n_e // 20  # the LU fallback stays rare
+    close(a, b)
+    idx = np.arange(0, sub.n_e, 37)
+    ref = orc.sweep(wl.waves[0], sub.energies, sel=(0, 3), energy_idx=idx, keep_R=False, keep_K=False)
+    close({k: v[idx] for k, v in a.items()}, as_ref(ref))
+
+
+def test_all_open_and_ragged(rm):
+    # energies above every threshold (no closed channel: no real elimination) and n not a
+    # multiple of the panel widths
+    wl = synth.small(41, 37, 300, 90, e_lo=0.05, e_hi=4.0, thr_hi=1.5, pole_lo=-2.0, pole_hi=8.0,
+                     a=15.0)
+    sel = (0, 1, 36)
+    a = run(rm, wl, "fp64", sel=sel)
+    ref = orc.sweep(wl.waves[0], wl.energies, sel=sel, keep_R=False, keep_K=False)
+    assert np.array_equal(a["n_open"], ref["n_open"])
+    close(a, as_ref(ref))
+
+
+def test_coulomb_matches_lu_path(rm):
+    wl = synth.small(7, 12, 160, 120, e_lo=0.02, e_hi=2.5, z=1.0)
+    a = run(rm, wl, "fp64", sel=(0, 2))
+    b = run(rm, wl, "fp64_lu", sel=(0, 2))
+    close(a, b)
+
+
+def bisect(f, lo, hi, it=200):
+    flo = f(lo)
+    for _ in range(it):
+        mid = 0.5 * (lo + hi)
+        if mid in (lo, hi):
+            break
+        fm = f(mid)
+        if (fm < 0) == (flo < 0):
+            lo, flo = mid, fm
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_vanishing_closed_pivot_goes_through_lu(rm):
+    # The first closed pivot (last channel, eliminated first) is d = R_nn - 1/(a Lambda_n); between
+    # two poles R_nn rises from -inf to +inf, so it vanishes once.  There the outgoing-wave path must
+    # hand the energy to LU, whose results still match the oracle.
+    wl0 = synth.small(12, 6, 60, 1, pole_lo=0.0, pole_hi=3.0, thr_hi=2.5, a=10.0)
+    w = wl0.waves[0]
+    last = w.n - 1
+
+    def d0(E):
+        R = orc.rmatrix(w.W, w.poles, E, w.a)
+        lam = orc.channel_functions(w.l, w.thresh, E, w.a)["lam"][last]
+        return R[last, last] - 1.0 / (w.a * lam)
+
+    k = int(np.searchsorted(w.poles, 0.3))
+    while w.poles[k + 1] - w.poles[k] < 0.02:
+        k += 1
+    assert w.poles[k + 1] < w.thresh[last]
+    lo, hi = w.poles[k] + 1e-7, w.poles[k + 1] - 1e-7
+    assert d0(lo) < 0 < d0(hi)
+    Es = bisect(d0, lo, hi)
+    E = np.array([Es - 0.01, Es, Es + 0.01]) if Es + 0.01 < w.poles[k + 1] else np.array([Es - 0.01, Es])
+    wl = synth.Workload("pivot", [w], np.sort(E))
+    a = run(rm, wl, "fp64", sel=(0,))
+    i = int(np.nonzero(wl.energies == Es)[0][0])
+    assert a["flags"][i] & FLAG_LU
+    ref = orc.sweep(w, wl.energies, sel=(0,), keep_R=False, keep_K=False)
+    close(a, as_ref(ref))
+
+
+def test_regular_where_c_prime_vanishes(rm):
+    # c'_0 = 0 at k a = x with nhat_l'(x) = 0: M's diagonal term c / (a c') diverges there, Z does not.
+    wl0 = synth.small(13, 5, 50, 1, pole_lo=-1.0, pole_hi=6.0, thr_hi=1.0, a=12.0)
+    w = wl0.waves[0]
+    l0 = int(w.l[0])
+
+    def cp0(E):
+        return orc.riccati_yn(l0, math.sqrt(E) * w.a)[1]
+
+    grid = np.linspace(1.2, 2.5, 400)
+    v = np.array([cp0(E) for E in grid])
+    j = int(np.nonzero(np.sign(v[1:]) != np.sign(v[:-1]))[0][0])
+    Es = bisect(cp0, grid[j], grid[j + 1])
+    E = np.array([Es - 1e-3, Es, Es + 1e-3])
+    assert np.min(np.abs(w.poles[:, None] - E[None, :])) > 1e-6
+    wl = synth.Workload("cprime", [w], E)
+    a = run(rm, wl, "fp64", sel=(0, 1))
+    ref = orc.sweep(w, wl.energies, sel=(0, 1), keep_R=False, keep_K=False)
+    close(a, as_ref(ref))
