@@ -11,6 +11,8 @@
  * open-open K-matrix by LU with partial pivoting, and reduces K to
  * S = (I + iK)(I - iK)^-1, the eigenphase sum and partial cross sections
  * sigma_{i->j} = (pi / k_i^2) |T_ji|^2, T = S - I (weights (2J+1)/g_i = 1).
+ * Cross sections and eigenphase sums (rm_xsec, rm_run) come by default from
+ * the equivalent outgoing-wave form without K (see rm_solve_precision_t).
  * Units: Rydberg energies, bohr lengths, k^2 = E - e_i, sigma in bohr^2.
  *
  * Threading and streams.  A plan belongs to one CUDA device and one stream
