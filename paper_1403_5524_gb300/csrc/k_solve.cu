@@ -57,6 +57,8 @@ struct Ops<double> {
   __device__ static double mul(double a, double b) { return a * b; }
   __device__ static double fms(double acc, double a, double b) { return fma(-a, b, acc); }
   __device__ static double fma_acc(double acc, double a, double b) { return fma(a, b, acc); }
+  __device__ static void put(double* d, double x) { d[0] = x; }
+  __device__ static double get(const double* d) { return d[0]; }
 };
 
 template <>
@@ -68,6 +70,8 @@ struct Ops<float> {
   __device__ static float mul(float a, float b) { return a * b; }
   __device__ static float fms(float acc, float a, float b) { return fmaf(-a, b, acc); }
   __device__ static float fma_acc(float acc, float a, float b) { return fmaf(a, b, acc); }
+  __device__ static void put(double* d, float x) { d[0] = x; }
+  __device__ static float get(const double* d) { return (float)d[0]; }
 };
 
 template <>
@@ -91,6 +95,8 @@ struct Ops<cplx> {
   __device__ static cplx fma_acc(cplx acc, cplx a, cplx b) {
     return cplx{fma(a.re, b.re, fma(-a.im, b.im, acc.re)), fma(a.re, b.im, fma(a.im, b.re, acc.im))};
   }
+  __device__ static void put(double* d, cplx x) { d[0] = x.re; d[1] = x.im; }
+  __device__ static cplx get(const double* d) { return cplx{d[0], d[1]}; }
 };
 
 // Panel width: 16 columns for the real LU, 8 for the complex one, so that a
@@ -124,6 +130,7 @@ struct Red {
   double v[NWARP];
   int i[NWARP];
   int piv;
+  double pinv[2];  // reciprocal of the chosen pivot (re, im; real types use [0])
 };
 
 // Block-wide argmax of Ops::mag over panel column j, rows [j, rows); ties -> smallest row.
@@ -151,6 +158,9 @@ __device__ int panel_argmax(const T* panel, int rows, int j, Red* red) {
     for (int q = 1; q < NWARP; ++q)
       if (red->v[q] > b || (red->v[q] == b && red->i[q] < bi)) { b = red->v[q]; bi = red->i[q]; }
     red->piv = bi;
+    // one reciprocal per pivot, shared by the block (bi < rows whenever rows > j)
+    const T pv = (bi < rows) ? panel[bi * NB + j] : Ops<T>::zero();
+    Ops<T>::put(red->pinv, (Ops<T>::mag(pv) == 0.0) ? Ops<T>::zero() : Ops<T>::inv(pv));
   }
   __syncthreads();
   return red->piv;
@@ -230,14 +240,13 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
         if (p != j) st.swaps++;
       }
       __syncthreads();
-      const T piv = panel[j * NB + j];
-      const double pm = O::mag(piv);
       if (t == 0) {
+        const double pm = O::mag(panel[j * NB + j]);
         st.pmin = fmin(st.pmin, pm);
         st.pmax = fmax(st.pmax, pm);
         if (pm == 0.0) st.singular = true;
       }
-      const T pinv = (pm == 0.0) ? O::zero() : O::inv(piv);
+      const T pinv = O::get(red->pinv);
       for (int r = j + 1 + t; r < rows; r += NT) {
         const T lr = O::mul(panel[r * NB + j], pinv);
         panel[r * NB + j] = lr;
@@ -371,6 +380,7 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
   constexpr int NB = Blk<T>::NB;
   const int t = threadIdx.x;
   if (nf < 0) nf = n;
+  __shared__ double s_pinv[2][2];
   st.pmin = INFINITY;
   st.pmax = 0.0;
   st.swaps = 0;
@@ -387,20 +397,29 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
       if (c < nb) v = (r >= c) ? A[(int64_t)(kb + r) * ld + kb + c] : A[(int64_t)(kb + c) * ld + kb + r];
       panel[idx] = v;
     }
+    // One reciprocal per pivot, double-buffered: thread 0 loads the first pivot and, at step j,
+    // updates row j + 1 (whose diagonal is then the next pivot), so it computes each one.
+    if (t == 0) {
+      const T p0 = panel[0];
+      O::put(s_pinv[0], (O::mag(p0) == 0.0) ? O::zero() : O::inv(p0));
+    }
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-      const T piv = panel[j * NB + j];
-      const double pm = O::mag(piv);
       if (t == 0) {
+        const double pm = O::mag(panel[j * NB + j]);
         st.pmin = fmin(st.pmin, pm);
         st.pmax = fmax(st.pmax, pm);
         if (pm == 0.0) st.singular = true;
       }
-      const T pinv = (pm == 0.0) ? O::zero() : O::inv(piv);
+      const T pinv = O::get(s_pinv[j & 1]);
       for (int r = j + 1 + t; r < rows; r += NT) {
         const T lr = O::mul(panel[r * NB + j], pinv);
         panel[r * NB + j] = lr;
         for (int c = j + 1; c < nb; ++c) panel[r * NB + c] = O::fms(panel[r * NB + c], lr, panel[j * NB + c]);
+        if (r == j + 1 && r < nb) {
+          const T pn = panel[r * NB + r];
+          O::put(s_pinv[r & 1], (O::mag(pn) == 0.0) ? O::zero() : O::inv(pn));
+        }
       }
       __syncthreads();
     }
