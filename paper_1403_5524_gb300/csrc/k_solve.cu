@@ -439,16 +439,20 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
       }
     }
     __syncthreads();
-    for (int c0 = kb + nb; c0 < m; c0 += TC) {
+    // Matrix columns in TC-wide tiles up to n, then the right-hand-side columns in tiles of their
+    // own: those run every row below the panel, the matrix columns only the rows below their
+    // tile's diagonal block, so sharing a warp would leave lanes idle.
+    for (int c0 = kb + nb; c0 < m;) {
+      const int ce = (c0 < n) ? min(c0 + TC, n) : min(c0 + TC, m);
       // tile column: d_j L[col][kb+j] for matrix columns, L11^-1 A12 for right-hand sides
       for (int idx = t; idx < NB * TC; idx += NT) {
         const int j = idx / TC, c = idx % TC, col = c0 + c;
-        tmp[idx] = (j < nb && col >= n && col < m) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
+        tmp[idx] = (j < nb && col >= n && col < ce) ? A[(int64_t)(kb + j) * ld + col] : O::zero();
       }
       __syncthreads();
       for (int idx = t; idx < NB * TC; idx += NT) {
         const int j = idx / TC, c = idx % TC, col = c0 + c;
-        if (col >= m) continue;
+        if (col >= ce) continue;
         T u;
         if (col < n) {
           u = (j < nb) ? O::mul(panel[j * NB + j], panel[(col - kb) * NB + j]) : O::zero();
@@ -460,18 +464,17 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
         tile[idx] = u;
       }
       __syncthreads();
-      // matrix columns [c0, cm) of this tile: the rows below its diagonal block as one rectangle
-      // (every lane of a warp runs the same rows), the block's lower triangle element by element;
+      // matrix columns [c0, ce): the rows below the tile's diagonal block as one rectangle (every
+      // lane of a warp runs the same rows), the block's lower triangle element by element;
       // right-hand-side columns: all rows below the panel
-      const int cm = min(c0 + TC, n);
-      const int cwp = tile_width_pow2(m - c0);
+      const int cwp = tile_width_pow2(ce - c0);
       const int tc = t % cwp, tr = t / cwp;
       const int col = c0 + tc;
-      if (col < m) {
-        const int rs = (col < n) ? max(kb + nb, cm) : kb + nb;
+      if (col < ce) {
+        const int rs = (col < n) ? max(kb + nb, ce) : kb + nb;
         rank_update<T>(A, ld, col, rs + tr, n, panel - (int64_t)kb * NB, tile + tc, nb, NT / cwp);
       }
-      const int w = cm - c0;
+      const int w = (c0 < n) ? ce - c0 : 0;
       for (int q = t; q < w * (w + 1) / 2; q += NT) {
         int rr = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
         while (rr * (rr + 1) / 2 > q) --rr;
@@ -485,6 +488,7 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
         A[(int64_t)r * ld + c0 + cc] = v;
       }
       __syncthreads();
+      c0 = ce;
     }
   }
   if (m == n) return;
