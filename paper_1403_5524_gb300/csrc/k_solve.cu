@@ -380,7 +380,7 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
   constexpr int NB = Blk<T>::NB;
   const int t = threadIdx.x;
   if (nf < 0) nf = n;
-  __shared__ double s_pinv[2][2];
+  __shared__ double s_pinv[Blk<T>::NB][2];  // pivot reciprocals of the current panel
   st.pmin = INFINITY;
   st.pmax = 0.0;
   st.swaps = 0;
@@ -397,38 +397,55 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
       if (c < nb) v = (r >= c) ? A[(int64_t)(kb + r) * ld + kb + c] : A[(int64_t)(kb + c) * ld + kb + r];
       panel[idx] = v;
     }
-    // One reciprocal per pivot, double-buffered: thread 0 loads the first pivot and, at step j,
-    // updates row j + 1 (whose diagonal is then the next pivot), so it computes each one.
-    if (t == 0) {
-      const T p0 = panel[0];
-      O::put(s_pinv[0], (O::mag(p0) == 0.0) ? O::zero() : O::inv(p0));
+    __syncthreads();
+    // The nb x nb diagonal block by warp 0 (one reciprocal per pivot, lane 0); its upper half then
+    // holds each pivot row as it was when eliminated, so every row below the block finishes its
+    // nb panel entries on its own, in registers, with the same operations in the same order.
+    if (t < 32) {
+      for (int j = 0; j < nb; ++j) {
+        if (t == 0) {
+          const T pv = panel[j * NB + j];
+          const double pm = O::mag(pv);
+          st.pmin = fmin(st.pmin, pm);
+          st.pmax = fmax(st.pmax, pm);
+          if (pm == 0.0) st.singular = true;
+          O::put(s_pinv[j], (pm == 0.0) ? O::zero() : O::inv(pv));
+        }
+        __syncwarp();
+        const T pinv = O::get(s_pinv[j]);
+        const int r = j + 1 + t;
+        if (r < nb) {
+          const T lr = O::mul(panel[r * NB + j], pinv);
+          panel[r * NB + j] = lr;
+          for (int c = j + 1; c < nb; ++c) panel[r * NB + c] = O::fms(panel[r * NB + c], lr, panel[j * NB + c]);
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-      if (t == 0) {
-        const double pm = O::mag(panel[j * NB + j]);
-        st.pmin = fmin(st.pmin, pm);
-        st.pmax = fmax(st.pmax, pm);
-        if (pm == 0.0) st.singular = true;
-      }
-      const T pinv = O::get(s_pinv[j & 1]);
-      for (int r = j + 1 + t; r < rows; r += NT) {
-        const T lr = O::mul(panel[r * NB + j], pinv);
-        panel[r * NB + j] = lr;
-        for (int c = j + 1; c < nb; ++c) panel[r * NB + c] = O::fms(panel[r * NB + c], lr, panel[j * NB + c]);
-        if (r == j + 1 && r < nb) {
-          const T pn = panel[r * NB + r];
-          O::put(s_pinv[r & 1], (O::mag(pn) == 0.0) ? O::zero() : O::inv(pn));
+    for (int r = nb + t; r < rows; r += NT) {
+      T a[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) a[c] = panel[r * NB + c];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (j < nb) {
+          a[j] = O::mul(a[j], O::get(s_pinv[j]));
+#pragma unroll
+          for (int c = j + 1; c < NB; ++c)
+            if (c < nb) a[c] = O::fms(a[c], a[j], panel[j * NB + c]);
         }
       }
-      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < NB; ++c) panel[r * NB + c] = a[c];
     }
+    __syncthreads();
     for (int idx = t; idx < rows * NB; idx += NT) {
       const int r = idx / NB, c = idx % NB;
       if (c < nb && r >= c) A[(int64_t)(kb + r) * ld + kb + c] = panel[idx];
     }
     // inverse of the unit-lower diagonal block (for the right-hand sides), column t by thread t
-    if (t < NB) {
+    if (m > n && t < NB) {
       for (int i = 0; i < NB; ++i) tri[i * NB + t] = (i == t) ? O::one() : O::zero();
       if (t < nb) {
         for (int i = t + 1; i < nb; ++i) {
@@ -1489,8 +1506,9 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   }
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
+// MINB: CTAs per SM the registers are sized for (3 when three CTAs' shared memory fits).
+template <bool MIXED, int MINB>
+__global__ void __launch_bounds__(NT, MINB) solve_kernel(SolveArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Red red;
   __shared__ double s_acc;
@@ -1500,8 +1518,8 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
 // All waves of a plan: persistent CTAs claim (wave, chunk energy) units from a
 // list sorted by decreasing cost through an atomic counter.  Per-wave
 // arguments hold base pointers; the chunk offset e_begin is applied here.
-template <bool MIXED>
-__global__ void __launch_bounds__(NT, 2) solve_grouped_kernel(const SolveArgs* __restrict__ waves,
+template <bool MIXED, int MINB>
+__global__ void __launch_bounds__(NT, MINB) solve_grouped_kernel(const SolveArgs* __restrict__ waves,
                                                               const int2* __restrict__ units, int n_units,
                                                               int64_t e_begin, int ne, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1540,20 +1558,30 @@ size_t solve_smem_bytes(int n_max) {
   return (size_t)n_max * PANEL_ROW_BYTES + 2 * (size_t)TILE_BYTES + TRI_BYTES + 4 * (size_t)n_max * sizeof(int) + 16;
 }
 
-// Resident solve CTAs per SM at this n_max (two when their shared memory fits:
-// one CTA's barrier and load bubbles are then filled by the other's FMAs).
-int solve_blocks_per_sm(int n_max) {
+// Resident solve CTAs per SM at this n_max: three when their shared memory fits (registers capped
+// at 80 per thread), else two (one CTA's barrier, division and load latencies are filled by the
+// others' FMAs).  The mixed-precision kernels need their 128 registers and stay at two.
+int solve_blocks_per_sm(int n_max, bool mixed) {
   const int smem = (int)solve_smem_bytes(n_max);
-  int b = 0;
-  if (cudaFuncSetAttribute(solve_grouped_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(solve_grouped_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, solve_grouped_kernel<false>, NT, smem) != cudaSuccess) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (cudaFuncSetAttribute(solve_grouped_kernel<false, 2>, a, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(solve_grouped_kernel<false, 3>, a, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(solve_grouped_kernel<true, 2>, a, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(solve_kernel<false, 2>, a, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(solve_kernel<false, 3>, a, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(solve_kernel<true, 2>, a, smem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
-  return b < 1 ? 1 : (b > 2 ? 2 : b);
+  int b3 = 0, b2 = 0;
+  if (!mixed && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, solve_grouped_kernel<false, 3>, NT, smem) ==
+                    cudaSuccess && b3 >= 3)
+    return 3;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, solve_grouped_kernel<false, 2>, NT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return b2 < 1 ? 1 : (b2 > 2 ? 2 : b2);
 }
 
 // slot layout: real augmented matrix n_max x 2 n_max, complex n_max x (n_max + n_sel), then
@@ -1598,7 +1626,7 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   g.ldC = p.n_max + p.n_sel + 1;  // + the dipole right-hand side
   g.out = out;
   const size_t smem = solve_smem_bytes(p.n_max);
-  auto kern = p.solve_mixed ? solve_kernel<true> : solve_kernel<false>;
+  auto kern = p.solve_mixed ? solve_kernel<true, 2> : (p.solve_bps >= 3 ? solve_kernel<false, 3> : solve_kernel<false, 2>);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int grid = min(ne, p.solve_slots);
@@ -1672,11 +1700,12 @@ cudaError_t group_setup_solve(Plan& p) {
     return err;
   if ((err = cudaMemcpy(G.units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
     return err;
-  cudaError_t e2 = cudaFuncSetAttribute(solve_grouped_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)solve_smem_bytes(p.n_max));
+  const int smem = (int)solve_smem_bytes(p.n_max);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e2 = cudaFuncSetAttribute(solve_grouped_kernel<true, 2>, a, smem);
+  if (e2 == cudaSuccess) e2 = cudaFuncSetAttribute(solve_grouped_kernel<false, 3>, a, smem);
   if (e2 != cudaSuccess) return e2;
-  return cudaFuncSetAttribute(solve_grouped_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)solve_smem_bytes(p.n_max));
+  return cudaFuncSetAttribute(solve_grouped_kernel<false, 2>, a, smem);
 }
 
 cudaError_t launch_solve_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {
@@ -1684,7 +1713,8 @@ cudaError_t launch_solve_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t
   cudaError_t err = cudaMemsetAsync(G.counter, 0, sizeof(int), s);
   if (err != cudaSuccess) return err;
   const int grid = std::min(p.solve_slots, p.n_waves * ne);
-  auto kern = p.solve_mixed ? solve_grouped_kernel<true> : solve_grouped_kernel<false>;
+  auto kern = p.solve_mixed ? solve_grouped_kernel<true, 2>
+                            : (p.solve_bps >= 3 ? solve_grouped_kernel<false, 3> : solve_grouped_kernel<false, 2>);
   kern<<<grid, NT, solve_smem_bytes(p.n_max), s>>>(
       reinterpret_cast<const SolveArgs*>(G.solve_waves), G.units, G.n_units, e0, ne, G.counter);
   return cudaGetLastError();

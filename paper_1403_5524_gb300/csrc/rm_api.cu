@@ -692,8 +692,9 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if (n_e > 0 && chunk > n_e) chunk = (int)n_e;
       if (chunk < 1) chunk = 1;
       p->chunk = chunk;
-      p->solve_slots = p->sm_count * solve_blocks_per_sm(n_max);
       p->solve_mixed = o.solve_prec == RM_SOLVE_MIXED ? 1 : 0;
+      p->solve_bps = solve_blocks_per_sm(n_max, p->solve_mixed != 0);
+      p->solve_slots = p->sm_count * p->solve_bps;
       p->solve_lu = o.solve_prec == RM_SOLVE_FP64_LU ? 1 : 0;
       p->slot_doubles = solve_slot_doubles(n_max, n_sel + 1, p->solve_mixed != 0);  // + the dipole column
       if (st == RM_OK) st = dalloc(p, &p->energies, n_e);

@@ -133,6 +133,7 @@ struct Plan {
   double* asym = nullptr;  // [4 * chunk * n_max]: lam, s, sp, c
   double* slot = nullptr;  // solve workspace, solve_slots * slot_doubles
   int solve_slots = 0;
+  int solve_bps = 2;  // resident solve CTAs per SM the kernels are launched for
   int64_t slot_doubles = 0;
   int32_t* err_word = nullptr;  // device error word (0 = ok)
   int64_t workspace_bytes = 0;
@@ -176,7 +177,7 @@ struct SolveOut {
 cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, const double* R,
                          const double* asym, int ld_chunk, const SolveOut& out, cudaStream_t s);
 size_t solve_smem_bytes(int n_max);
-int solve_blocks_per_sm(int n_max);
+int solve_blocks_per_sm(int n_max, bool mixed);
 int64_t solve_slot_doubles(int n_max, int n_sel, bool mixed);
 int64_t solve_mix_offset(int n_max, int n_sel);
 
