@@ -87,12 +87,13 @@ typedef enum {
 #define RM_LMAX 32           /* largest supported channel angular momentum */
 #define RM_MAX_SEL 64        /* largest number of selected initial channels */
 
-/* Matching solve.  FP64: rm_kmatrix (and every wave with a dipole vector) solves for K by LU
+/* Matching solve.  FP64: rm_kmatrix solves for K by LU
    with partial pivoting, then the S-step by an LDL^T of I - iK; rm_run and rm_xsec go straight
    to the cross sections and eigenphase sum through the outgoing-wave form: the closed channels
    eliminated by a real LDL^T, then one complex symmetric LDL^T of
    Z = G - diag(h / (a h')), h = c + i s, on the open channels (about half the flops; an energy
-   whose real elimination shows large growth or a tiny pivot goes through LU, RM_FLAG_LU).
+   whose real elimination shows large growth or a tiny pivot goes through LU, RM_FLAG_LU);
+   dipole waves' photoionisation amplitudes come from one more right-hand side of Z.
    FP64_LU: the LU path for every energy.  MIXED: LU in FP32, then iterative refinement
    with residuals r = -B - M Y in double-float (FP32 hi + lo, error-free products and sums, about
    48 bits) and FP32 correction solves until the last correction is below 1e-11 of Y; an energy
@@ -205,7 +206,9 @@ rm_status_t rm_results(rm_plan_t plan, int32_t wave, int64_t e0, int64_t e1, dou
    length form, standard R-matrix reading (the paper names its photoionisation module but prints
    no formulas): from the K-normalised solutions' boundary derivatives
    F'_im = s'_m delta_im + Lambda_i Y_im, the amplitudes M^K_m = sqrt(2) a sum_i F'_im y_i(E),
-   the incoming-wave amplitudes M^- = (I + iK)^-1 M^K, and
+   the incoming-wave amplitudes M^- = (I + iK)^-1 M^K (computed, with RM_SOLVE_FP64, as
+   M^-_m = -sqrt(2) (conj(Zhat)^-1 y)_m / conj(h'_m) from the outgoing-wave matrix, the same
+   quantity), and
    sigma_PI,m = (4 pi alpha / 3) (E - e0) |M^-_m|^2 (a0^2; initial statistical weight 1;
    s, c = k^-1/2 sin, cos i.e. sqrt(pi) times per-Rydberg energy normalisation).
    sig_pi[(e1-e0)] total, sig_pi_ch[(e1-e0)*n] per final channel; either may be NULL. */

@@ -371,8 +371,9 @@ __device__ void lu_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* t
 // the columns to its right in TC-column tiles, where a matrix column col takes
 // the tile column d_j L[col][kb+j] straight from the panel and updates rows
 // >= col only, and a right-hand-side column takes L11^-1 A12 as in lu_solve.
-// With nf < n only the first nf pivots are taken (m must equal n then): the
-// trailing block [nf, n) is left holding its Schur complement.
+// With nf < n only the first nf pivots are taken: the trailing block [nf, n)
+// is left holding its Schur complement, and the rows [nf, n) of the
+// right-hand-side columns the matching forward elimination (no solve).
 template <typename T>
 __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* tile, T* tmp, T* tri,
                           LUStat& st, int nf = -1) {
@@ -508,7 +509,7 @@ __device__ void ldl_solve(T* __restrict__ A, int n, int m, int ld, T* panel, T* 
       c0 = ce;
     }
   }
-  if (m == n) return;
+  if (m == n || nf < n) return;
   // -------------------------------------------- D^-1, then back substitution
   for (int64_t idx = t; idx < (int64_t)n * (m - n); idx += NT) {
     const int i = (int)(idx / (m - n)), col = n + (int)(idx % (m - n));
@@ -1100,6 +1101,14 @@ __device__ void ldl_check(const double* A, int n, int nf, int ld, Red& red, doub
   rmin = -block_max(-rm, red);
 }
 
+// Photoionisation (a wave with a dipole row y): the boundary derivatives of the
+// incoming-wave solutions are V = -(1/a) conj(Zhat)^-1 [diag(1/h'^*); 0], Zhat
+// the full-channel form of Z, so M^-_m = sqrt(2) a (V^T y)_m
+// = -sqrt(2) (conj(Zhat)^-1 y)_m / h'^*_m.  Eliminating the closed channels
+// carries y along as a right-hand side (y_o - M_oc M_cc^-1 y_c, real), and
+// conj(Z)^-1 of a real vector is the conjugate of Z^-1 of it, so
+// |M^-_m|^2 = 2 |(Z^-1 y')_m|^2 / |h'_m|^2: one more right-hand side of Z.
+//
 // Returns true when energy e is finished (outputs written), false when its
 // real eliminations fail the growth / pivot check and the caller must solve it
 // by the LU path (the workspace is then free).
@@ -1117,6 +1126,8 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
   const double* s = g.asym + 1 * g.ld_asym + (int64_t)e * n;
   const double* sp = g.asym + 2 * g.ld_asym + (int64_t)e * n;
   const double* c = g.asym + 3 * g.ld_asym + (int64_t)e * n;
+  const bool photo = g.dip && (g.out.pi_tot || g.out.pi_ch);
+  const double* ye = g.R + (int64_t)e * g.npR + 1;  // dipole vector y_i (rows with a dipole)
   // ------------------------------------- M, lower triangle, channels reversed (closed first)
   double gm = 0.0;
   for (int p = t >> 5; p < n; p += NWARP) {
@@ -1130,17 +1141,20 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
       gm = fmax(gm, fabs(v));
     }
   }
+  if (photo)  // the dipole vector as column n, channels reversed
+    for (int p = t; p < n; p += NT) A[(int64_t)p * ld + n] = ye[n - 1 - p];
   gm = block_max(gm, red);
   LUStat st;
   double growth_c = 0.0, piv_c = INFINITY;
   if (nc > 0) {
-    ldl_solve<double>(A, n, n, ld, reinterpret_cast<double*>(panel_b), reinterpret_cast<double*>(tile_b),
-                      reinterpret_cast<double*>(tmp_b), reinterpret_cast<double*>(tri_b), st, nc);
+    ldl_solve<double>(A, n, photo ? n + 1 : n, ld, reinterpret_cast<double*>(panel_b),
+                      reinterpret_cast<double*>(tile_b), reinterpret_cast<double*>(tmp_b),
+                      reinterpret_cast<double*>(tri_b), st, nc);
     ldl_check(A, n, nc, ld, red, growth_c, piv_c);
     growth_c /= gm;
   }
-  // ------------------------------------- Z = G - diag(h / (a h')) and unit right-hand sides
-  const int r = g.n_sel, mc = no + r;
+  // ------------------------------------- Z = G - diag(h / (a h')), unit right-hand sides, y'
+  const int r = g.n_sel, mc = no + r + (photo ? 1 : 0);
   for (int64_t idx = t; idx < (int64_t)no * mc; idx += NT) {
     const int i = (int)(idx / mc), j = (int)(idx % mc);
     cplx v;
@@ -1153,8 +1167,10 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
         v.re -= (c[i] * cp + s[i] * sp[i]) / den;  // h / h' = (c c' + s s' + i (s c' - c s')) / |h'|^2
         v.im -= (s[i] * cp - c[i] * sp[i]) / den;
       }
-    } else {
+    } else if (j < no + r) {
       v = cplx{(g.sel[j - no] == i) ? 1.0 : 0.0, 0.0};
+    } else {
+      v = cplx{A[(int64_t)(n - 1 - i) * ld + n], 0.0};
     }
     C[(int64_t)i * g.ldC + j] = v;
   }
@@ -1238,6 +1254,23 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
     part = block_sum(part, red);
     if (t == 0 && g.out.sig_tot) g.out.sig_tot[(int64_t)e * r + q] = part;
   }
+  if (photo) {
+    // sigma_PI,j = (4 pi alpha / 3) omega |M^-_j|^2 = (4 pi alpha / 3) omega 2 |x_j|^2 / |h'_j|^2
+    const double pref = (4.0 * M_PI * 7.2973525693e-3 / 3.0) * (g.E[e] - g.e0);
+    double part = 0.0;
+    for (int j = t; j < n; j += NT) {
+      double v = 0.0;
+      if (j < no) {
+        const double cp = lam[j] * c[j];
+        const cplx x = C[(int64_t)j * g.ldC + no + r];
+        v = pref * 2.0 * (x.re * x.re + x.im * x.im) / (cp * cp + sp[j] * sp[j]);
+      }
+      if (g.out.pi_ch) g.out.pi_ch[(int64_t)e * n + j] = v;
+      part += v;
+    }
+    part = block_sum(part, red);
+    if (t == 0 && g.out.pi_tot) g.out.pi_tot[e] = part;
+  }
   __syncthreads();
   return true;
 }
@@ -1296,8 +1329,7 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     return;
   }
   if constexpr (!MIXED) {
-    const bool photo_req = g.dip && (g.out.pi_tot || g.out.pi_ch);
-    if (g.out.do_xsec && !g.out.K && !photo_req && !g.lu_only) {
+    if (g.out.do_xsec && !g.out.K && !g.lu_only) {
       if (sym_xsec(g, e, no, fl, smem_raw, red)) return;
       fl |= RM_FLAG_LU;
     }
