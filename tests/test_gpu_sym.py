@@ -159,3 +159,25 @@ def test_regular_where_c_prime_vanishes(rm):
     a = run(rm, wl, "fp64", sel=(0, 1))
     ref = orc.sweep(w, wl.energies, sel=(0, 1), keep_R=False, keep_K=False)
     close(a, as_ref(ref))
+
+
+def test_photo_matches_lu_path(rm):
+    # dipole amplitudes from one more right-hand side of Z against the K-normalised LU form
+    for z in (0.0, 1.0):
+        wl = synth.small(23, 18, 240, 60, e_lo=0.05, e_hi=2.5, z=z, dipole=True)
+        w = wl.waves[0]
+        out = {}
+        for solve in ("fp64", "fp64_lu"):
+            with rm.Plan(wl.waves, wl.energies, prec="fp64", sel=(0,), solve=solve) as p:
+                p.run()
+                pi = np.zeros(wl.n_e)
+                pich = np.zeros((wl.n_e, w.n))
+                p.results_photo(0, 0, wl.n_e, sig_pi=pi, sig_pi_ch=pich)
+                out[solve] = (pi, pich)
+        a, b = out["fp64"], out["fp64_lu"]
+        for e in range(wl.n_e):
+            if b[0][e] == 0:
+                assert a[0][e] == 0
+                continue
+            assert abs(a[0][e] - b[0][e]) <= TOL * b[0][e], (z, e)
+            assert np.abs(a[1][e] - b[1][e]).max() <= TOL * b[0][e], (z, e)
