@@ -662,7 +662,7 @@ __global__ void prep_energy_split_kernel(const double* __restrict__ E, int64_t n
 }
 
 // ------------------------------------------------------- near-pole window
-constexpr int NEB = 8;    // energies per CTA
+constexpr int NEB = 16;   // energies per CTA (they share each pair's products w_ik w_jk)
 constexpr int NKP = 32;   // poles per staged piece
 constexpr int NNT = 256;  // threads
 
@@ -690,6 +690,8 @@ __device__ __forceinline__ void near_block(const double* __restrict__ W, int n, 
   const int Klo = klo[e0], Khi = khi[e1 - 1];
   const int t = threadIdx.x;
   for (int Ks = Klo; Ks < Khi; Ks += NKP) {
+    // groups of 8 poles that hold window poles (the last piece of a window is usually partial)
+    const int ng = (min(NKP, Khi - Ks) + 7) >> 3;
     for (int idx = t; idx < n * NKP; idx += NNT) {
       const int i = idx / NKP, kk = idx % NKP;
       Ws[i * (NKP + 1) + kk] = (Ks + kk < Khi) ? W[(int64_t)i * Npad + Ks + kk] : 0.0;
@@ -714,11 +716,22 @@ __device__ __forceinline__ void near_block(const double* __restrict__ W, int n, 
       for (; p < pe; p += NNT) {
         double P[NKP];
 #pragma unroll
-        for (int kk = 0; kk < NKP; ++kk) P[kk] = Ws[i * (NKP + 1) + kk] * Ws[j * (NKP + 1) + kk];
+        for (int g8 = 0; g8 < NKP / 8; ++g8)
+          if (g8 < ng) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int kk = 8 * g8 + q;
+              P[kk] = Ws[i * (NKP + 1) + kk] * Ws[j * (NKP + 1) + kk];
+            }
+          }
         for (int e = 0; e < e1 - e0; ++e) {
           double acc = 0.0;
 #pragma unroll
-          for (int kk = 0; kk < NKP; ++kk) acc = fma(P[kk], Dm[e * NKP + kk], acc);
+          for (int g8 = 0; g8 < NKP / 8; ++g8)
+            if (g8 < ng) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) acc = fma(P[8 * g8 + q], Dm[e * NKP + 8 * g8 + q], acc);
+            }
           R[(int64_t)(e0 + e) * np + p] += acc;
         }
         j += NNT;
