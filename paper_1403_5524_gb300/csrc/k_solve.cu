@@ -1705,14 +1705,16 @@ cudaError_t group_setup_solve(Plan& p) {
     a.out.do_xsec = true;
     h[g] = a;
   }
-  // units of one chunk, waves in decreasing cost (n^3), energies in order
+  // units of one chunk, waves in decreasing cost (n^3), energies from the top of the chunk down:
+  // a wave's thresholds are sorted and the mesh ascends, so the open-channel count and with it
+  // the cost of an energy never fall with its index, and the cheapest units come last
   std::vector<int> order(p.n_waves);
   for (int g = 0; g < p.n_waves; ++g) order[g] = g;
   std::sort(order.begin(), order.end(), [&](int x, int y) { return p.waves[x].n > p.waves[y].n; });
   std::vector<int2> units;
   units.reserve((size_t)p.n_waves * G.chunk);
   for (int g : order)
-    for (int e = 0; e < G.chunk; ++e) units.push_back(make_int2(g, e));
+    for (int e = G.chunk - 1; e >= 0; --e) units.push_back(make_int2(g, e));
   cudaError_t err;
   if (!G.solve_waves) {
     if ((err = cudaMalloc(&G.solve_waves, sizeof(SolveArgs) * p.n_waves)) != cudaSuccess) return err;

@@ -181,3 +181,17 @@ def test_photo_matches_lu_path(rm):
                 continue
             assert abs(a[0][e] - b[0][e]) <= TOL * b[0][e], (z, e)
             assert np.abs(a[1][e] - b[1][e]).max() <= TOL * b[0][e], (z, e)
+
+
+def test_maximum_channel_count(rm):
+    # n_ch = 640, the largest the library accepts: two solve CTAs per SM, 40 panels of the real and
+    # 80 of the complex LDL^T; energies with a few, about half, and all channels open
+    wl = synth.small(31, 640, 1500, 5, e_lo=0.02, e_hi=3.0, thr_hi=2.0, pole_lo=-3.0, pole_hi=8.0, a=20.0)
+    sel = (0, 1, 639)
+    a = run(rm, wl, "fp64", sel=sel)
+    b = run(rm, wl, "fp64_lu", sel=sel)
+    ref = orc.sweep(wl.waves[0], wl.energies, sel=sel, keep_R=False, keep_K=False)
+    assert np.array_equal(a["n_open"], ref["n_open"])
+    assert ref["n_open"].min() < 100 and ref["n_open"].max() == 640
+    close(a, as_ref(ref))
+    close(b, as_ref(ref))
