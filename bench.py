@@ -35,7 +35,7 @@ SPLIT_PRODUCTS = 13      # BF16 slice products per far term in the tensor-core p
 # DRAM bytes (read + write) per energy from one ncu capture each, n_ch=256 / N=20000 wave,
 # 1000-energy launch (profiles/solve_grouped_kernel_n256_1000E.md,
 # profiles/polesum_tc_grouped_2x2_n256_1000E.md); scaled to a launch by its energies.
-DRAM_BYTES_PER_ENERGY_N256 = {"solve": 8.540e6, "polesum_split": 0.4638e6}
+DRAM_BYTES_PER_ENERGY_N256 = {"solve": 8.540e6}
 
 
 def measured_peaks():
@@ -375,7 +375,8 @@ def run_ours(args):
                    else "fallback 1.7 PFLOP/s sustained",
                    "flops_per_launch": hw / n_l, "avg_launch_ms": avg_ms,
                    "algorithmic_tflops": pole_flops * args.steps / (kern["polesum_split"]["ms_total"]
-                                                                    + kern.get("near", {}).get("ms_total", 0.0)) / 1e9,
+                                                                    + kern.get("near", {}).get("ms_total", 0.0)
+                                                                    + kern.get("dslice", {}).get("ms_total", 0.0)) / 1e9,
                    "note": f"{SPLIT_PRODUCTS} BF16 products per far term; algorithmic = 2 n_p N n_e of Eq. 1-2"}
 
     # mixed solve: energies whose refinement fell back to FP64 (flag 32) in the last run

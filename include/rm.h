@@ -143,7 +143,10 @@ typedef struct {
                               energies; keep the fastest */
   const char* tune_cache;  /* optional file caching autotuned choices (NULL = none) */
   int32_t cluster_x;       /* split modes, rm_run: CTAs per cluster sharing one energy tile
-                              (each forms 1/cluster_x of the D slices): 1, 2 or 4; 0 = automatic */
+                              (each forms 1/cluster_x of the D slices): 1, 2 or 4; 0 = automatic.
+                              With 1, the D slices of each chunk are written once by a separate
+                              kernel and loaded by TMA (no formation in the pole-sum kernel; the
+                              plan holds 8 bytes per energy and pole of the chunk for them) */
   int32_t cluster_y;       /* CTAs per cluster sharing one pair tile (each forms 1/cluster_y of
                               the P slices): 1, 2 or 4; 0 = automatic.  At most 8 CTAs per
                               cluster; a shape the device cannot co-schedule is rejected with
@@ -255,8 +258,9 @@ int64_t rm_plan_launches(rm_plan_t plan);
 #define RM_KERNEL_POLESUM_SPLIT 1  /* sliced BF16 tcgen05 pole sum (far poles) */
 #define RM_KERNEL_NEAR 2           /* FP64 near-pole window */
 #define RM_KERNEL_ASYM 3           /* asymptotic functions */
-#define RM_KERNEL_SOLVE 4          /* matching LU + S-step */
-#define RM_KERNEL_COUNT 5
+#define RM_KERNEL_SOLVE 4          /* matching solve + S-step */
+#define RM_KERNEL_DSLICE 5         /* D = 1/(E_k - E) slices for the tensor-core pole sum (rm_run, cluster_x = 1) */
+#define RM_KERNEL_COUNT 6
 
 /* Per-kernel device timing.  While enabled, every kernel launch of the plan
    is bracketed by CUDA events on the plan's stream.  rm_profile_read waits

@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <algorithm>
+#include <cstring>
 #include <vector>
 #include <cudaTypedefs.h>
 
@@ -53,7 +54,7 @@ constexpr int WJ_FLOATS = 32 * KS;   // 16 channels x (hi, lo) rows
 constexpr int PO_FLOATS = 2 * KS;    // poles hi row, lo row
 constexpr int TX_BYTES = (WI_FLOATS + WJ_FLOATS + PO_FLOATS) * 4;  // 6400
 constexpr int STAGE_STRIDE = ((A_BYTES + B_BYTES + TX_BYTES + 1023) / 1024) * 1024;
-constexpr int NBARS = 4 * STAGES + 3;
+constexpr int NBARS = 5 * STAGES + 3;
 constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_STRIDE + 1024 + NBARS * 8 + 16;
 constexpr long long WAIT_BUDGET = 4000000000LL;   // clock cycles (~2 s)
 
@@ -124,6 +125,22 @@ __device__ __forceinline__ uint32_t pack_slice(float lo, float hi, bool f16) {
   return f16 ? pack_f16x2(lo, hi) : pack_bf16x2(lo, hi);
 }
 
+// The four packed slices of D for the poles (k, k + 1) = (ph0 + pl0, ph1 + pl1) at the energy
+// eh + el: 1 / (E_k - E) in double-float, scaled by m0, m1 (0 for a near-window or padding pole),
+// cut into slices, word v holding slice v of both poles.  The producers and the D-slice kernel
+// both use it, so the two ways of staging D give the same bits.
+__device__ __forceinline__ void d_pack(float ph0, float pl0, float ph1, float pl1, float eh, float el, float m0,
+                                       float m1, bool f16, uint32_t (&w)[4]) {
+  float rh0, rl0, rh1, rl1;
+  df_recip_diff(ph0, pl0, eh, el, rh0, rl0);
+  df_recip_diff(ph1, pl1, eh, el, rh1, rl1);
+  float s0[4], s1[4];
+  slice4(__fmul_rn(rh0, m0), __fmul_rn(rl0, m0), s0);
+  slice4(__fmul_rn(rh1, m1), __fmul_rn(rl1, m1), s1);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) w[v] = pack_slice(s0[v], s1[v], f16);
+}
+
 struct TCArgs {
   const float* mult_p;
   const double* f_p;
@@ -158,11 +175,19 @@ struct TCArgs {
 // 1/CX + 1/CY of a full tile while the MMAs stay local.  A stage is empty
 // when the MMAs of every CTA that it feeds are done (their commits are
 // multicast to the senders).
-template <int CX, int CY>
-__device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUtensorMap* map_pol, const TCArgs& g,
-                                        int I0, int J0, int n0, unsigned char* smem_raw) {
+//
+// DT: the D slices of the chunk were written to global memory by the D-slice
+// kernel (the same arithmetic, d_pack) and come in by TMA, one 3-D box (32
+// poles x 128 energies x 4 slices) per k-step, issued by one producer thread
+// once the stage is empty and completing on dfull; the producers form only P,
+// and clusters share P alone (CX = 1).
+template <int CX, int CY, bool DT>
+__device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUtensorMap* map_pol,
+                                        const CUtensorMap* map_d, const TCArgs& g, int I0, int J0, int n0,
+                                        unsigned char* smem_raw) {
   using namespace ptx;
   constexpr int CL = CX * CY;
+  static_assert(!DT || CX == 1, "TMA-staged D slices are not shared across the cluster");
   static_assert(CX == 1 || CX == 2 || CX == 4, "CX in {1, 2, 4}");
   static_assert(CY == 1 || CY == 2 || CY == 4, "CY in {1, 2, 4}");
   static_assert(CX * CY <= 8, "portable cluster size");
@@ -172,7 +197,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
   uint64_t* empty = bars + STAGES;
   uint64_t* wfull = bars + 2 * STAGES;
   uint64_t* gen = bars + 3 * STAGES;
-  uint64_t* acc_full = bars + 4 * STAGES;
+  uint64_t* dfull = bars + 4 * STAGES;
+  uint64_t* acc_full = bars + 5 * STAGES;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* done = acc_full + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBARS);
@@ -198,6 +224,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       mbar_init(empty + s, NPEERS);
       mbar_init(wfull + s, 1);
       mbar_init(gen + s, NWORK);
+      mbar_init(dfull + s, 1);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NWORK);
@@ -243,6 +270,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         bool got;
         if constexpr (CL > 1) got = mbar_wait_cluster(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET);
         else got = mbar_wait(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET);
+        if (got && DT) got = mbar_wait(dfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET);
         if (!got) { ok = false; break; }
         if (j + STAGES < nK) issue_tma(s, j + STAGES);
         const int d = j / DRAIN_KSTEPS;
@@ -302,7 +330,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
     // ------------------------------------- cluster copies (1 thread; CL > 1 only)
     if (CL > 1 && lane == 0) {
       constexpr uint32_t ABLK = SLICE_BYTES / CY, BBLK = SLICE_BYTES / CX;
-      constexpr uint32_t IN_BYTES = (CX - 1) * 4 * BBLK + (CY - 1) * 4 * ABLK;
+      constexpr uint32_t IN_BYTES = (DT ? 0u : (CX - 1) * 4 * BBLK) + (CY - 1) * 4 * ABLK;
       const uint32_t sbase = smem_u32(smem);
       for (int j = 0; j < nK; ++j) {
         const int s = j % STAGES;
@@ -310,7 +338,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         mbar_arrive_expect_tx(full + s, IN_BYTES);
         const uint32_t st = sbase + (uint32_t)(s * STAGE_STRIDE);
 #pragma unroll
-        for (int q = 0; q < CX; ++q) {
+        for (int q = 0; q < (DT ? 1 : CX); ++q) {
           if (q == rx) continue;
           const uint32_t peer = (uint32_t)(q + CX * ry);
           const uint32_t bar = mapa(smem_u32(full + s), peer);
@@ -377,6 +405,10 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
 #pragma unroll
     for (int c = 0; c < 32; ++c) Vh[c] = Vl[c] = 0.0f;
     bool ok = true;
+    const bool dloader = DT && w == 0 && lane == 0;
+    int d_last[STAGES];
+#pragma unroll
+    for (int q = 0; q < STAGES; ++q) d_last[q] = -1;
     for (int j = 0; j < nK && ok; ++j) {
       const int s = j % STAGES;
       if (j >= STAGES) {
@@ -388,6 +420,11 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           ok = false;
           break;
         }
+      }
+      if (dloader) {  // the stage's B area is free: fetch this k-step's D slices
+        mbar_arrive_expect_tx(dfull + s, (uint32_t)B_BYTES);
+        tma_load_3d(smem + s * STAGE_STRIDE + A_BYTES, map_d, dfull + s, j * KS, n0, 0);
+        d_last[s] = j;
       }
       if (!mbar_wait(wfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) {
         ok = false;
@@ -418,28 +455,24 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         for (int u = 0; u < 4; ++u)
           *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + offA[t]) = pack_slice(s0[u], s1[u], f16);
       }
-      const int k0 = j * KS;
-      // the whole k-step lies outside this energy's near window (and inside the real poles):
-      // no per-element test
-      const bool all_far = (k0 + KS <= klo || k0 >= khi) && k0 + KS <= g.N;
+      if constexpr (!DT) {
+        const int k0 = j * KS;
+        // the whole k-step lies outside this energy's near window (and inside the real poles):
+        // no per-element test
+        const bool all_far = (k0 + KS <= klo || k0 >= khi) && k0 + KS <= g.N;
 #pragma unroll
-      for (int t = 0; t < TB; ++t) {
-        const int k = 2 * (kpb + 4 * (kq0 + t));
-        const int kg = k0 + k;
-        const float2 ph = *reinterpret_cast<const float2*>(PO + k);
-        const float2 pl = *reinterpret_cast<const float2*>(PO + KS + k);
-        float rh0, rl0, rh1, rl1;
-        df_recip_diff(ph.x, pl.x, eh, el, rh0, rl0);
-        df_recip_diff(ph.y, pl.y, eh, el, rh1, rl1);
-        const bool far0 = all_far || ((kg < klo || kg >= khi) && kg < g.N);
-        const bool far1 = all_far || ((kg + 1 < klo || kg + 1 >= khi) && kg + 1 < g.N);
-        const float m0 = far0 ? me : 0.0f, m1 = far1 ? me : 0.0f;
-        float s0[4], s1[4];
-        slice4(__fmul_rn(rh0, m0), __fmul_rn(rl0, m0), s0);
-        slice4(__fmul_rn(rh1, m1), __fmul_rn(rl1, m1), s1);
+        for (int t = 0; t < TB; ++t) {
+          const int k = 2 * (kpb + 4 * (kq0 + t));
+          const int kg = k0 + k;
+          const float2 ph = *reinterpret_cast<const float2*>(PO + k);
+          const float2 pl = *reinterpret_cast<const float2*>(PO + KS + k);
+          const bool far0 = all_far || ((kg < klo || kg >= khi) && kg < g.N);
+          const bool far1 = all_far || ((kg + 1 < klo || kg + 1 >= khi) && kg + 1 < g.N);
+          uint32_t wd[4];
+          d_pack(ph.x, pl.x, ph.y, pl.y, eh, el, far0 ? me : 0.0f, far1 ? me : 0.0f, f16, wd);
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + offB[t]) = pack_slice(s0[v], s1[v], f16);
+          for (int v = 0; v < 4; ++v) *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + offB[t]) = wd[v];
+        }
       }
       // the MMAs (and, in clusters, the bulk copies) read these slices through the async proxy
       fence_proxy_async_smem();
@@ -480,6 +513,16 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         if (lane == 0) mbar_arrive(acc_empty);
       }
     }
+    if (dloader) {
+      // no D copy may still be landing when the CTA exits (completed ones return at once)
+      const long long cleanup = 400000000LL;
+      for (int q = 0; q < STAGES; ++q) {
+        if (d_last[q] < 0) continue;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(dfull + q, (uint32_t)((d_last[q] / STAGES) & 1)) && clock64() - t0 < cleanup) {
+        }
+      }
+    }
     // ------------------------------------------------------------- epilogue
     if (ok) {
       const int row = 32 * (w & 3) + lane;
@@ -511,7 +554,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                       TCArgs g) {
   extern __shared__ unsigned char smem_raw[];
   const int2 tile = g.tiles[blockIdx.x];
-  tc_tile<1, 1>(&map_omega, &map_pol, g, tile.x * 8, tile.y * 16, blockIdx.y * BN, smem_raw);
+  tc_tile<1, 1, false>(&map_omega, &map_pol, nullptr, g, tile.x * 8, tile.y * 16, blockIdx.y * BN, smem_raw);
 }
 
 // Every wave of a plan in one launch: tile list entries (wave, i-block, j-block),
@@ -519,7 +562,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // range is shared by all waves.  Launched in clusters of CX x CY CTAs: the tile
 // list holds each wave's tiles padded to a multiple of CX, and grid.y is a
 // multiple of CY.
-template <int CX, int CY>
+template <int CX, int CY, bool DT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     polesum_tc_grouped_kernel(const TCArgs* __restrict__ waves, const CUtensorMap* __restrict__ maps,
                               const int4* __restrict__ tiles, int64_t e_begin, int ne) {
@@ -528,7 +571,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   TCArgs g = waves[t.x];
   g.e_begin = e_begin;
   g.ne = ne;
-  tc_tile<CX, CY>(maps + 2 * t.x, maps + 2 * t.x + 1, g, t.y * 8, t.z * 16, blockIdx.y * BN, smem_raw);
+  tc_tile<CX, CY, DT>(maps + 3 * t.x, maps + 3 * t.x + 1, maps + 3 * t.x + 2, g, t.y * 8, t.z * 16,
+                      blockIdx.y * BN, smem_raw);
 }
 
 // ------------------------------------------------------------ preparation
@@ -659,6 +703,52 @@ __global__ void prep_energy_split_kernel(const double* __restrict__ E, int64_t n
   const float h = (float)x;
   Eh[e] = h;
   El[e] = (float)(x - (double)h);
+}
+
+// ---------------------------------------------------------- D-slice kernel
+// The D slices of a chunk for the tensor-core pole sum (shapes with cluster_x = 1): row e
+// (chunk-relative energy) of slice v at D[(v rows + e) Npad / 2 + k / 2], two poles per word, the
+// same values the producers would form (d_pack); rows past the chunk's energies are zero.
+struct DSliceWave {
+  const float* pol;     // [2][Npad] poles, FP32 hi row then lo row
+  const float* Eh;      // per absolute energy: FP32 hi, lo, D scale, near window [klo, khi)
+  const float* El;
+  const float* mult_e;
+  const int32_t* klo;
+  const int32_t* khi;
+  uint32_t* D;          // [4][rows][Npad / 2]
+  int N, Npad, rows, f16;
+};
+
+__global__ void __launch_bounds__(256) dslice_grouped_kernel(const DSliceWave* __restrict__ waves, int64_t e_begin,
+                                                             int ne) {
+  const DSliceWave w = waves[blockIdx.y];
+  const int e = blockIdx.x;  // chunk-relative energy row
+  if (e >= w.rows) return;
+  float eh = 1.0e30f, el = 0.0f, me = 0.0f;
+  int klo = 0, khi = 0;
+  if (e < ne) {
+    const int64_t ge = e_begin + e;
+    eh = w.Eh[ge];
+    el = w.El[ge];
+    me = w.mult_e[ge];
+    klo = w.klo[ge];
+    khi = w.khi[ge];
+  }
+  const int np2 = w.Npad >> 1;
+  const int64_t plane = (int64_t)w.rows * np2;
+  uint32_t* row = w.D + (int64_t)e * np2;
+  for (int kp = threadIdx.x; kp < np2; kp += blockDim.x) {
+    const int k = 2 * kp;
+    const float2 ph = *reinterpret_cast<const float2*>(w.pol + k);
+    const float2 pl = *reinterpret_cast<const float2*>(w.pol + w.Npad + k);
+    const bool far0 = (k < klo || k >= khi) && k < w.N;
+    const bool far1 = (k + 1 < klo || k + 1 >= khi) && k + 1 < w.N;
+    uint32_t wd[4];
+    d_pack(ph.x, pl.x, ph.y, pl.y, eh, el, far0 ? me : 0.0f, far1 ? me : 0.0f, w.f16 != 0, wd);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) row[v * plane + kp] = wd[v];
+  }
 }
 
 // ------------------------------------------------------- near-pole window
@@ -872,26 +962,49 @@ namespace {
 
 using GroupedFn = void (*)(const TCArgs*, const CUtensorMap*, const int4*, int64_t, int);
 
-GroupedFn grouped_fn(int cx, int cy) {
-  if (cx == 1 && cy == 1) return polesum_tc_grouped_kernel<1, 1>;
-  if (cx == 2 && cy == 1) return polesum_tc_grouped_kernel<2, 1>;
-  if (cx == 4 && cy == 1) return polesum_tc_grouped_kernel<4, 1>;
-  if (cx == 1 && cy == 2) return polesum_tc_grouped_kernel<1, 2>;
-  if (cx == 2 && cy == 2) return polesum_tc_grouped_kernel<2, 2>;
-  if (cx == 4 && cy == 2) return polesum_tc_grouped_kernel<4, 2>;
-  if (cx == 2 && cy == 4) return polesum_tc_grouped_kernel<2, 4>;
-  if (cx == 1 && cy == 4) return polesum_tc_grouped_kernel<1, 4>;
+GroupedFn grouped_fn(int cx, int cy, bool dt) {
+  if (dt) {
+    if (cx == 1 && cy == 1) return polesum_tc_grouped_kernel<1, 1, true>;
+    if (cx == 1 && cy == 2) return polesum_tc_grouped_kernel<1, 2, true>;
+    if (cx == 1 && cy == 4) return polesum_tc_grouped_kernel<1, 4, true>;
+    return nullptr;
+  }
+  if (cx == 1 && cy == 1) return polesum_tc_grouped_kernel<1, 1, false>;
+  if (cx == 2 && cy == 1) return polesum_tc_grouped_kernel<2, 1, false>;
+  if (cx == 4 && cy == 1) return polesum_tc_grouped_kernel<4, 1, false>;
+  if (cx == 1 && cy == 2) return polesum_tc_grouped_kernel<1, 2, false>;
+  if (cx == 2 && cy == 2) return polesum_tc_grouped_kernel<2, 2, false>;
+  if (cx == 4 && cy == 2) return polesum_tc_grouped_kernel<4, 2, false>;
+  if (cx == 2 && cy == 4) return polesum_tc_grouped_kernel<2, 4, false>;
+  if (cx == 1 && cy == 4) return polesum_tc_grouped_kernel<1, 4, false>;
   return nullptr;
 }
 
 cudaError_t set_tc_smem() {
   const int shapes[8][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 2}, {2, 2}, {4, 2}, {2, 4}, {1, 4}};
-  for (const auto& sh : shapes) {
-    cudaError_t err = cudaFuncSetAttribute(grouped_fn(sh[0], sh[1]), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)TC_SMEM);
-    if (err != cudaSuccess) return err;
-  }
+  for (int dt = 0; dt < 2; ++dt)
+    for (const auto& sh : shapes) {
+      GroupedFn fn = grouped_fn(sh[0], sh[1], dt != 0);
+      if (!fn) continue;
+      cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+      if (err != cudaSuccess) return err;
+    }
   return cudaSuccess;
+}
+
+// 16-bit [4][rows][Npad] array of D slices, 32-pole x 128-energy x 4-slice boxes in the 64-byte
+// swizzle the MMA descriptors expect (the producers' layout, swz)
+bool encode_3d_d(CUtensorMap* map, const uint32_t* base, uint64_t npad, uint64_t rows) {
+  auto enc = get_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {npad, rows, 4};
+  cuuint64_t strides[2] = {npad * 2, rows * npad * 2};
+  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)BN, 4};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint32_t*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -901,7 +1014,8 @@ cudaError_t group_setup_split(Plan& p) {
   const int W = p.n_waves;
   std::vector<TCArgs> tw(W);
   std::vector<NearWave> nw(W);
-  std::vector<CUtensorMap> maps(2 * W);
+  std::vector<CUtensorMap> maps(3 * W);
+  std::vector<DSliceWave> dw(W);
   std::vector<int4> tiles;
   std::vector<int2> jobs;
   for (int g = 0; g < W; ++g) {
@@ -926,8 +1040,14 @@ cudaError_t group_setup_split(Plan& p) {
     a.R = G.R[g];
     a.err = p.err_word;
     tw[g] = a;
-    maps[2 * g] = sd.map_omega;
-    maps[2 * g + 1] = sd.map_pol;
+    maps[3 * g] = sd.map_omega;
+    maps[3 * g + 1] = sd.map_pol;
+    std::memset(&maps[3 * g + 2], 0, sizeof(CUtensorMap));
+    if (G.d_rows > 0 && G.D[g]) {
+      if (!encode_3d_d(&maps[3 * g + 2], G.D[g], (uint64_t)w.Npad, (uint64_t)G.d_rows)) return cudaErrorInvalidValue;
+    }
+    dw[g] = DSliceWave{sd.pol, sd.Eh, sd.El, sd.mult_e, sd.klo, sd.khi, G.D[g], w.N, w.Npad, G.d_rows,
+                       p.prec == RM_PREC_SPLIT_FP16 ? 1 : 0};
     const std::vector<int2> wt = split_tiles(w.nR);
     for (const int2& t : wt) tiles.push_back(make_int4(g, t.x, t.y, w.Npad / KS));
     // pad to a multiple of the cluster width with empty tiles (i-block past the last channel)
@@ -951,9 +1071,10 @@ cudaError_t group_setup_split(Plan& p) {
     return cudaSuccess;
   };
   if ((err = ensure(&G.tc_waves, sizeof(TCArgs) * W, sizeof(TCArgs) * W)) != cudaSuccess) return err;
-  if ((err = ensure(reinterpret_cast<void**>(&G.maps), sizeof(CUtensorMap) * 2 * W, sizeof(CUtensorMap) * 2 * W)) !=
+  if ((err = ensure(reinterpret_cast<void**>(&G.maps), sizeof(CUtensorMap) * 3 * W, sizeof(CUtensorMap) * 3 * W)) !=
       cudaSuccess)
     return err;
+  if ((err = ensure(&G.dslice_waves, sizeof(DSliceWave) * W, sizeof(DSliceWave) * W)) != cudaSuccess) return err;
   if ((err = ensure(reinterpret_cast<void**>(&G.tiles), sizeof(int4) * tiles.size(), sizeof(int4) * G.n_tiles)) !=
       cudaSuccess)
     return err;
@@ -964,7 +1085,9 @@ cudaError_t group_setup_split(Plan& p) {
   G.n_tiles = (int)tiles.size();
   G.n_near_jobs = (int)jobs.size();
   if ((err = cudaMemcpy(G.tc_waves, tw.data(), sizeof(TCArgs) * W, cudaMemcpyHostToDevice)) != cudaSuccess) return err;
-  if ((err = cudaMemcpy(G.maps, maps.data(), sizeof(CUtensorMap) * 2 * W, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((err = cudaMemcpy(G.maps, maps.data(), sizeof(CUtensorMap) * 3 * W, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return err;
+  if ((err = cudaMemcpy(G.dslice_waves, dw.data(), sizeof(DSliceWave) * W, cudaMemcpyHostToDevice)) != cudaSuccess)
     return err;
   if ((err = cudaMemcpy(G.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
     return err;
@@ -978,7 +1101,7 @@ cudaError_t group_setup_split(Plan& p) {
 }
 
 bool polesum_cluster_ok(int cx, int cy) {
-  GroupedFn fn = grouped_fn(cx, cy);
+  GroupedFn fn = grouped_fn(cx, cy, cx == 1);
   if (!fn) return false;
   if (cx * cy == 1) return true;
   if (set_tc_smem() != cudaSuccess) return false;
@@ -1004,7 +1127,7 @@ bool polesum_cluster_ok(int cx, int cy) {
 cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {
   if (ne <= 0) return cudaSuccess;
   const GroupDev& G = p.grp;
-  GroupedFn fn = grouped_fn(G.tc_cx, G.tc_cy);
+  GroupedFn fn = grouped_fn(G.tc_cx, G.tc_cy, G.dt());
   if (!fn) return cudaErrorInvalidValue;
   const int ny = (ne + BN - 1) / BN;
   cudaLaunchConfig_t cfg = {};
@@ -1029,6 +1152,18 @@ cudaError_t launch_near_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t 
   dim3 grid(G.n_near_jobs, G.near_splits);
   near_grouped_kernel<<<grid, NNT, near_smem_bytes(p.nR_max), s>>>(reinterpret_cast<const NearWave*>(G.near_waves),
                                                                   G.near_jobs, e0, ne, G.near_splits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dslice_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {
+  if (ne <= 0) return cudaSuccess;
+  const GroupDev& G = p.grp;
+  if (G.d_rows <= 0) return cudaErrorInvalidValue;
+  // rows of the last 128-energy tile past ne are zeroed too (the MMAs read whole tiles)
+  int rows = (ne + BN - 1) / BN * BN;
+  if (rows > G.d_rows) rows = G.d_rows;
+  dslice_grouped_kernel<<<dim3(rows, p.n_waves), 256, 0, s>>>(reinterpret_cast<const DSliceWave*>(G.dslice_waves), e0,
+                                                               ne);
   return cudaGetLastError();
 }
 

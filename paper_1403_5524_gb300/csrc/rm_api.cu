@@ -65,6 +65,8 @@ void free_plan(Plan* p) {
   GroupDev& G = p->grp;
   for (double* r : G.R) dfree(r);
   for (double* a : G.asym) dfree(a);
+  for (uint32_t* d : G.D) dfree(d);
+  dfree(G.dslice_waves);
   dfree(G.tc_waves); dfree(G.maps); dfree(G.tiles); dfree(G.near_waves); dfree(G.near_jobs);
   dfree(G.asym_waves); dfree(G.solve_waves); dfree(G.units); dfree(G.counter);
   if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -348,6 +350,11 @@ rm_status_t enqueue_grouped(Plan* p, cudaStream_t s, bool prof, int* kernels, bo
         }
         --nk;
       } else {
+        if (G.dt()) {
+          Prof pr(p, RM_KERNEL_DSLICE, prof, s, count);
+          RM_CUDA(launch_dslice_grouped(*p, c0, ne, s), "grouped D-slice kernel");
+          ++nk;
+        }
         Prof pr(p, RM_KERNEL_POLESUM_SPLIT, prof, s, count);
         RM_CUDA(launch_polesum_split_grouped(*p, c0, ne, s), "grouped split pole-sum kernel");
       }
@@ -465,8 +472,9 @@ rm_status_t time_grouped(Plan* p, int64_t ne_t, cudaEvent_t a, cudaEvent_t b, fl
 }
 
 // Tensor-core cluster shapes in order of preference (the automatic shape is the
-// first one the device co-schedules).
-constexpr int kShapes[][2] = {{2, 2}, {4, 1}, {2, 1}, {1, 2}, {1, 1}};
+// first one the device co-schedules).  Shapes with cluster_x = 1 take the D
+// slices by TMA from the D-slice kernel; the others form them in the pole sum.
+constexpr int kShapes[][2] = {{1, 2}, {1, 4}, {2, 2}, {1, 1}, {4, 1}, {2, 1}};
 
 rm_status_t autotune(Plan* p, const char* cache, int chunk_max, bool tune_chunk, bool tune_cluster) {
   // 1. cluster shape: every co-schedulable shape, timed on the first
@@ -706,8 +714,11 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       // grouped-run buffers (all waves at once).  R for the whole mesh when it
       // fits min(24 GiB, a third of free device memory): one launch per kernel
       // and sweep, no chunk tails; otherwise chunks (autotuned when asked).
+      // per energy and wave: R, the asymptotic data and (tensor-core modes) the D slices,
+      // 4 x 2 bytes per pole
+      const bool dslices = is_split_like(o.prec) && o.prec != RM_PREC_FP32_SIMT;
       int64_t per_e = 0;
-      for (const auto& w : p->waves) per_e += w.npR() + 4ll * w.n;
+      for (const auto& w : p->waves) per_e += w.npR() + 4ll * w.n + (dslices ? (int64_t)w.Npad : 0);
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 2ull << 30; }
       int64_t budget = (int64_t)(free_b / 3);
@@ -720,11 +731,14 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       p->grp.chunk = o.chunk > 0 ? o.chunk : grp_chunk_max;
       p->grp.R.assign(n_waves, nullptr);
       p->grp.asym.assign(n_waves, nullptr);
+      p->grp.D.assign(n_waves, nullptr);
       for (int g = 0; g < n_waves && st == RM_OK; ++g) {
         const WaveDev& d = p->waves[g];
         st = dalloc(p, &p->grp.R[g], cmax * d.npR());
         if (st == RM_OK) st = dalloc(p, &p->grp.asym[g], 4ll * cmax * d.n);
+        if (st == RM_OK && dslices) st = dalloc(p, &p->grp.D[g], 2ll * cmax * d.Npad);  // 4 x Npad/2 words
       }
+      p->grp.d_rows = (st == RM_OK && dslices) ? (int)cmax : 0;
     }
     if (st == RM_OK) {
       if (cudaMemcpy(p->sel_dev, p->sel, sizeof(int32_t) * n_sel, cudaMemcpyHostToDevice) != cudaSuccess)

@@ -90,10 +90,16 @@ struct GroupDev {
   std::vector<double*> R;     // per wave [chunk * n_p]
   std::vector<double*> asym;  // per wave [4 * chunk * n]
   void* tc_waves = nullptr;   // per-wave tensor-core arguments
-  CUtensorMap* maps = nullptr;  // [2 * n_waves] TMA descriptors (omega, poles)
+  CUtensorMap* maps = nullptr;  // [3 * n_waves] TMA descriptors (omega, poles, D slices)
   int4* tiles = nullptr;      // (wave, i-block, j-block), longest K first
   int n_tiles = 0;
   int tc_cx = 1, tc_cy = 1;   // tensor-core cluster shape (pair tiles x energy tiles)
+  std::vector<uint32_t*> D;   // per wave [4 slices][d_rows energies][Npad / 2 pole pairs] packed D slices
+  int d_rows = 0;             // energy rows of each D buffer (the largest chunk); 0: none allocated
+  void* dslice_waves = nullptr;
+  // D slices staged by TMA (written by the D-slice kernel) instead of formed by the producers:
+  // the shapes that share only P (one pair tile per cluster row)
+  bool dt() const { return tc_cx == 1 && d_rows > 0; }
   void* near_waves = nullptr;
   int2* near_jobs = nullptr;  // (wave, first energy of an 8-energy block)
   int n_near_jobs = 0;
@@ -203,6 +209,8 @@ cudaError_t group_setup_split(Plan& p);
 cudaError_t group_setup_asym(Plan& p);
 cudaError_t group_setup_solve(Plan& p);
 cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
+// D slices of the chunk [e0, e0 + ne) for every wave (shapes with cluster_x = 1)
+cudaError_t launch_dslice_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
 // clusters of this shape can be resident (grouped tensor-core kernel)
 bool polesum_cluster_ok(int cx, int cy);
 cudaError_t launch_near_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);

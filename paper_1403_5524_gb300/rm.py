@@ -29,7 +29,7 @@ EXPORTS = ["rm_options_default", "rm_plan_create", "rm_plan_load", "rm_rmatrix",
            "rm_plan_destroy", "rm_status_str", "rm_last_error", "rm_profile_enable", "rm_profile_read",
            "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve"]
 
-KERNELS = {"polesum_fp64": 0, "polesum_split": 1, "near": 2, "asym": 3, "solve": 4}
+KERNELS = {"polesum_fp64": 0, "polesum_split": 1, "near": 2, "asym": 3, "solve": 4, "dslice": 5}
 
 
 class rm_wave(C.Structure):
