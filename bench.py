@@ -87,6 +87,8 @@ def parse():
                     help="photoionisation: give every wave a bound-free dipole vector (sigma_PI per energy)")
     ap.add_argument("--cluster", default="", help="tensor-core cluster shape CXxCY (default: autotuned)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--k-formed", type=int, default=1,
+                    help="1: also time the sweep with the K-matrix formed by LU (solve fp64_lu), as k_formed")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     return ap.parse_args()
@@ -464,6 +466,27 @@ def run_ours(args):
         fp64 = {"value": v64, "unit": "energies/s", "sample": f"every {args.fp64_stride}th energy of the mesh "
                 f"({sub.shape[0]} energies), one timed pass", "split_speedup": value / v64}
 
+    # the same sweep with the K-matrix formed: rm_run with solve "fp64_lu" (LU of the matching system
+    # -> K, then the LDL^T of I - iK) instead of the outgoing-wave factorisation, which gives the same
+    # S, eta and sigma without forming K; one warm-up and one timed pass over the whole mesh
+    k_formed = None
+    if args.solve == "fp64" and args.k_formed and rank == 0:
+        with rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream, solve="fp64_lu",
+                     cluster=plan.cluster() if args.prec != "fp64" else None) as pk:
+            pk.run()
+            torch.cuda.synchronize(dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(1)
+            a0.record(stream)
+            pk.run()
+            a1.record(stream)
+            pk.sync()
+            msk = a0.elapsed_time(a1)
+        k_formed = {"value": len(wl.waves) * wl.n_e / (msk / 1000.0), "unit": "energies/s",
+                    "note": "rm_run with the K-matrix formed by LU for every energy (solve fp64_lu), then the "
+                            "LDL^T of I - iK; the headline run computes the same S, eta and sigma from the "
+                            "outgoing-wave factorisation without forming K (rm_kmatrix forms K on request)"}
+
     # CPU baseline leg: the oracle timed on a bounded sample of the same mesh;
     # its outputs for those energies also give the accuracy report.
     cpu = None
@@ -491,7 +514,7 @@ def run_ours(args):
                            "n_sel": len(sel), "l2": "flushed (512 MB write) between timed steps",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "roofline_tensor": roof_tc, "kernels": kern, "gpu_launches": int(launches),
-                "fp64_gpu": fp64, "post_convolve": post,
+                "fp64_gpu": fp64, "k_formed": k_formed, "post_convolve": post,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "errors": errors}
         print(json.dumps(line), flush=True)
     plan.close()
