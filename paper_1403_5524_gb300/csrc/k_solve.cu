@@ -1,5 +1,12 @@
 // Per-energy matching solve and S-matrix step, FP64, one CTA per energy.
 //
+// Two forms.  Cross sections, eigenphase sums and photoionisation (rm_run,
+// rm_xsec) come from the outgoing-wave form (sym_xsec below): the closed
+// channels eliminated by a real LDL^T, one complex symmetric LDL^T of
+// Z = G - diag(h / (a h')) on the open ones, no K.  The K-matrix (rm_kmatrix),
+// the mixed-precision option, and energies whose real eliminations fail their
+// checks take the LU form described next.
+//
 // Matching (Bloch constant b = 0; the paper states the problem but not the
 // matching, so this is the standard zero-potential form): with the column of
 // channel j divided by c_j (open) or e_j (closed),
@@ -28,9 +35,9 @@
 // (row interchanges, triangular solve with the unit-lower panel block, then
 // the rank-16 update).  Each matrix lives in a per-CTA global workspace slot
 // that stays in L2 while the CTA works on it.  GB300 retires about two FP64
-// FMAs per clock per SM; two 256-thread CTAs share an SM where their shared
-// memory fits (n_ch up to about 280), so that one CTA's barriers and load
-// latencies are covered by the other's FMAs.
+// FMAs per clock per SM; three 256-thread CTAs share an SM where their shared
+// memory fits (n_ch up to about 380; two up to 640), so that one CTA's pivot
+// chains, barriers and load latencies are covered by the others' FMAs.
 #include <algorithm>
 #include <vector>
 
