@@ -73,7 +73,9 @@ typedef enum {
 
 /* per-energy flag bits */
 #define RM_FLAG_NUDGED 1u    /* energy was within 1e-9 Ry of a pole or threshold; moved up 1e-6 Ry */
-#define RM_FLAG_ILLCOND 2u   /* min|pivot| / max|pivot| of the matching LU below 1e-12 */
+#define RM_FLAG_ILLCOND 2u   /* min|pivot| / max|pivot| of the matching LU below 1e-12 (set where an LU runs:
+                                rm_kmatrix, solve_prec FP64_LU / MIXED, and RM_FLAG_LU energies; the
+                                outgoing-wave form forms no LU) */
 #define RM_FLAG_NO_OPEN 4u   /* no open channel (E below every threshold); outputs are zero */
 #define RM_FLAG_SINGULAR 8u  /* exact zero pivot; outputs are NaN */
 #define RM_FLAG_ASYM 16u     /* a Coulomb / Whittaker continued fraction did not converge within its
