@@ -87,13 +87,11 @@ struct Ops<cplx> {
   __device__ static cplx one() { return cplx{1.0, 0.0}; }
   __device__ static double mag(cplx x) { return fabs(x.re) + fabs(x.im); }  // LAPACK cabs1
   __device__ static cplx inv(cplx x) {
-    // Smith's division 1 / (re + i im)
-    if (fabs(x.re) >= fabs(x.im)) {
-      const double r = x.im / x.re, d = x.re + x.im * r;
-      return cplx{1.0 / d, -r / d};
-    }
-    const double r = x.re / x.im, d = x.im + x.re * r;
-    return cplx{r / d, -1.0 / d};
+    // 1 / (re + i im) = (re - i im) / (re^2 + im^2): one real division on the pivot's dependent
+    // chain (Smith's form needs two in sequence); pivots here lie far inside the range where
+    // re^2 + im^2 neither overflows nor underflows
+    const double q = 1.0 / fma(x.re, x.re, x.im * x.im);
+    return cplx{x.re * q, -x.im * q};
   }
   __device__ static cplx mul(cplx a, cplx b) { return a * b; }
   __device__ static cplx fms(cplx acc, cplx a, cplx b) {
