@@ -35,7 +35,7 @@ SPLIT_PRODUCTS = 13      # BF16 slice products per far term in the tensor-core p
 # DRAM bytes (read + write) per energy from one ncu capture each, n_ch=256 / N=20000 wave,
 # 1000-energy launch (profiles/solve_grouped_kernel_n256_1000E.md,
 # profiles/polesum_tc_grouped_1x2_dslices_n256_1000E.md); scaled to a launch by its energies.
-DRAM_BYTES_PER_ENERGY_N256 = {"solve": 8.540e6, "polesum_split": 1.445e6}
+DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.278e6, "polesum_split": 1.445e6}
 
 
 def measured_peaks():
