@@ -195,3 +195,14 @@ def test_maximum_channel_count(rm):
     assert ref["n_open"].min() < 100 and ref["n_open"].max() == 640
     close(a, as_ref(ref))
     close(b, as_ref(ref))
+
+
+def test_maximum_channel_count_split(rm):
+    # the same size through the split-BF16 tensor-core pole sum with TMA-staged D slices
+    # (205120 pairs: 1603 pair tiles) and the FP64 near window; sigma within the method's 1e-8
+    wl = synth.small(32, 640, 1500, 4, e_lo=0.3, e_hi=3.0, thr_hi=2.0, pole_lo=-3.0, pole_hi=8.0, a=20.0)
+    sel = (0, 5)
+    a = run(rm, wl, "fp64", sel=sel, prec="split_bf16")
+    ref = orc.sweep(wl.waves[0], wl.energies, sel=sel, keep_R=False, keep_K=False)
+    assert np.array_equal(a["n_open"], ref["n_open"])
+    close(a, as_ref(ref), tol=1e-8)
