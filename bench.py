@@ -91,6 +91,9 @@ def parse():
                     help="1: also time the sweep with the K-matrix formed by LU (solve fp64_lu), as k_formed")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--oracle-probe", type=int, default=0,
+                    help="internal: time the oracle on this many energies with the inherited thread limits, "
+                         "print one JSON line, touch no GPU")
     return ap.parse_args()
 
 
@@ -494,7 +497,8 @@ def run_ours(args):
     if not args.no_cpu and rank == 0 and world == 1:
         n, dt, idx, ref = oracle_sample(wl, sel, budget_s=15.0, max_e=24, keep=not args.no_check)
         cpu = {"value": n / dt, "unit": "energies/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{n} evenly spaced energies of the same mesh, FP64 NumPy/SciPy (incl. R and K)"}
+               "sample": f"{n} evenly spaced energies of the same mesh, FP64 NumPy/SciPy (incl. R and K)",
+               "one_thread": oracle_one_thread(args, 4)}
         if ref is not None:
             errors = accuracy(plan, wl, sel, idx, ref)
 
@@ -611,8 +615,38 @@ def run_variants(args):
                                                   "energies": int(E.size), "errors_on": int(idx.size)}}))
 
 
+def oracle_one_thread(args, n_e):
+    """The oracle timed on n_e energies of the workload in a child process limited to one BLAS /
+    OpenMP thread (the thread count is fixed when NumPy loads, hence a fresh interpreter)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-probe", str(n_e), "--config", str(args.config),
+           "--stride", str(args.stride), "--sel", str(args.sel), "--z", str(args.z)]
+    if args.dipole:
+        cmd.append("--dipole")
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300)
+        line = [x for x in r.stdout.splitlines() if x.startswith("{")][-1]
+        d = json.loads(line)
+        return {"value": d["n"] / d["seconds"], "unit": "energies/s", "cores": 1,
+                "sample": f"{d['n']} evenly spaced energies of the same mesh, one BLAS thread"}
+    except Exception as exc:  # reported, not fatal: the all-core figure is the baseline
+        return {"error": str(exc)[:200]}
+
+
+def oracle_probe(args):
+    wl, _ = workload(args)
+    sel = tuple(range(args.sel))
+    n, dt, _, _ = oracle_sample(wl, sel, budget_s=1e9, max_e=args.oracle_probe, keep=False)
+    print(json.dumps({"n": int(n), "seconds": dt}))
+
+
 def main():
     args = parse()
+    if args.oracle_probe > 0:
+        oracle_probe(args)
+        return
     if args.variants:
         run_variants(args)
         return
