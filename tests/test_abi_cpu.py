@@ -120,3 +120,21 @@ def test_convolve_arguments_checked_on_host(lib):
     assert call(E, 2, float("nan")) == rm.RM_ERR_ARG
     assert call(E, 2, 0.1, np.array([0.5, float("inf")])) == rm.RM_ERR_ARG
     assert call(E[::-1].copy(), 2, 0.1) == rm.RM_ERR_ORDER
+
+
+def test_binding_constants_match_the_header():
+    # flag bits, kernel ids and solve-precision values of the binding are the header's
+    txt = open(os.path.join(os.path.dirname(__file__), "..", "include", "rm.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (RM_\w+) (\d+)u?\b", txt)}
+    flags = {"NUDGED": rm.FLAG_NUDGED, "ILLCOND": rm.FLAG_ILLCOND, "NO_OPEN": rm.FLAG_NO_OPEN,
+             "SINGULAR": rm.FLAG_SINGULAR, "ASYM": rm.FLAG_ASYM, "FP64": rm.FLAG_FP64, "LU": rm.FLAG_LU}
+    for k, v in flags.items():
+        assert defs["RM_FLAG_" + k] == v, k
+    kern = {"polesum_fp64": "POLESUM_FP64", "polesum_split": "POLESUM_SPLIT", "near": "NEAR", "asym": "ASYM",
+            "solve": "SOLVE", "dslice": "DSLICE"}
+    for k, v in rm.KERNELS.items():
+        assert defs["RM_KERNEL_" + kern[k]] == v, k
+    assert defs["RM_KERNEL_COUNT"] == len(rm.KERNELS)
+    enum = re.search(r"typedef enum \{([^}]*)\} rm_solve_precision_t;", txt).group(1)
+    vals = {m.group(1): int(m.group(2)) for m in re.finditer(r"RM_SOLVE_(\w+) = (\d+)", enum)}
+    assert vals == {"FP64": rm.SOLVE["fp64"], "MIXED": rm.SOLVE["mixed"], "FP64_LU": rm.SOLVE["fp64_lu"]}
