@@ -89,3 +89,43 @@ def test_outgoing_identities_coulomb():
                      z=1.0, dipole=True)
     seen = check_wave(wl.waves[0], wl.energies, 1.0)
     assert 3 in seen and (1 in seen or 2 in seen)
+
+
+def test_eta_across_a_k_pole():
+    # where an eigenvalue of S_oo crosses zero, K has a pole and eta (mod 2 pi) jumps by pi: the
+    # inertia term of the outgoing-wave formula must follow the oracle on both sides
+    wl = synth.small(63, 5, 80, 1, pole_lo=-1.0, pole_hi=5.0, thr_hi=1.0, a=10.0)
+    w = wl.waves[0]
+
+    def detsign(E):
+        R = orc.rmatrix(w.W, w.poles, E, w.a)
+        f = orc.channel_functions(w.l, w.thresh, E, w.a)
+        no, n = f["n_o"], w.n
+        lam = f["lam"]
+        M = R.copy()
+        for j in range(n):
+            M[j, j] -= (f["c"][j] / (w.a * f["cp"][j])) if j < no else 1.0 / (w.a * lam[j])
+        S = M[:no, :no] - (M[:no, no:] @ np.linalg.solve(M[no:, no:], M[no:, :no]) if no < n else 0.0)
+        V = f["cp"][:no] / np.hypot(f["cp"][:no], f["sp"][:no])
+        return np.prod(np.sign(np.linalg.eigvalsh(V[:, None] * S * V[None, :]))), no
+
+    grid = np.linspace(1.2, 2.4, 241)  # above every threshold (all five channels open)
+    signs = [detsign(E)[0] for E in grid]
+    # det S_oo also changes sign where R has a pole (an eigenvalue passes through infinity): keep
+    # the intervals that hold no pole
+    flips = [k for k in range(len(grid) - 1) if signs[k] != signs[k + 1]
+             and not np.any((w.poles > grid[k] - 1e-3) & (w.poles < grid[k + 1] + 1e-3))]
+    assert flips, "no K pole on the grid"
+    lo, hi = grid[flips[0]], grid[flips[0] + 1]
+    s_lo = detsign(lo)[0]
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if detsign(mid)[0] == s_lo:
+            lo = mid
+        else:
+            hi = mid
+    for E in (lo - 1e-7, hi + 1e-7):
+        R = orc.rmatrix(w.W, w.poles, E, w.a)
+        K, no, fl, _ = orc.kmatrix(R, w.l, w.thresh, E, w.a)
+        _, T, eta, _ = outgoing(R, w.l, w.thresh, E, w.a, 0.0, (0,))
+        assert abs(orc.wrap_angle(eta - orc.eigenphase_sum(K))) <= 1e-6, E
