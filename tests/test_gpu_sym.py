@@ -206,3 +206,39 @@ def test_maximum_channel_count_split(rm):
     ref = orc.sweep(wl.waves[0], wl.energies, sel=sel, keep_R=False, keep_K=False)
     assert np.array_equal(a["n_open"], ref["n_open"])
     close(a, as_ref(ref), tol=1e-8)
+
+
+def test_eta_across_a_k_pole(rm):
+    # the kernel's sign of det S'' (the inertia of its real LDL^T) against the oracle on both sides of
+    # a K pole, where eta mod 2 pi jumps by pi; the energy is found on the CPU as in
+    # tests/test_oracle_outgoing.py
+    wl0 = synth.small(63, 5, 80, 1, pole_lo=-1.0, pole_hi=5.0, thr_hi=1.0, a=10.0)
+    w = wl0.waves[0]
+
+    def detsign(E):
+        R = orc.rmatrix(w.W, w.poles, E, w.a)
+        f = orc.channel_functions(w.l, w.thresh, E, w.a)
+        no = f["n_o"]
+        M = R[:no, :no] - np.diag(f["c"][:no] / (w.a * f["cp"][:no]))
+        V = f["cp"][:no] / np.hypot(f["cp"][:no], f["sp"][:no])
+        return np.prod(np.sign(np.linalg.eigvalsh(V[:, None] * M * V[None, :])))
+
+    grid = np.linspace(1.2, 2.4, 241)  # every channel open
+    signs = [detsign(E) for E in grid]
+    flips = [k for k in range(len(grid) - 1) if signs[k] != signs[k + 1]
+             and not np.any((w.poles > grid[k] - 1e-3) & (w.poles < grid[k + 1] + 1e-3))]
+    assert flips
+    lo, hi = grid[flips[0]], grid[flips[0] + 1]
+    s_lo = detsign(lo)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if detsign(mid) == s_lo:
+            lo = mid
+        else:
+            hi = mid
+    E = np.array([lo - 1e-7, hi + 1e-7])
+    wl = synth.Workload("kpole", [w], E)
+    a = run(rm, wl, "fp64", sel=(0, 1))
+    ref = orc.sweep(w, E, sel=(0, 1), keep_R=False, keep_K=False)
+    assert not np.any(a["flags"] & FLAG_LU)
+    close(a, as_ref(ref), tol=1e-7)
