@@ -10,8 +10,10 @@ path differs from the oracle: the tolerances are those of the FP64 parity
 tests (1e-9 on sigma normalised by the total of its initial channel, on eta
 mod 2 pi).  Cases: a contiguous block of the n_ch = 64 mesh (thresholds up to
 2 Ry, so 1..64 open channels), a Coulomb wave, an energy where the first
-closed pivot vanishes (must go through LU, RM_FLAG_LU), and one where c'_0 = 0
-(K is regular there, but M and the unit-right-hand-side LU form divide by c').
+closed pivot vanishes (must go through LU, RM_FLAG_LU), one where c'_0 = 0
+(K is regular there, but M and the unit-right-hand-side LU form divide by c'),
+photoionisation against the LU form, the largest channel count (640, FP64 and
+split BF16), and the two sides of a K pole (the inertia of S'' flips there).
 """
 import math
 
