@@ -36,7 +36,7 @@
 // the rank-16 update).  Each matrix lives in a per-CTA global workspace slot
 // that stays in L2 while the CTA works on it.  GB300 retires about two FP64
 // FMAs per clock per SM; three 256-thread CTAs share an SM where their shared
-// memory fits (n_ch up to about 380; two up to 640), so that one CTA's pivot
+// memory fits (n_ch up to about 390; two up to 640), so that one CTA's pivot
 // chains, barriers and load latencies are covered by the others' FMAs.
 #include <algorithm>
 #include <vector>
