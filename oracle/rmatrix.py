@@ -79,9 +79,11 @@ FLAG_NUDGED = 1
 FLAG_ILLCOND = 2
 FLAG_NO_OPEN = 4
 FLAG_SINGULAR = 8
+FLAG_NEAR_THRESHOLD = 128
 
 NUDGE_TOL = 1e-9
 NUDGE_SHIFT = 1e-6
+NEAR_THRESHOLD = 1e-6
 ILLCOND_RATIO = 1e-12
 
 
@@ -92,7 +94,10 @@ def nudge_energies(energies, poles, thresh):
     """Move every energy within 1e-9 Ry of a pole or a threshold up by 1e-6 Ry.
 
     Applied once per energy (no re-check after the move).  Returns the new mesh
-    and a uint8 flag array with FLAG_NUDGED set where a move happened.
+    and a uint8 flag array with FLAG_NUDGED set where a move happened, and
+    FLAG_NEAR_THRESHOLD where the given energy lies within 1e-6 Ry of a channel
+    threshold: a channel opens there (k -> 0), so such energies are judged
+    apart from the rest of the mesh.
     """
     E = np.array(energies, dtype=np.float64, copy=True)
     flags = np.zeros(E.shape, dtype=np.uint8)
@@ -101,7 +106,10 @@ def nudge_energies(energies, poles, thresh):
         if poles.size:
             near |= bool(np.min(np.abs(poles - E[e])) < NUDGE_TOL)
         if thresh.size:
-            near |= bool(np.min(np.abs(thresh - E[e])) < NUDGE_TOL)
+            dthr = float(np.min(np.abs(thresh - E[e])))
+            near |= dthr < NUDGE_TOL
+            if dthr < NEAR_THRESHOLD:
+                flags[e] |= FLAG_NEAR_THRESHOLD
         if near:
             E[e] = E[e] + NUDGE_SHIFT
             flags[e] |= FLAG_NUDGED

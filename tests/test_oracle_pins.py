@@ -374,9 +374,22 @@ def test_nudge():
     E = np.array([0.5 + 5e-10, 0.7 - 2e-10, 0.9, 1.0])
     En, fl = o.nudge_energies(E, poles, thr)
     assert En[0] == E[0] + 1e-6 and fl[0] == o.FLAG_NUDGED
-    assert En[1] == E[1] + 1e-6 and fl[1] == o.FLAG_NUDGED
+    assert En[1] == E[1] + 1e-6 and fl[1] == o.FLAG_NUDGED | o.FLAG_NEAR_THRESHOLD
     assert En[2] == E[2] and fl[2] == 0
     assert En[3] == 1.0 + 1e-6
+
+
+def test_near_threshold_classification():
+    # flagged when the given energy is strictly within 1e-6 Ry of a threshold, from either side;
+    # poles do not count; the flag comes from the energy before the nudge
+    poles = np.array([0.3])
+    thr = np.array([0.0, 0.7, 1.2])
+    E = np.array([0.7 - 9e-7, 0.7 + 9e-7, 0.7 - 1.1e-6, 0.7 + 1.1e-6, 0.3 + 5e-7, 1.2, 1.2 + 2e-6, 5e-7])
+    En, fl = o.nudge_energies(E, poles, thr)
+    near = (fl & o.FLAG_NEAR_THRESHOLD) != 0
+    assert near.tolist() == [True, True, False, False, False, True, False, True]
+    assert fl[5] & o.FLAG_NUDGED and En[5] == 1.2 + 1e-6   # on a threshold: moved and flagged
+    assert not fl[4] & o.FLAG_NUDGED                        # 5e-7 from a pole: neither
 
 
 def test_pole_sum_loops_and_packing():
