@@ -30,12 +30,12 @@ sys.path.insert(0, ROOT)
 from paper_1403_5524_gb300 import synth  # noqa: E402
 
 METRIC = "energies/sec (R+K+σ) split-precision vs FP64 GPU at n_ch=256; max rel err"
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU
-SPLIT_PRODUCTS = 13      # BF16 slice products per far term in the tensor-core pole sum
-# DRAM bytes (read + write) per energy from one ncu capture each, n_ch=256 / N=20000 wave,
-# 1000-energy launch (profiles/solve_grouped_kernel_n256_1000E.md,
-# profiles/polesum_tc_grouped_1x2_dslices_n256_1000E.md); scaled to a launch by its energies.
-DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.278e6, "polesum_split": 1.445e6}
+FP64_NOMINAL_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU; the measured probe is the peak used
+# DRAM bytes (read + write) per energy of the solve kernel, from one ncu capture of the n_ch=256 /
+# N=20000 wave, 1000-energy launch; scaled to a launch by its energies.  Kernels changed since
+# their capture have no entry (traffic null).
+DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.278e6}
+PRODUCT_SETS = (3, 6, 10, 13)
 
 
 def measured_peaks():
@@ -46,20 +46,39 @@ def measured_peaks():
         return {}
 
 
+def fp64_peak():
+    """FP64 pipe peak of the current device, measured by the DFMA probe built with the library
+    (libpeak.so): {"tflops", "ms"} or None when it cannot run."""
+    import ctypes as C
+    path = os.path.join(ROOT, "paper_1403_5524_gb300", "libpeak.so")
+    try:
+        lib = C.CDLL(path)
+    except OSError:
+        return None
+    lib.rm_probe_fp64_peak.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.rm_probe_fp64_peak.restype = C.c_int
+    tf, ms = C.c_double(), C.c_double()
+    if lib.rm_probe_fp64_peak(5, C.byref(tf), C.byref(ms)) != 0:
+        return None
+    return {"tflops": tf.value, "ms": ms.value,
+            "how": "libpeak.so: 8 independent FMA chains per thread, 8 x 256-thread CTAs per SM, "
+                   "best of 5 launches after a warm-up (CUDA events)"}
+
+
 def split_tiles(n):
     """Pair tiles of the tensor-core kernel: 8-channel i-blocks x 16-channel j-blocks with some i <= j."""
     return sum(1 for I in range((n + 7) // 8) for J in range((n + 15) // 16) if 16 * J + 15 >= 8 * I)
 
 
-def tensor_flops(wl, chunk):
-    """Tensor-pipe FLOPs the split kernel issues per step (13 products, padded tiles)."""
+def tensor_flops(wl, chunk, products):
+    """Tensor-pipe FLOPs the split kernel issues per step (its slice products, padded tiles)."""
     tot = 0.0
     for w in wl.waves:
         npad = (w.N + 63) // 64 * 64
         ntile_e = 0
         for c0 in range(0, wl.n_e, chunk):
             ntile_e += (min(chunk, wl.n_e - c0) + 127) // 128
-        tot += SPLIT_PRODUCTS * 2.0 * 128 * 128 * npad * split_tiles(w.n) * ntile_e
+        tot += products * 2.0 * 128 * 128 * npad * split_tiles(w.n) * ntile_e
     return tot
 
 
@@ -73,8 +92,17 @@ def parse():
     ap.add_argument("--prec", default="split_bf16", choices=["fp64", "split_bf16", "split_fp16", "fp32_simt"])
     ap.add_argument("--variants", action="store_true",
                     help="compare the pole-sum forms (split BF16, split FP16, FP32 SIMT, FP64) on this workload")
-    ap.add_argument("--fp64-stride", type=int, default=25,
-                    help="mesh stride of the plain FP64 GPU comparison run (0 = skip it)")
+    ap.add_argument("--fp64-stride", type=int, default=5,
+                    help="mesh stride of the plain FP64 GPU comparison run (0 = skip it): every 5th energy "
+                         "of the n_ch=256 mesh is 10000 energies spanning the whole mesh")
+    ap.add_argument("--fp64-passes", type=int, default=3, help="timed passes of the plain FP64 GPU run")
+    ap.add_argument("--slices", type=int, default=0, choices=(0,) + PRODUCT_SETS,
+                    help="slice products per far term of the tensor-core pole sum (0: the library default)")
+    ap.add_argument("--slices-study", action="store_true",
+                    help="accuracy and energies/s of every product set (3, 6, 10, 13) on this workload")
+    ap.add_argument("--accuracy-energies", type=int, default=64,
+                    help="evenly spaced mesh energies checked against the oracle (plus near-threshold and "
+                         "near-pole energies)")
     ap.add_argument("--stride", type=int, default=0,
                     help="use every stride-th energy of the mesh (0 = automatic)")
     ap.add_argument("--sel", type=int, default=1, help="number of selected initial channels")
@@ -282,7 +310,7 @@ def run_ours(args):
     dE = torch.from_numpy(wl.energies).to(dev)
     cluster = tuple(int(x) for x in args.cluster.split("x")) if args.cluster else None
     plan = rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream, autotune=True,
-                   chunk=args.chunk, cluster=cluster, solve=args.solve)
+                   chunk=args.chunk, cluster=cluster, solve=args.solve, slices=args.slices)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
     def barrier():
@@ -292,6 +320,8 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         plan.run()
+    barrier()
+    peak64 = fp64_peak()  # measured FP64 pipe peak (burst), outside the timed region
     barrier()
     plan.profile(True)
     plan.profile_read()
@@ -354,9 +384,13 @@ def run_ours(args):
         n_l = kern[dom]["launches"]
         avg_ms = kern[dom]["ms_total"] / n_l
         achieved = (total_fl / n_l) / (avg_ms / 1000.0) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic(dom),
-                "peak_source": "FP64 pipe: nominal 1.25 TFLOP/s (a DFMA probe measured 1.2)",
+        pk64 = peak64["tflops"] if peak64 else FP64_NOMINAL_TFLOPS
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": pk64,
+                "unit": "TFLOP/s", "frac": achieved / pk64, "traffic": traffic(dom),
+                "peak_source": ("FP64 pipe, measured in this run by the DFMA probe (libpeak.so, burst)"
+                                if peak64 else "FP64 pipe: nominal 1.25 TFLOP/s (the probe could not run)"),
+                "peak_nominal": FP64_NOMINAL_TFLOPS, "frac_nominal": achieved / FP64_NOMINAL_TFLOPS,
+                "peak_probe": peak64,
                 "flops_per_launch": total_fl / n_l, "avg_launch_ms": avg_ms,
                 "flop_model": ("per energy n^3/3 (real LDL^T: closed channels, then S') + (4/3)n_o^3 + "
                                "8 n_o^2 r (complex LDL^T of Z and its unit right-hand sides); energies "
@@ -367,22 +401,27 @@ def run_ours(args):
                                "skip about 2/3 of the forward elimination, so the FP64 pipe does less "
                                "work than counted (an effective rate)")}
     roof_tc = None
-    if "polesum_split" in kern:
+    products = plan.slices()
+    if "polesum_split" in kern and products:
         info = plan.info(0)
-        hw = tensor_flops(wl, info["chunk"]) * args.steps
+        hw = tensor_flops(wl, info["chunk"], products) * args.steps
         n_l = kern["polesum_split"]["launches"]
         avg_ms = kern["polesum_split"]["ms_total"] / n_l
         achieved = (hw / n_l) / (avg_ms / 1000.0) / 1e12
         pk = peaks.get("bf16_tflops_sustained") or 1700.0
+        alg_kernel = pole_flops * args.steps / (kern["polesum_split"]["ms_total"] / 1000.0) / 1e12
         roof_tc = {"kernel": "polesum_split", "bound": "tensor", "achieved": achieved, "peak": pk,
                    "unit": "TFLOP/s", "frac": achieved / pk, "traffic": traffic("polesum_split"),
-                   "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks
-                   else "fallback 1.7 PFLOP/s sustained",
-                   "flops_per_launch": hw / n_l, "avg_launch_ms": avg_ms,
+                   "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+                   if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)",
+                   "flops_per_launch": hw / n_l, "avg_launch_ms": avg_ms, "products": products,
+                   "algorithmic_tflops_kernel": alg_kernel, "algorithmic_frac": alg_kernel / pk,
                    "algorithmic_tflops": pole_flops * args.steps / (kern["polesum_split"]["ms_total"]
                                                                     + kern.get("near", {}).get("ms_total", 0.0)
                                                                     + kern.get("dslice", {}).get("ms_total", 0.0)) / 1e9,
-                   "note": f"{SPLIT_PRODUCTS} BF16 products per far term; algorithmic = 2 n_p N n_e of Eq. 1-2"}
+                   "note": f"achieved/frac count the {products} BF16 slice products the kernel issues per far "
+                           "term; algorithmic_* count the method's 2 n_p N n_e of Eq. 1-2 (algorithmic_frac: over "
+                           "this kernel's time alone; algorithmic_tflops: over the pole sum's three kernels)"}
 
     # mixed solve: energies whose refinement fell back to FP64 (flag 32) in the last run
     fallback = None
@@ -450,24 +489,29 @@ def run_ours(args):
         e2e = {"value": world * len(wl.waves) * wl.n_e / dt, "unit": "energies/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
 
-    # the plain FP64 GPU form on a strided sub-mesh of the same workload
+    # the plain FP64 GPU form on a sub-mesh of the same workload that spans the whole mesh (the same
+    # mix of open-channel counts): one warm-up pass, then fp64_passes timed passes, L2 flushed before each
     fp64 = None
     if args.prec != "fp64" and args.fp64_stride > 0 and rank == 0:
         sub = wl.energies[::args.fp64_stride].copy()
         dsub = torch.from_numpy(sub).to(dev)
+        ms_l = []
         with rm.Plan(dwaves, dsub, prec="fp64", sel=sel, stream=stream) as p64:
             p64.run()
             torch.cuda.synchronize(dev)
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            flush.fill_(1)
-            a0.record(stream)
-            p64.run()
-            a1.record(stream)
-            p64.sync()
-            ms64 = a0.elapsed_time(a1)
+            for _ in range(max(1, args.fp64_passes)):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(1)
+                a0.record(stream)
+                p64.run()
+                a1.record(stream)
+                p64.sync()
+                ms_l.append(a0.elapsed_time(a1))
+        ms64 = float(np.mean(ms_l))
         v64 = len(wl.waves) * sub.shape[0] / (ms64 / 1000.0)
-        fp64 = {"value": v64, "unit": "energies/s", "sample": f"every {args.fp64_stride}th energy of the mesh "
-                f"({sub.shape[0]} energies), one timed pass", "split_speedup": value / v64}
+        fp64 = {"value": v64, "unit": "energies/s", "ms_per_pass": ms_l,
+                "sample": f"every {args.fp64_stride}th energy of the mesh ({sub.shape[0]} energies spanning it), "
+                          f"one warm-up and {len(ms_l)} timed passes (mean)", "split_speedup": value / v64}
 
     # the same sweep with the K-matrix formed: rm_run with solve "fp64_lu" (LU of the matching system
     # -> K, then the LDL^T of I - iK) instead of the outgoing-wave factorisation, which gives the same
@@ -495,12 +539,19 @@ def run_ours(args):
     cpu = None
     errors = None
     if not args.no_cpu and rank == 0 and world == 1:
-        n, dt, idx, ref = oracle_sample(wl, sel, budget_s=15.0, max_e=24, keep=not args.no_check)
+        _, extra = accuracy_sample(wl, args.accuracy_energies)
+        n, dt, idx, ref = oracle_sample(wl, sel, budget_s=30.0, max_e=args.accuracy_energies,
+                                        keep=not args.no_check)
         cpu = {"value": n / dt, "unit": "energies/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n} evenly spaced energies of the same mesh, FP64 NumPy/SciPy (incl. R and K)",
                "one_thread": oracle_one_thread(args, 4)}
         if ref is not None:
-            errors = accuracy(plan, wl, sel, idx, ref)
+            from oracle import rmatrix as orc
+            ref_x = orc.sweep(wl.waves[0], extra, sel=sel)
+            with rm.Plan(dwaves[:1], torch.from_numpy(extra).to(dev), prec=args.prec, delta=wl.delta, sel=sel,
+                         stream=stream, solve=args.solve, slices=args.slices,
+                         cluster=plan.cluster() if args.prec != "fp64" else None) as px:
+                errors = accuracy(plan, wl, sel, idx, ref, extra, px, ref_x)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": world,
@@ -526,42 +577,178 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def accuracy(plan, wl, sel, idx, ref):
-    """Max normwise errors of the GPU path against oracle outputs on energies idx."""
-    FL_SKIP = 2 | 4 | 8  # ILLCOND | NO_OPEN | SINGULAR
+def accuracy_sample(wl, n_mesh):
+    """Energies the accuracy report checks: n_mesh evenly spaced mesh indices, and extra energies
+    placed 5e-7 Ry either side of four channel thresholds, on two thresholds (nudged) and 5e-7 Ry
+    either side of two poles of the first wave -- the energies the method's targets set apart."""
     w = wl.waves[0]
-    n = w.n
-    eR = eK = eS = eE = ePI = 0.0
+    E = wl.energies
+    idx = np.unique(np.linspace(0, wl.n_e - 1, n_mesh).astype(int))
+    lo, hi = float(E[0]), float(E[-1])
+    thr = np.array([t for t in w.thresh[1:] if lo + 1e-5 < t < hi - 1e-5])
+    extra = []
+    if thr.size:
+        for k in np.unique(np.linspace(0, thr.size - 1, 4).astype(int)):
+            extra += [thr[k] - 5e-7, thr[k] + 5e-7]
+        for k in np.unique(np.linspace(0, thr.size - 1, 2).astype(int)):
+            extra.append(float(thr[k]))
+    pol = w.poles[(w.poles > lo + 1e-3) & (w.poles < hi - 1e-3)]
+    if pol.size:
+        for k in np.unique(np.linspace(0, pol.size - 1, 2).astype(int)):
+            extra += [pol[k] - 5e-7, pol[k] + 5e-7]
+    return idx, np.unique(np.array(extra, dtype=np.float64))
+
+
+def energy_errors(plan, e_idx, ref, run_out, sel, n):
+    """Per energy: normwise errors of the per-range calls (rm_rmatrix, rm_kmatrix, rm_xsec, rm_photo)
+    and of the last rm_run's results (run_out from rm_results) against the oracle outputs ref."""
+    rows = []
     R = np.zeros((1, n * (n + 1) // 2))
     K = np.zeros((1, n, n))
-    for t, e in enumerate(idx):
+    for t, e in enumerate(e_idx):
         e = int(e)
         plan.rmatrix(0, e, e + 1, R)
         Ro = ref["R"][t]
-        eR = max(eR, float(np.abs(R[0] - Ro).max() / np.abs(Ro).max()))
-        if ref["flags"][t] & FL_SKIP:
+        r = {"R": float(np.abs(R[0] - Ro).max() / np.abs(Ro).max())}
+        rows.append(r)
+        if ref["flags"][t] & (4 | 8):  # no open channel, singular
             continue
         plan.kmatrix(0, e, e + 1, K=K)
         no = ref["n_open"][t]
         Ko = ref["K"][t, :no, :no]
-        eK = max(eK, float(np.abs(K[0, :no, :no] - Ko).max() / np.abs(Ko).max()))
+        r["K"] = float(np.abs(K[0, :no, :no] - Ko).max() / np.abs(Ko).max())
         out = {"eigsum": np.zeros(1), "sig_tot": np.zeros((1, len(sel))), "sig_sel": np.zeros((1, len(sel), n))}
         plan.xsec(0, e, e + 1, **out)
+        r["sigma"] = r["rm_run_sigma"] = 0.0
         for q in range(len(sel)):
             st = ref["sig_tot"][t, q]
             if st > 0:
-                eS = max(eS, float(np.abs(out["sig_sel"][0, q] - ref["sig_sel"][t, q]).max() / st))
-        d = out["eigsum"][0] - ref["eta"][t]
-        eE = max(eE, float(abs(np.mod(d + np.pi, 2 * np.pi) - np.pi)))
+                r["sigma"] = max(r["sigma"], float(np.abs(out["sig_sel"][0, q] - ref["sig_sel"][t, q]).max() / st))
+                r["rm_run_sigma"] = max(r["rm_run_sigma"],
+                                        float(np.abs(run_out["sig_sel"][e, q] - ref["sig_sel"][t, q]).max() / st))
+        wrap = lambda d: float(abs(np.mod(d + np.pi, 2 * np.pi) - np.pi))
+        r["eigsum_abs"] = wrap(out["eigsum"][0] - ref["eta"][t])
+        r["rm_run_eta"] = wrap(run_out["eigsum"][e] - ref["eta"][t])
         if "sig_pi" in ref and ref["sig_pi"][t] > 0:
             pi = np.zeros(1)
             plan.photo(0, e, e + 1, sig_pi=pi)
-            ePI = max(ePI, float(abs(pi[0] - ref["sig_pi"][t]) / ref["sig_pi"][t]))
-    res = {"energies_checked": int(len(idx)), "R": eR, "K": eK, "sigma": eS, "eigsum_abs": eE,
-           "norm": "max|x - x*| / max|x*| per energy (sigma: / sigma_tot of the initial channel)"}
+            r["sigma_pi"] = float(abs(pi[0] - ref["sig_pi"][t]) / ref["sig_pi"][t])
+    return rows
+
+
+def flag_classes(w, E_raw, flags):
+    """Masks of the energies the targets set apart: within 1e-6 Ry of a threshold (the oracle's
+    NEAR_THRESHOLD flag) or of a pole, or with an ill-conditioned matching LU (ILLCOND)."""
+    near_pole = np.array([np.min(np.abs(w.poles - e)) < 1e-6 for e in E_raw], dtype=bool)
+    return {"near_threshold": (flags & 128) != 0, "near_pole": near_pole, "illcond": (flags & 2) != 0}
+
+
+def summarize(rows, classes):
+    """Max errors over regular energies, and over the flagged ones in a section of their own
+    (K of ILLCOND energies, which the LU form cannot resolve, reported as K_illcond)."""
+    keys = ("R", "K", "sigma", "eigsum_abs", "rm_run_sigma", "rm_run_eta", "sigma_pi")
+    flagged = np.zeros(len(rows), bool)
+    for m in classes.values():
+        flagged |= m
+    reg = {k: 0.0 for k in keys}
+    fl = {k: 0.0 for k in keys}
+    fl["K_illcond"] = 0.0
+    for i, r in enumerate(rows):
+        tgt = fl if flagged[i] else reg
+        for k in keys:
+            if k in r:
+                if k == "K" and classes["illcond"][i]:
+                    fl["K_illcond"] = max(fl["K_illcond"], r[k])
+                else:
+                    tgt[k] = max(tgt[k], r[k])
+    counts = {k: int(m.sum()) for k, m in classes.items()}
+    fl.update(energies=int(flagged.sum()), **counts)
+    reg["energies"] = int((~flagged).sum())
+    return reg, fl
+
+
+def accuracy(plan, wl, sel, idx, ref, extra=None, extra_plan=None, ref_extra=None):
+    """Max normwise errors of the GPU path against the oracle: the timed plan on mesh energies idx
+    (per-range calls and the last rm_run's rm_results), and a second plan of the same options on
+    the near-threshold / near-pole energies `extra`; flagged energies reported apart."""
+    w = wl.waves[0]
+    n = w.n
+    run_out = {"eigsum": np.zeros(wl.n_e), "sig_sel": np.zeros((wl.n_e, len(sel), n))}
+    plan.results(0, 0, wl.n_e, eigsum=run_out["eigsum"], sig_sel=run_out["sig_sel"])
+    rows = energy_errors(plan, idx, ref, run_out, sel, n)
+    E_raw = list(wl.energies[idx])
+    flags = list(ref["flags"])
+    if extra is not None and extra_plan is not None and extra.size:
+        extra_plan.run()
+        xo = {"eigsum": np.zeros(extra.size), "sig_sel": np.zeros((extra.size, len(sel), n))}
+        extra_plan.results(0, 0, extra.size, eigsum=xo["eigsum"], sig_sel=xo["sig_sel"])
+        rows += energy_errors(extra_plan, np.arange(extra.size), ref_extra, xo, sel, n)
+        E_raw += list(extra)
+        flags += list(ref_extra["flags"])
+    classes = flag_classes(w, np.array(E_raw), np.array(flags, dtype=np.uint8))
+    reg, fl = summarize(rows, classes)
+    res = {"energies_checked": len(rows), "mesh_energies": int(len(idx)),
+           "extra_energies": 0 if extra is None else int(extra.size),
+           "R": reg["R"], "K": reg["K"], "sigma": reg["sigma"], "eigsum_abs": reg["eigsum_abs"],
+           "rm_run_sigma": reg["rm_run_sigma"], "rm_run_eta": reg["rm_run_eta"],
+           "flagged": fl,
+           "norm": "max|x - x*| / max|x*| per energy (sigma: / sigma_tot of the initial channel); "
+                   "rm_run_*: the timed rm_run's rm_results; flagged: within 1e-6 Ry of a threshold or a "
+                   "pole, or ILLCOND, judged apart"}
     if "sig_pi" in ref:
-        res["sigma_pi"] = ePI
+        res["sigma_pi"] = reg["sigma_pi"]
     return res
+
+
+def run_slices_study(args):
+    """Every product set of the tensor-core pole sum on this workload: rm_run energies/s (one warm-up,
+    three timed passes, L2 flushed before each), the pole-sum kernel's time, and the accuracy report
+    (mesh and near-threshold / near-pole energies against the oracle).  One JSON line per set."""
+    import torch
+    from oracle import rmatrix as orc
+    from paper_1403_5524_gb300 import rm
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl, stride = workload(args)
+    sel = tuple(range(args.sel))
+    stream = torch.cuda.current_stream(dev)
+    dwaves = [synth.Wave(l=torch.from_numpy(w.l).to(dev), thresh=torch.from_numpy(w.thresh).to(dev),
+                         poles=torch.from_numpy(w.poles).to(dev), W=torch.from_numpy(w.W).to(dev), a=w.a, z=w.z,
+                         dip=None if w.dip is None else torch.from_numpy(w.dip).to(dev), e0=w.e0)
+              for w in wl.waves]
+    dE = torch.from_numpy(wl.energies).to(dev)
+    idx, extra = accuracy_sample(wl, args.accuracy_energies)
+    ref = orc.sweep(wl.waves[0], wl.energies, sel=sel, energy_idx=idx)
+    ref_x = orc.sweep(wl.waves[0], extra, sel=sel)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    prec = args.prec if args.prec in ("split_bf16", "split_fp16") else "split_bf16"
+    for products in PRODUCT_SETS:
+        with rm.Plan(dwaves, dE, prec=prec, delta=wl.delta, sel=sel, stream=stream, autotune=True,
+                     slices=products, solve=args.solve) as p:
+            p.run()
+            torch.cuda.synchronize(dev)
+            ms = []
+            for _ in range(3):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(1)
+                a0.record(stream)
+                p.run()
+                a1.record(stream)
+                p.sync()
+                ms.append(a0.elapsed_time(a1))
+            p.profile(True)
+            p.profile_read()
+            p.run()
+            prof = p.profile_read()
+            p.profile(False)
+            with rm.Plan(dwaves[:1], torch.from_numpy(extra).to(dev), prec=prec, delta=wl.delta, sel=sel,
+                         stream=stream, solve=args.solve, slices=products, cluster=p.cluster()) as px:
+                err = accuracy(p, wl, sel, idx, ref, extra, px, ref_x)
+            line = {"slices_study": products, "prec": prec, "workload": wl.name, "mesh_stride": stride,
+                    "energies_per_s": len(wl.waves) * wl.n_e / (float(np.mean(ms)) / 1000.0), "ms_per_step": ms,
+                    "polesum_split_ms": prof["polesum_split"][0], "tc_cluster": "%dx%d" % p.cluster(),
+                    "errors": err}
+        print(json.dumps(line), flush=True)
 
 
 def run_variants(args):
@@ -649,6 +836,9 @@ def main():
         return
     if args.variants:
         run_variants(args)
+        return
+    if args.slices_study:
+        run_slices_study(args)
         return
     if args.impl == "reference":
         run_reference(args)

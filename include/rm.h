@@ -28,6 +28,19 @@
  * trouble at a single energy is not an error: it is reported in the per-energy
  * flags (RM_FLAG_*).
  *
+ * Fault injection for tests (host side only; read at each rm_plan_create):
+ *   RM_FAULT_ALLOC=k        the k-th device allocation of the call fails as if
+ *                           the device were out of memory (RM_ERR_NOMEM; the
+ *                           partial plan is freed, *out stays NULL).
+ *   RM_FAULT_WAIT_CYCLES=c  every mbarrier wait of the plan's unclustered
+ *                           tensor-core launches gives up after c clock cycles
+ *                           instead of about 2 s; an aborted tile lets its own
+ *                           copies and MMAs finish, frees its TMEM and reports
+ *                           RM_ERR_TIMEOUT through rm_sync / the next host-
+ *                           memory call.  Clustered launches ignore it.
+ * Tracing: every ABI call, and every kernel launch while per-kernel timing is
+ * on, is an NVTX range named after it (no cost without a profiler).
+ *
  * Layouts (all row-major, 0-based):
  *   W          n_ch x n_poles, w_ik at W[i*n_poles + k]
  *   R_packed   per energy, the upper triangle row by row:
@@ -79,14 +92,19 @@ typedef enum {
 #define RM_FLAG_NO_OPEN 4u   /* no open channel (E below every threshold); outputs are zero */
 #define RM_FLAG_SINGULAR 8u  /* exact zero pivot; outputs are NaN */
 #define RM_FLAG_ASYM 16u     /* a Coulomb / Whittaker continued fraction did not converge within its
-                                iteration cap for some channel (z > 0 only); outputs are unreliable */
+                                iteration cap for some channel (z > 0 only), or (rm_xsec_from_r_static
+                                only) a channel's l lay outside [0, RM_LMAX]; outputs are unreliable */
 #define RM_FLAG_FP64 32u     /* solve_prec = RM_SOLVE_MIXED: the FP32 refinement did not converge (or hit a
                                 zero pivot) and the matching system was solved in FP64 instead */
 #define RM_FLAG_LU 64u       /* rm_run / rm_xsec with solve_prec = RM_SOLVE_FP64: the outgoing-wave
                                 factorisation failed its growth or pivot check and the energy was solved
                                 by LU with partial pivoting instead (same results, more flops) */
+#define RM_FLAG_NEAR_THRESHOLD 128u /* the input energy lies within 1e-6 Ry of a channel threshold (tested
+                                       before any nudge): a channel opens there (k -> 0), so its results
+                                       are reported, and judged, apart from the rest of the mesh */
 
 #define RM_LMAX 32           /* largest supported channel angular momentum */
+#define RM_DEFAULT_SLICES 13 /* slice products of the tensor-core pole sum when rm_options.slices = 0 */
 #define RM_MAX_SEL 64        /* largest number of selected initial channels */
 
 /* Matching solve.  FP64: rm_kmatrix solves for K by LU
@@ -132,7 +150,15 @@ typedef struct {
 typedef struct {
   int32_t prec;            /* rm_precision_t */
   double delta;            /* near-pole window half width (Ry) for split modes; > 0 */
-  int32_t slices;          /* split slices per operand (0 = default) */
+  int32_t slices;          /* SPLIT_BF16 / SPLIT_FP16: slice products per far term P_pk D_ke.  Both
+                              operands are cut into up to four 8-bit slices q_0..q_3, r_0..r_3
+                              (orders of 2^-8); the product sums q_u r_v over
+                                3:  u + v <= 1 (two slices each),
+                                6:  u + v <= 2 (three slices each),
+                                10: u + v <= 3 (four slices each),
+                                13: u + v <= 3 and (1,3), (2,2), (3,1).
+                              0 = RM_DEFAULT_SLICES.  Fewer products are faster and less
+                              accurate; other precisions take 0 only (else RM_ERR_ARG). */
   const int32_t* sel_init; /* host array of selected initial channels; NULL = {0} */
   int32_t n_sel;           /* entries in sel_init (ignored when sel_init is NULL) */
   int32_t mem;             /* rm_mem_t of every input pointer (waves and energies) */
@@ -252,6 +278,10 @@ rm_status_t rm_plan_info(rm_plan_t plan, int32_t wave, int32_t* n_ch, int32_t* n
 /* Cluster shape of rm_run's tensor-core pole-sum launch (1 x 1 outside split modes). */
 rm_status_t rm_plan_cluster(rm_plan_t plan, int32_t* cluster_x, int32_t* cluster_y);
 
+/* Slice products per far term of the plan's tensor-core pole sum (3, 6, 10 or 13; 0 when the
+   plan's precision has no tensor-core pole sum). */
+rm_status_t rm_plan_slices(rm_plan_t plan, int32_t* products);
+
 /* Number of kernel launches this plan has issued since creation. */
 int64_t rm_plan_launches(rm_plan_t plan);
 
@@ -279,16 +309,17 @@ const char* rm_last_error(void);
 /*
  * K-matrix / S-step without any device allocation.  The paper has no
  * counterpart to this call: it exists for callers that are not allowed to
- * call cudaMalloc (code that runs inside another library's stream capture,
- * plug-ins bound to a host application's fixed memory pool, real-time loops
- * where an allocation may block or fail).  It computes what rm_kmatrix and
+ * call cudaMalloc (plug-ins bound to a host application's fixed memory pool,
+ * real-time loops where an allocation may block or fail, code running where
+ * the device allocator is off limits to it).  It computes what rm_kmatrix and
  * rm_xsec compute, from packed R-matrices the caller already holds, with the
  * same kernels; its only scratch is a static device array of
  * RM_STATIC_SCRATCH_BYTES inside this library, which every GPU that loads the
  * library holds until the process exits.  It allocates nothing, host or
  * device, and calls no allocating library routine.
  *
- * All array pointers are DEVICE pointers except sel_init (host; NULL = {0}).
+ * All array pointers are DEVICE pointers except sel_init (host; NULL = {0}),
+ * which is read before the call returns (it travels as a kernel argument).
  *   R_packed  [n_e * n_p] packed upper triangles, energy-major (as rm_rmatrix)
  *   l, thresh [n_ch]; pole_E [n_poles] (used only to nudge energies that sit
  *             on a pole, exactly as rm_plan_create does); energies [n_e]
@@ -296,15 +327,24 @@ const char* rm_last_error(void);
  *             sig_tot [n_e*n_sel], sig_sel [n_e*n_sel*n], flags, n_open);
  *             any may be NULL
  * Inputs are not validated on the device: thresholds and poles must be sorted
- * ascending and finite.  The work is enqueued on cuda_stream (NULL = default
- * stream) and the call returns without waiting.
- * Sizes: n_ch is limited by the scratch (one solve workspace of about
- * 4 n_ch^2 + 2 n_ch (n_sel + 1) doubles must fit); larger n_ch returns RM_ERR_ARG.
- * Set-up: the first call on each device looks up the scratch array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one scratch array and every call overwrites
- * it, so calls that may overlap on the GPU (different streams, or threads)
- * race and must be serialised by the caller.  Errors: rm_static_last_error().
+ * ascending and finite.  An l outside [0, RM_LMAX] is clamped for the
+ * asymptotic functions and sets RM_FLAG_ASYM on every energy of the call.
+ * The work is enqueued on cuda_stream (NULL = default stream) and the call
+ * returns without waiting.
+ * Sizes: 1 <= n_ch <= 640, as for rm_wave (larger n_ch returns RM_ERR_ARG);
+ * 1 <= n_sel <= RM_MAX_SEL.  Each resident solve CTA needs a workspace of about
+ * 4 n_ch^2 + 2 n_ch (n_sel + 1) doubles in the scratch (13 MB at n_ch = 640),
+ * besides 32 n_ch bytes per energy of the current chunk, so the scratch holds at
+ * most one workspace per SM and about 2^21 / n_ch^2 in all: from n_ch ~ 120 up
+ * fewer solve CTAs run than a plan would use (30 at n_ch = 256, 5 at 640), the
+ * price of not allocating.  rm_static_layout reports the energy chunk and the
+ * number of solve workspaces a call will use.
+ * Set-up: the first call on each device (with that device current) looks up
+ * the scratch array's device address (cudaGetSymbolAddress) and the device's
+ * attributes; make that first call before any stream capture.  All calls
+ * share the one scratch array and every call overwrites it, so calls that may
+ * overlap on the GPU (different streams, or threads) race and must be
+ * serialised by the caller.  Errors: rm_static_last_error().
  */
 #define RM_STATIC_SCRATCH_BYTES (64ll << 20)
 rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_ch, int32_t n_poles, double a,
@@ -314,6 +354,10 @@ rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_ch, int32_t 
                                   double* sig_sel, uint8_t* flags, int32_t* n_open,
                                   void* cuda_stream);
 const char* rm_static_last_error(void);
+/* Energy chunk and number of solve workspaces rm_xsec_from_r_static uses for n_ch channels and
+   n_sel selected channels on the current device; RM_ERR_ARG for sizes the call rejects.  Does
+   the call's per-device set-up, no other device work. */
+rm_status_t rm_static_layout(int32_t n_ch, int32_t n_sel, int32_t* chunk, int32_t* slots);
 
 #ifdef __cplusplus
 }

@@ -1,8 +1,12 @@
-"""Build the CUDA library ``librm.so`` in-tree for sm_103a (GB300).
+"""Build the CUDA libraries in-tree for sm_103a (GB300).
 
-Each translation unit under ``csrc/`` is compiled in parallel with nvcc
-(``-gencode arch=compute_103a,code=sm_103a``) and linked into a shared object
-next to this file.  Nothing here needs a GPU, so it runs on a build host too.
+``librm.so``   the R-matrix library: every translation unit under ``csrc/``,
+               compiled in parallel with nvcc (``-gencode arch=compute_103a,code=sm_103a``)
+               and linked into a shared object next to this file.
+``libpeak.so`` the FP64 pipe peak probe (``probe/fp64_peak.cu``), the measured
+               denominator of the FP64 rooflines the benchmark reports.
+
+Nothing here needs a GPU, so it runs on a build host too.
 """
 from __future__ import annotations
 
@@ -15,8 +19,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
+PROBE = os.path.join(HERE, "probe")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librm.so")
+PEAK_LIB = os.path.join(HERE, "libpeak.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -30,12 +36,12 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+def sources(folder=CSRC):
+    return sorted(os.path.join(folder, f) for f in os.listdir(folder) if f.endswith(".cu"))
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra, tag: str = "") -> str:
+    obj = os.path.join(BUILD, tag + os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -43,19 +49,25 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
+def _link(objs, out: str):
+    tmp = out + ".tmp"
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link of {out} failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, out)
+
+
 def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    if verbose:
-        print("built", LIB)
+    jobs = [(s, "", LIB) for s in sources()] + [(s, "probe_", PEAK_LIB) for s in sources(PROBE)]
+    # the longest translation units first, so the pool's tail is short
+    jobs.sort(key=lambda j: -os.path.getsize(j[0]))
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(lambda j: (j[2], _compile(j[0], list(extra), j[1])), jobs))
+    for lib in (LIB, PEAK_LIB):
+        _link([o for l, o in objs if l == lib], lib)
+        if verbose:
+            print("built", lib)
     return LIB
 
 

@@ -56,7 +56,7 @@ constexpr int TX_BYTES = (WI_FLOATS + WJ_FLOATS + PO_FLOATS) * 4;  // 6400
 constexpr int STAGE_STRIDE = ((A_BYTES + B_BYTES + TX_BYTES + 1023) / 1024) * 1024;
 constexpr int NBARS = 5 * STAGES + 3;
 constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_STRIDE + 1024 + NBARS * 8 + 16;
-constexpr long long WAIT_BUDGET = 4000000000LL;   // clock cycles (~2 s)
+constexpr long long WAIT_BUDGET = 4000000000LL;   // clock cycles (~2 s) per mbarrier wait
 
 static_assert(BM == 128 && BN == 128, "TMEM layout assumes 128 x 128 tiles");
 
@@ -153,6 +153,8 @@ struct TCArgs {
   const int2* tiles;
   int n, N, nK;
   int f16;          // slices in FP16 instead of BF16
+  int nprod;        // slice products per far term: 3, 6, 10 or 13
+  long long wait_budget;  // clock cycles a single mbarrier wait may take before the tile aborts
   int64_t e_begin;  // absolute index of the chunk's first energy
   int ne;           // energies in the chunk
   double* R;        // [ne * np]
@@ -263,20 +265,21 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       for (int s = 0; s < STAGES && s < nK; ++s) issue_tma(s, s);
       const uint32_t idN256 = idesc_bf16_f32(128, 256, g.f16 != 0);
       const uint32_t idN128 = idesc_bf16_f32(128, 128, g.f16 != 0);
+      const int nprod = g.nprod;
       bool ok = true;
       bool issued = false;
       for (int j = 0; j < nK; ++j) {
         const int s = j % STAGES;
         bool got;
-        if constexpr (CL > 1) got = mbar_wait_cluster(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET);
-        else got = mbar_wait(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET);
-        if (got && DT) got = mbar_wait(dfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET);
+        if constexpr (CL > 1) got = mbar_wait_cluster(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget);
+        else got = mbar_wait(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget);
+        if (got && DT) got = mbar_wait(dfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget);
         if (!got) { ok = false; break; }
         if (j + STAGES < nK) issue_tma(s, j + STAGES);
         const int d = j / DRAIN_KSTEPS;
         const bool first = (j % DRAIN_KSTEPS) == 0;
         if (first && d > 0) {
-          if (!mbar_wait(acc_empty, (uint32_t)((d - 1) & 1), abort_flag, WAIT_BUDGET)) { ok = false; break; }
+          if (!mbar_wait(acc_empty, (uint32_t)((d - 1) & 1), abort_flag, g.wait_budget)) { ok = false; break; }
         }
         tc_fence_after();
         const uint32_t a = smem_u32(smem + s * STAGE_STRIDE);
@@ -285,17 +288,31 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         for (int kk = 0; kk < 2; ++kk) {
           const uint32_t ko = kk * 32;
           const uint32_t f = (first && kk == 0) ? 0u : 1u;
-          // columns: order 0 [0,128), 1 [128,256), 2 [256,384), 3 [384,512)
-          mma_bf16_ss(tmem + 0, desc_kmajor_sw64(a + 0 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 0 * SLICE_BYTES + ko), idN256, f);
-          mma_bf16_ss(tmem + 256, desc_kmajor_sw64(a + 0 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 2 * SLICE_BYTES + ko), idN256, f);
-          mma_bf16_ss(tmem + 128, desc_kmajor_sw64(a + 1 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 0 * SLICE_BYTES + ko), idN256, 1u);
-          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 1 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 2 * SLICE_BYTES + ko), idN128, 1u);
-          mma_bf16_ss(tmem + 256, desc_kmajor_sw64(a + 2 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 0 * SLICE_BYTES + ko), idN256, 1u);
-          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 3 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 0 * SLICE_BYTES + ko), idN128, 1u);
-          // order-4 products (1,3), (2,2), (3,1) into the order-3 accumulator
-          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 1 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 3 * SLICE_BYTES + ko), idN128, 1u);
-          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 2 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 2 * SLICE_BYTES + ko), idN128, 1u);
-          mma_bf16_ss(tmem + 384, desc_kmajor_sw64(a + 3 * SLICE_BYTES + ko), desc_kmajor_sw64(b + 1 * SLICE_BYTES + ko), idN128, 1u);
+          auto A = [&](int u) { return desc_kmajor_sw64(a + u * SLICE_BYTES + ko); };
+          auto B = [&](int v) { return desc_kmajor_sw64(b + v * SLICE_BYTES + ko); };
+          // columns: order 0 [0,128), 1 [128,256), 2 [256,384), 3 [384,512); an N = 256 product
+          // q_u x [r_v | r_v+1] writes orders u+v and u+v+1 at once.  The first product into
+          // each used accumulator of a drain period starts it (f = 0).
+          mma_bf16_ss(tmem + 0, A(0), B(0), idN256, f);  // (0,0) (0,1)
+          if (nprod == 3) {
+            mma_bf16_ss(tmem + 128, A(1), B(0), idN128, 1u);  // (1,0)
+          } else if (nprod == 6) {
+            mma_bf16_ss(tmem + 256, A(0), B(2), idN128, f);   // (0,2)
+            mma_bf16_ss(tmem + 128, A(1), B(0), idN256, 1u);  // (1,0) (1,1)
+            mma_bf16_ss(tmem + 256, A(2), B(0), idN128, 1u);  // (2,0)
+          } else {
+            mma_bf16_ss(tmem + 256, A(0), B(2), idN256, f);   // (0,2) (0,3)
+            mma_bf16_ss(tmem + 128, A(1), B(0), idN256, 1u);  // (1,0) (1,1)
+            mma_bf16_ss(tmem + 384, A(1), B(2), idN128, 1u);  // (1,2)
+            mma_bf16_ss(tmem + 256, A(2), B(0), idN256, 1u);  // (2,0) (2,1)
+            mma_bf16_ss(tmem + 384, A(3), B(0), idN128, 1u);  // (3,0)
+            if (nprod == 13) {
+              // order-4 products (1,3), (2,2), (3,1) into the order-3 accumulator
+              mma_bf16_ss(tmem + 384, A(1), B(3), idN128, 1u);
+              mma_bf16_ss(tmem + 384, A(2), B(2), idN128, 1u);
+              mma_bf16_ss(tmem + 384, A(3), B(1), idN128, 1u);
+            }
+          }
         }
         issued = true;
         if constexpr (CL > 1) mma_commit_mc(empty + s, (uint16_t)peer_mask);
@@ -306,7 +323,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         // every peer's commit for the last use of each stage has landed here, so no
         // arrive can reach this CTA's barriers after it exits
         for (int j = (nK > STAGES ? nK - STAGES : 0); j < nK; ++j)
-          if (!mbar_wait_cluster(empty + j % STAGES, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) break;
+          if (!mbar_wait_cluster(empty + j % STAGES, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget)) break;
       }
       if (!ok) {
         // abort path: let in-flight TMA loads and MMAs finish before the CTA exits
@@ -334,7 +351,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       const uint32_t sbase = smem_u32(smem);
       for (int j = 0; j < nK; ++j) {
         const int s = j % STAGES;
-        if (!mbar_wait(gen + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) break;
+        if (!mbar_wait(gen + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget)) break;
         mbar_arrive_expect_tx(full + s, IN_BYTES);
         const uint32_t st = sbase + (uint32_t)(s * STAGE_STRIDE);
 #pragma unroll
@@ -366,6 +383,9 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
     // -------------------------------------------------- producers and drains
     const int w = warp;
     const bool f16 = g.f16 != 0;
+    // slices per operand and accumulator orders the product set uses
+    const int nsl = g.nprod == 3 ? 2 : (g.nprod == 6 ? 3 : 4);
+    const int nord = nsl;
     // A role (pair rows of i-blocks ry*8/CY .. +8/CY): i-row ai, j-rows
     // jj = jbase + 2t, k-pair kpa; a half-warp writes one full slice row.
     constexpr int TA = 4 / CY;   // j-rows per thread
@@ -414,8 +434,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       if (j >= STAGES) {
         bool got;
         if constexpr (CL > 1)
-          got = mbar_wait_cluster(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, WAIT_BUDGET);
-        else got = mbar_wait(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, WAIT_BUDGET);
+          got = mbar_wait_cluster(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, g.wait_budget);
+        else got = mbar_wait(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, g.wait_budget);
         if (!got) {
           ok = false;
           break;
@@ -426,7 +446,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         tma_load_3d(smem + s * STAGE_STRIDE + A_BYTES, map_d, dfull + s, j * KS, n0, 0);
         d_last[s] = j;
       }
-      if (!mbar_wait(wfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, WAIT_BUDGET)) {
+      if (!mbar_wait(wfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget)) {
         ok = false;
         break;
       }
@@ -453,7 +473,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         slice4(__fmul_rn(ph1, mp[t]), __fmul_rn(pl1, mp[t]), s1);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + offA[t]) = pack_slice(s0[u], s1[u], f16);
+          if (u < nsl) *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + offA[t]) = pack_slice(s0[u], s1[u], f16);
       }
       if constexpr (!DT) {
         const int k0 = j * KS;
@@ -471,7 +491,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           uint32_t wd[4];
           d_pack(ph.x, pl.x, ph.y, pl.y, eh, el, far0 ? me : 0.0f, far1 ? me : 0.0f, f16, wd);
 #pragma unroll
-          for (int v = 0; v < 4; ++v) *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + offB[t]) = wd[v];
+          for (int v = 0; v < 4; ++v)
+            if (v < nsl) *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + offB[t]) = wd[v];
         }
       }
       // the MMAs (and, in clusters, the bulk copies) read these slices through the async proxy
@@ -480,7 +501,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       if (lane == 0) mbar_arrive(CL > 1 ? gen + s : full + s);
       if ((j + 1) % DRAIN_KSTEPS == 0 || j == nK - 1) {
         const int d = j / DRAIN_KSTEPS;
-        if (!mbar_wait(acc_full, (uint32_t)(d & 1), abort_flag, WAIT_BUDGET)) {
+        if (!mbar_wait(acc_full, (uint32_t)(d & 1), abort_flag, g.wait_budget)) {
           ok = false;
           break;
         }
@@ -496,7 +517,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
               const int i = h * 16 + c;
-              const float x = __uint_as_float(r[c]);
+              // an order the product set leaves unused holds stale TMEM: select it away
+              const float x = o < nord ? __uint_as_float(r[c]) : 0.0f;
               if (o < 3) {
                 float sh, se;
                 two_sum(Vh[i], x, sh, se);
@@ -930,6 +952,8 @@ cudaError_t launch_polesum_split(const Plan& p, const WaveDev& w, int64_t e0, in
   g.N = w.N;
   g.nK = w.Npad / KS;
   g.f16 = p.prec == RM_PREC_SPLIT_FP16 ? 1 : 0;
+  g.nprod = p.slices;
+  g.wait_budget = p.fault_wait > 0 ? p.fault_wait : WAIT_BUDGET;  // this launch runs unclustered
   g.e_begin = e0;
   g.ne = ne;
   g.R = R;
@@ -1035,6 +1059,10 @@ cudaError_t group_setup_split(Plan& p) {
     a.N = w.N;
     a.nK = w.Npad / KS;
     a.f16 = p.prec == RM_PREC_SPLIT_FP16 ? 1 : 0;
+    a.nprod = p.slices;
+    // the test hook that shortens the waits applies to unclustered launches only: there no
+    // other CTA's copies or commits can still be arriving when an aborted tile exits
+    a.wait_budget = (p.fault_wait > 0 && G.tc_cx * G.tc_cy == 1) ? p.fault_wait : WAIT_BUDGET;
     a.e_begin = 0;
     a.ne = 0;
     a.R = G.R[g];

@@ -51,14 +51,16 @@ __global__ void prep_kernel(const double* __restrict__ energies, int64_t n_e,
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_e) return;
   double E = energies[e];
-  double dmin = INFINITY;
+  double dmin = INFINITY, dthr = INFINITY;
   int k = lower_bound(poles, N, E);
   if (k < N) dmin = fmin(dmin, fabs(poles[k] - E));
   if (k > 0) dmin = fmin(dmin, fabs(poles[k - 1] - E));
   int i = lower_bound(thr, n, E);
-  if (i < n) dmin = fmin(dmin, fabs(thr[i] - E));
-  if (i > 0) dmin = fmin(dmin, fabs(thr[i - 1] - E));
+  if (i < n) dthr = fmin(dthr, fabs(thr[i] - E));
+  if (i > 0) dthr = fmin(dthr, fabs(thr[i - 1] - E));
+  dmin = fmin(dmin, dthr);
   uint8_t f = 0;
+  if (dthr < 1e-6) f |= RM_FLAG_NEAR_THRESHOLD;  // a channel opens within 1e-6 Ry of the input energy
   if (dmin < 1e-9) {  // one move of 1e-6 Ry up, no re-check
     E += 1e-6;
     f |= RM_FLAG_NUDGED;

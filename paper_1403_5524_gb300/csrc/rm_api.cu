@@ -6,6 +6,8 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rm_internal.cuh"
 
 using namespace rm;
@@ -14,6 +16,27 @@ namespace {
 
 
 thread_local std::string g_err;
+
+// Host-side fault injection for tests (no GPU fault is ever made): with RM_FAULT_ALLOC=k in the
+// environment, the k-th device allocation of each rm_plan_create call fails as if cudaMalloc had
+// run out of memory.  Read at the start of every rm_plan_create.
+thread_local int g_alloc_fail_at = 0;
+thread_local int g_alloc_count = 0;
+
+long long env_ll(const char* name) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return 0;
+  char* end = nullptr;
+  const long long x = std::strtoll(v, &end, 10);
+  return (end && *end == 0 && x > 0) ? x : 0;
+}
+
+// NVTX range around each ABI call and (with per-kernel timing) each kernel launch; a no-op unless
+// a profiler is attached.
+struct Nvtx {
+  explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+  ~Nvtx() { nvtxRangePop(); }
+};
 
 rm_status_t fail(rm_status_t s, const std::string& msg) {
   g_err = msg;
@@ -36,6 +59,8 @@ rm_status_t dalloc(Plan* p, T** ptr, int64_t count) {
   *ptr = nullptr;
   if (count <= 0) return RM_OK;
   const size_t bytes = (size_t)count * sizeof(T);
+  if (g_alloc_fail_at > 0 && ++g_alloc_count == g_alloc_fail_at)
+    return fail(RM_ERR_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (RM_FAULT_ALLOC)");
   cudaError_t e = cudaMalloc((void**)ptr, bytes);
   if (e != cudaSuccess) {
     *ptr = nullptr;
@@ -197,14 +222,20 @@ struct Prof {
   cudaEvent_t a = nullptr, b = nullptr;
   Prof(Plan* p_, int k_) : Prof(p_, k_, p_->prof, p_->stream, true) {}
   // count = false while capturing into a graph (graph launches are counted per replay)
+  bool range = false;
   Prof(Plan* p_, int k_, bool on, cudaStream_t s_, bool count) : p(p_), k(k_), s(s_) {
     if (count) p->launches++;
     if (!on) return;
+    static const char* names[RM_KERNEL_COUNT] = {"rm:polesum_fp64", "rm:polesum_split", "rm:near",
+                                                 "rm:asym", "rm:solve", "rm:dslice"};
+    nvtxRangePushA(names[k]);
+    range = true;
     a = pool_event(p);
     b = pool_event(p);
     if (a) cudaEventRecord(a, s);
   }
   ~Prof() {
+    if (range) nvtxRangePop();
     if (!a || !b) return;
     cudaEventRecord(b, s);
     p->ev_live[k].push_back({a, b});
@@ -413,7 +444,8 @@ rm_status_t build_graph(Plan* p) {
 // an optional text file, one "key|chunk cluster_x cluster_y" line per plan
 // shape, keyed by the plan's sizes.
 std::string tune_key(const Plan* p) {
-  std::string k = "rm2 prec=" + std::to_string(p->prec) + " ne=" + std::to_string(p->n_e) +
+  std::string k = "rm3 prec=" + std::to_string(p->prec) + " prod=" + std::to_string(p->slices) +
+                  " ne=" + std::to_string(p->n_e) +
                   " sel=" + std::to_string(p->n_sel);
   for (const auto& w : p->waves) k += " " + std::to_string(w.nR) + "x" + std::to_string(w.N);
   return k;
@@ -583,9 +615,12 @@ const char* rm_last_error(void) { return g_err.c_str(); }
 rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves,
                            const double* energies, int64_t n_e, const rm_options* opt,
                            void* cuda_stream) {
+  Nvtx range("rm_plan_create");
   try {
     if (!out) return fail(RM_ERR_ARG, "out is null");
     *out = nullptr;
+    g_alloc_fail_at = (int)env_ll("RM_FAULT_ALLOC");
+    g_alloc_count = 0;
     if (!waves || n_waves < 1) return fail(RM_ERR_ARG, "need at least one wave");
     if (n_e < 0 || (n_e > 0 && !energies)) return fail(RM_ERR_ARG, "bad energy mesh");
     rm_options o;
@@ -594,6 +629,10 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     if (o.prec < RM_PREC_FP64 || o.prec > RM_PREC_FP32_SIMT) return fail(RM_ERR_ARG, "bad precision mode");
     if (o.prec != RM_PREC_FP64 && !(o.delta > 0.0)) return fail(RM_ERR_ARG, "delta must be > 0");
     if (o.chunk < 0) return fail(RM_ERR_ARG, "chunk must be >= 0");
+    if (!(o.slices == 0 || o.slices == 3 || o.slices == 6 || o.slices == 10 || o.slices == 13))
+      return fail(RM_ERR_ARG, "slices must be 0 (default), 3, 6, 10 or 13 slice products");
+    if (o.slices != 0 && o.prec != RM_PREC_SPLIT_BF16 && o.prec != RM_PREC_SPLIT_FP16)
+      return fail(RM_ERR_ARG, "slices applies to the tensor-core modes (SPLIT_BF16, SPLIT_FP16) only");
     if (o.solve_prec != RM_SOLVE_FP64 && o.solve_prec != RM_SOLVE_MIXED && o.solve_prec != RM_SOLVE_FP64_LU)
       return fail(RM_ERR_ARG, "bad solve precision");
     if (!(o.cluster_x == 0 || o.cluster_x == 1 || o.cluster_x == 2 || o.cluster_x == 4) ||
@@ -630,7 +669,8 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     p->n_e = n_e;
     p->prec = o.prec;
     p->delta = o.delta;
-    p->slices = o.slices;
+    p->slices = o.slices ? o.slices : RM_DEFAULT_SLICES;
+    p->fault_wait = env_ll("RM_FAULT_WAIT_CYCLES");
     p->n_sel = n_sel;
     std::memcpy(p->sel, sel, sizeof(sel));
     p->sm_count = prop.multiProcessorCount;
@@ -791,6 +831,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
 }
 
 rm_status_t rm_plan_load(rm_plan_t h, const rm_wave* waves, const double* energies, int32_t mem) {
+  Nvtx range("rm_plan_load");
   try {
     Plan* p = as_plan(h);
     if (!p) return fail(RM_ERR_ARG, "null plan");
@@ -812,6 +853,7 @@ rm_status_t rm_plan_load(rm_plan_t h, const rm_wave* waves, const double* energi
 }
 
 rm_status_t rm_rmatrix(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* R_packed, int32_t mem) {
+  Nvtx range("rm_rmatrix");
   try {
     Plan* p = as_plan(h);
     rm_status_t st = check_range(p, wave, e0, e1);
@@ -842,6 +884,7 @@ rm_status_t rm_rmatrix(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double
 
 rm_status_t rm_kmatrix(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* K, int32_t* n_open,
                        uint8_t* flags, int32_t mem) {
+  Nvtx range("rm_kmatrix");
   try {
     Plan* p = as_plan(h);
     rm_status_t st = check_range(p, wave, e0, e1);
@@ -872,6 +915,7 @@ rm_status_t rm_kmatrix(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double
 
 rm_status_t rm_xsec(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* eigsum, double* sig_tot,
                     double* sig_sel, int32_t mem) {
+  Nvtx range("rm_xsec");
   try {
     Plan* p = as_plan(h);
     rm_status_t st = check_range(p, wave, e0, e1);
@@ -901,6 +945,7 @@ rm_status_t rm_xsec(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* e
 }
 
 rm_status_t rm_run(rm_plan_t h) {
+  Nvtx range("rm_run");
   try {
     Plan* p = as_plan(h);
     if (!p) return fail(RM_ERR_ARG, "null plan");
@@ -928,6 +973,7 @@ rm_status_t rm_run(rm_plan_t h) {
 
 rm_status_t rm_photo(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* sig_pi, double* sig_pi_ch,
                      int32_t mem) {
+  Nvtx range("rm_photo");
   try {
     Plan* p = as_plan(h);
     rm_status_t st = check_range(p, wave, e0, e1);
@@ -957,6 +1003,7 @@ rm_status_t rm_photo(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* 
 
 rm_status_t rm_results_photo(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* sig_pi,
                              double* sig_pi_ch, int32_t mem) {
+  Nvtx range("rm_results_photo");
   try {
     Plan* p = as_plan(h);
     rm_status_t st = check_range(p, wave, e0, e1);
@@ -985,6 +1032,7 @@ rm_status_t rm_results_photo(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, 
 
 rm_status_t rm_convolve(const double* energies, int64_t n_e, const double* sigma, int32_t n_series,
                         const double* weights, double fwhm, double* out, int32_t mem, void* cuda_stream) {
+  Nvtx range("rm_convolve");
   try {
     if (n_e < 0 || (n_e > 0 && (!energies || !sigma || !out)) || !valid_mem(mem))
       return fail(RM_ERR_ARG, "bad arguments");
@@ -1031,6 +1079,7 @@ rm_status_t rm_convolve(const double* energies, int64_t n_e, const double* sigma
 
 rm_status_t rm_results(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double* eigsum, double* sig_tot,
                        double* sig_sel, int32_t* n_open, uint8_t* flags, int32_t mem) {
+  Nvtx range("rm_results");
   try {
     Plan* p = as_plan(h);
     rm_status_t st = check_range(p, wave, e0, e1);
@@ -1062,6 +1111,7 @@ rm_status_t rm_results(rm_plan_t h, int32_t wave, int64_t e0, int64_t e1, double
 }
 
 rm_status_t rm_sync(rm_plan_t h) {
+  Nvtx range("rm_sync");
   Plan* p = as_plan(h);
   if (!p) return fail(RM_ERR_ARG, "null plan");
   RM_CUDA(cudaStreamSynchronize(p->stream), "rm_sync");
@@ -1091,6 +1141,13 @@ rm_status_t rm_plan_cluster(rm_plan_t h, int32_t* cx, int32_t* cy) {
   return RM_OK;
 }
 
+rm_status_t rm_plan_slices(rm_plan_t h, int32_t* products) {
+  Plan* p = as_plan(h);
+  if (!p || !products) return fail(RM_ERR_ARG, "null argument");
+  *products = (p->prec == RM_PREC_SPLIT_BF16 || p->prec == RM_PREC_SPLIT_FP16) ? p->slices : 0;
+  return RM_OK;
+}
+
 int64_t rm_plan_launches(rm_plan_t h) {
   Plan* p = as_plan(h);
   return p ? p->launches : -1;
@@ -1117,6 +1174,7 @@ rm_status_t rm_profile_read(rm_plan_t h, int32_t kernel, double* total_ms, int64
 }
 
 rm_status_t rm_plan_destroy(rm_plan_t h) {
+  Nvtx range("rm_plan_destroy");
   Plan* p = as_plan(h);
   if (!p) return RM_OK;
   cudaSetDevice(p->device);

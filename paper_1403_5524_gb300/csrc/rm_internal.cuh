@@ -122,7 +122,7 @@ struct Plan {
   int64_t n_e = 0;
   int prec = RM_PREC_FP64;
   double delta = 0.05;
-  int slices = 0;
+  int slices = 13;  // slice products per far term of the tensor-core pole sum: 3, 6, 10 or 13
   int n_sel = 1;
   int32_t sel[RM_MAX_SEL] = {0};
   int32_t* sel_dev = nullptr;
@@ -153,6 +153,9 @@ struct Plan {
   int64_t prof_n[RM_KERNEL_COUNT] = {0};
   GroupDev grp;
   bool autotuned = false;
+  // test hooks, read from the environment at plan creation (host-side fault injection):
+  // RM_FAULT_WAIT_CYCLES shortens every mbarrier wait of unclustered tensor-core launches
+  long long fault_wait = 0;
 };
 
 // ---------------------------------------------------------------------------

@@ -19,6 +19,7 @@ RM_OK, RM_ERR_ARG, RM_ERR_ORDER, RM_ERR_NOMEM, RM_ERR_CUDA, RM_ERR_TIMEOUT, RM_E
 RM_MEM_HOST, RM_MEM_DEVICE = 0, 1
 RM_PREC_FP64, RM_PREC_SPLIT_BF16, RM_PREC_SPLIT_FP16, RM_PREC_FP32_SIMT = 0, 1, 2, 3
 FLAG_NUDGED, FLAG_ILLCOND, FLAG_NO_OPEN, FLAG_SINGULAR, FLAG_ASYM, FLAG_FP64, FLAG_LU = 1, 2, 4, 8, 16, 32, 64
+FLAG_NEAR_THRESHOLD = 128
 SOLVE = {"fp64": 0, "mixed": 1, "fp64_lu": 2}
 
 PREC = {"fp64": RM_PREC_FP64, "split_bf16": RM_PREC_SPLIT_BF16, "split_fp16": RM_PREC_SPLIT_FP16,
@@ -27,7 +28,8 @@ PREC = {"fp64": RM_PREC_FP64, "split_bf16": RM_PREC_SPLIT_BF16, "split_fp16": RM
 EXPORTS = ["rm_options_default", "rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix",
            "rm_xsec", "rm_run", "rm_results", "rm_sync", "rm_plan_info", "rm_plan_launches",
            "rm_plan_destroy", "rm_status_str", "rm_last_error", "rm_profile_enable", "rm_profile_read",
-           "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve"]
+           "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve", "rm_plan_slices",
+           "rm_xsec_from_r_static", "rm_static_last_error", "rm_static_layout"]
 
 KERNELS = {"polesum_fp64": 0, "polesum_split": 1, "near": 2, "asym": 3, "solve": 4, "dslice": 5}
 
@@ -80,6 +82,11 @@ def load_library(path: str = LIB_PATH):
     lib.rm_photo.argtypes = [P, i32, i64, i64, P, P, i32]
     lib.rm_results_photo.argtypes = [P, i32, i64, i64, P, P, i32]
     lib.rm_convolve.argtypes = [P, i64, P, i32, P, dbl, P, i32, P]
+    lib.rm_plan_slices.argtypes = [P, C.POINTER(i32)]
+    lib.rm_xsec_from_r_static.argtypes = [P, i32, i32, dbl, P, P, P, P, i64, P, i32, P, P, P, P, P, P, P]
+    lib.rm_static_last_error.argtypes = []
+    lib.rm_static_last_error.restype = C.c_char_p
+    lib.rm_static_layout.argtypes = [i32, i32, C.POINTER(i32), C.POINTER(i32)]
     lib.rm_plan_launches.argtypes = [P]
     lib.rm_plan_launches.restype = i64
     lib.rm_plan_destroy.argtypes = [P]
@@ -91,7 +98,8 @@ def load_library(path: str = LIB_PATH):
     lib.rm_last_error.restype = C.c_char_p
     for name in ["rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix", "rm_xsec", "rm_run",
                  "rm_results", "rm_sync", "rm_plan_info", "rm_plan_destroy", "rm_profile_enable",
-                 "rm_profile_read", "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve"]:
+                 "rm_profile_read", "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve",
+                 "rm_plan_slices", "rm_xsec_from_r_static", "rm_static_layout"]:
         getattr(lib, name).restype = C.c_int32
     _lib = lib
     return lib
@@ -226,6 +234,12 @@ class Plan:
         cx, cy = C.c_int32(), C.c_int32()
         _check(self.lib.rm_plan_cluster(self.h, C.byref(cx), C.byref(cy)))
         return int(cx.value), int(cy.value)
+
+    def slices(self) -> int:
+        """Slice products per far term of the tensor-core pole sum (0 without one)."""
+        v = C.c_int32()
+        _check(self.lib.rm_plan_slices(self.h, C.byref(v)))
+        return int(v.value)
 
     def launches(self) -> int:
         return int(self.lib.rm_plan_launches(self.h))

@@ -89,6 +89,49 @@ def test_bad_arguments_rejected_before_device(lib):
     assert lib.rm_last_error()
 
 
+def test_slices_option_checked_on_host(lib):
+    # the product set of the tensor-core pole sum: 0 (default), 3, 6, 10 or 13, split modes only
+    wl = synth.small(1, 4, 20, 5)
+    o = rm.rm_options()
+    lib.rm_options_default(C.byref(o))
+    o.prec = rm.RM_PREC_SPLIT_BF16
+    for bad in (1, 2, 4, 5, 7, 12, 14, -1):
+        o.slices = bad
+        assert _create(lib, wl.waves, wl.energies, o)[0] == rm.RM_ERR_ARG, bad
+        assert b"slices" in lib.rm_last_error()
+    for prec in (rm.RM_PREC_FP64, rm.RM_PREC_FP32_SIMT):
+        o.prec, o.slices = prec, 6
+        assert _create(lib, wl.waves, wl.energies, o)[0] == rm.RM_ERR_ARG
+    v = C.c_int32(-7)
+    assert lib.rm_plan_slices(None, C.byref(v)) == rm.RM_ERR_ARG
+
+
+def test_static_entry_arguments_checked_on_host(lib):
+    # the allocation-free entry point rejects bad sizes and null pointers before any CUDA call
+    buf = np.zeros(64)
+    ib = np.zeros(8, np.int32)
+    d, i = buf.ctypes.data, ib.ctypes.data
+
+    def call(R=d, n=4, N=10, a=1.0, l=i, thr=d, poles=d, E=d, ne=3, sel=None, ns=1):
+        return lib.rm_xsec_from_r_static(R, n, N, a, l, thr, poles, E, ne, sel, ns,
+                                         None, None, None, None, None, None, None)
+    assert call(n=0) == rm.RM_ERR_ARG
+    assert call(N=0) == rm.RM_ERR_ARG
+    assert call(a=0.0) == rm.RM_ERR_ARG and call(a=float("nan")) == rm.RM_ERR_ARG
+    assert call(ne=-1) == rm.RM_ERR_ARG
+    assert call(ne=0) == rm.RM_OK  # nothing to do
+    for k in ("R", "l", "thr", "poles", "E"):
+        assert call(**{k: None}) == rm.RM_ERR_ARG, k
+        assert b"null" in lib.rm_static_last_error()
+    sel = np.array([0, -2], np.int32)
+    assert call(sel=sel.ctypes.data, ns=2) == rm.RM_ERR_ARG
+    assert call(sel=sel.ctypes.data, ns=0) == rm.RM_ERR_ARG
+    assert call(sel=sel.ctypes.data, ns=65) == rm.RM_ERR_ARG
+    c, sl = C.c_int32(), C.c_int32()
+    assert lib.rm_static_layout(0, 1, C.byref(c), C.byref(sl)) == rm.RM_ERR_ARG
+    assert lib.rm_static_layout(4, 0, C.byref(c), C.byref(sl)) == rm.RM_ERR_ARG
+
+
 def test_no_gpu_is_an_error_not_a_crash(lib):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
@@ -127,7 +170,8 @@ def test_binding_constants_match_the_header():
     txt = open(os.path.join(os.path.dirname(__file__), "..", "include", "rm.h")).read()
     defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (RM_\w+) (\d+)u?\b", txt)}
     flags = {"NUDGED": rm.FLAG_NUDGED, "ILLCOND": rm.FLAG_ILLCOND, "NO_OPEN": rm.FLAG_NO_OPEN,
-             "SINGULAR": rm.FLAG_SINGULAR, "ASYM": rm.FLAG_ASYM, "FP64": rm.FLAG_FP64, "LU": rm.FLAG_LU}
+             "SINGULAR": rm.FLAG_SINGULAR, "ASYM": rm.FLAG_ASYM, "FP64": rm.FLAG_FP64, "LU": rm.FLAG_LU,
+             "NEAR_THRESHOLD": rm.FLAG_NEAR_THRESHOLD}
     for k, v in flags.items():
         assert defs["RM_FLAG_" + k] == v, k
     kern = {"polesum_fp64": "POLESUM_FP64", "polesum_split": "POLESUM_SPLIT", "near": "NEAR", "asym": "ASYM",
@@ -135,6 +179,7 @@ def test_binding_constants_match_the_header():
     for k, v in rm.KERNELS.items():
         assert defs["RM_KERNEL_" + kern[k]] == v, k
     assert defs["RM_KERNEL_COUNT"] == len(rm.KERNELS)
+    assert defs["RM_DEFAULT_SLICES"] in (3, 6, 10, 13)
     enum = re.search(r"typedef enum \{([^}]*)\} rm_solve_precision_t;", txt).group(1)
     vals = {m.group(1): int(m.group(2)) for m in re.finditer(r"RM_SOLVE_(\w+) = (\d+)", enum)}
     assert vals == {"FP64": rm.SOLVE["fp64"], "MIXED": rm.SOLVE["mixed"], "FP64_LU": rm.SOLVE["fp64_lu"]}

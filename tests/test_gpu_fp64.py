@@ -108,6 +108,32 @@ def test_ragged_sizes(rm, n, N, ne):
     compare(wl, g, ref)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+def test_lmax15_zero_potential(rm, prec):
+    # angular momenta up to 15 (the n_ch = 512 workload's range) in the zero-potential outer
+    # region: open channels with x = k a < l take jhat_l from the downward (Miller) recurrence,
+    # x > l from the upward one; closed channels of high l their khat_l log-derivative.  Energies
+    # just above thresholds (x from 0.02 up), just below, and up to 6 Ry (x up to about 85).
+    rng = np.random.default_rng(1515)
+    l = np.array([0, 15, 8, 12, 3, 15, 9, 14, 1, 11, 10, 13, 2, 15, 7, 5], np.int32)
+    w = synth.make_wave(rng, l.size, 1500, thr_hi=2.0, pole_lo=-10.0, pole_hi=80.0, a=35.0, l_fixed=l)
+    E = list(np.linspace(0.01, 6.0, 40))
+    for t in w.thresh[1:]:
+        E += [t + 3e-7, t + (0.6 / w.a) ** 2, t + (4.0 / w.a) ** 2, t - 1e-4]
+    E = np.unique(np.array([e for e in E if e > 0.005]))
+    wl = synth.Workload("lmax15", [w], E, delta=0.05)
+    sel = (0, 1, 5)
+    g = gpu_sweep(rm, wl, sel=sel, prec=prec)
+    ref = orc.sweep(w, E, sel=sel)
+    if prec == "fp64":
+        compare(wl, g, ref)
+    else:
+        compare(wl, g, ref, tolK=1e-6, tolS=1e-8, checkR=False)
+        for t in range(E.size):
+            Rg, Ro = g["R"][t], ref["R"][t]
+            assert np.abs(Rg - Ro).max() <= 1e-6 * np.abs(Ro).max(), t
+
+
 def test_config2_sampled(rm):
     wl = synth.config(2)
     w = wl.waves[0]
