@@ -303,6 +303,16 @@ rm_status_t rm_profile_read(rm_plan_t plan, int32_t kernel, double* total_ms, in
 
 rm_status_t rm_plan_destroy(rm_plan_t plan);
 
+/* Bounds-checked build (librm_checked.so, compiled with -DRM_CHECKED): the kernels guard their
+   index arithmetic (output and workspace stores, staged tiles, per-energy ranges); a failing
+   guard skips the access and records the source line of the first failure per translation unit,
+   without trapping.  rm_checked_report waits for the device, returns the first recorded failure
+   (unit: 0 prep, 1 tensor-core pole sum / D slices / near window, 2 FP64 pole sum, 3 FP32 pole
+   sum, 4 asymptotic functions, 5 solve, 6 convolution, 7 allocation-free entry point; line: its
+   source line) or unit -1, line 0 when none, and clears the records.  In the normal library it
+   returns RM_ERR_STATE. */
+rm_status_t rm_checked_report(int32_t* unit, int32_t* line);
+
 const char* rm_status_str(rm_status_t s);
 const char* rm_last_error(void);
 

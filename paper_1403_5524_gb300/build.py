@@ -3,6 +3,9 @@
 ``librm.so``   the R-matrix library: every translation unit under ``csrc/``,
                compiled in parallel with nvcc (``-gencode arch=compute_103a,code=sm_103a``)
                and linked into a shared object next to this file.
+``librm_checked.so`` the same sources with ``-DRM_CHECKED``: every guarded index of the
+               kernels is checked and a violation recorded instead of performed
+               (``rm_checked_report``); the tests load it with ``RM_LIBRARY=checked``.
 ``libpeak.so`` the FP64 pipe peak probe (``probe/fp64_peak.cu``), the measured
                denominator of the FP64 rooflines the benchmark reports.
 
@@ -23,6 +26,7 @@ PROBE = os.path.join(HERE, "probe")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librm.so")
 PEAK_LIB = os.path.join(HERE, "libpeak.so")
+CHECKED_LIB = os.path.join(HERE, "librm_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -59,12 +63,13 @@ def _link(objs, out: str):
 
 def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    jobs = [(s, "", LIB) for s in sources()] + [(s, "probe_", PEAK_LIB) for s in sources(PROBE)]
+    jobs = ([(s, "", LIB, []) for s in sources()] + [(s, "chk_", CHECKED_LIB, ["-DRM_CHECKED"]) for s in sources()]
+            + [(s, "probe_", PEAK_LIB, []) for s in sources(PROBE)])
     # the longest translation units first, so the pool's tail is short
     jobs.sort(key=lambda j: -os.path.getsize(j[0]))
     with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda j: (j[2], _compile(j[0], list(extra), j[1])), jobs))
-    for lib in (LIB, PEAK_LIB):
+        objs = list(ex.map(lambda j: (j[2], _compile(j[0], list(extra) + j[3], j[1])), jobs))
+    for lib in (LIB, CHECKED_LIB, PEAK_LIB):
         _link([o for l, o in objs if l == lib], lib)
         if verbose:
             print("built", lib)

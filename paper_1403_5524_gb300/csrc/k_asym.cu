@@ -275,6 +275,7 @@ __global__ void asym_kernel(const int32_t* __restrict__ lch, const double* __res
   const int e = (int)(t / n), i = (int)(t % n);
   double lam, s, sp, c;
   if (!channel_data(lch[i], E[e] - thr[i], a, z, lam, s, sp, c)) flag_energy(flags, e, RM_FLAG_ASYM);
+  if (!RM_CHECK(t < ld)) return;  // the four blocks of the chunk buffer are ld apart
   out[0 * ld + t] = lam;
   out[1 * ld + t] = s;
   out[2 * ld + t] = sp;
@@ -303,6 +304,7 @@ __global__ void asym_grouped_kernel(const AsymWave* __restrict__ waves, int64_t 
   double lam, s, sp, c;
   if (!channel_data(w.l[i], w.E[e_begin + e] - w.thr[i], w.a, w.z, lam, s, sp, c))
     flag_energy(w.flags, e_begin + e, RM_FLAG_ASYM);
+  if (!RM_CHECK(t < ld)) return;
   w.out[0 * ld + t] = lam;
   w.out[1 * ld + t] = s;
   w.out[2 * ld + t] = sp;
@@ -341,5 +343,7 @@ cudaError_t launch_asym(const WaveDev& w, int64_t e0, int ne, double* asym, int 
                                                               asym, (int64_t)ld_chunk, w.flags0 + e0);
   return cudaGetLastError();
 }
+
+RM_CHECK_READER(asym)
 
 }  // namespace rm

@@ -52,6 +52,7 @@ __global__ void convolve_kernel(const double* __restrict__ E, int64_t n_e, const
                                                                    // vanishes next to x (then: no kernel)
   const double inv = 1.0 / sd;
   double num = 0.0, den = 0.0;
+  if (!RM_CHECK(lo >= 0 && hi <= n_e && lo <= hi)) return;
   for (int64_t q = lo; q < hi; ++q) {
     const double el = q > 0 ? E[q - 1] : E[q];
     const double er = q + 1 < n_e ? E[q + 1] : E[q];
@@ -78,5 +79,7 @@ cudaError_t launch_convolve(const double* E, int64_t n_e, const double* sigma, i
 }
 
 int convolve_max_series() { return CONV_MAX_SERIES; }
+
+RM_CHECK_READER(convolve)
 
 }  // namespace rm

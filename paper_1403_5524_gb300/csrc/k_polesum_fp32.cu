@@ -54,8 +54,9 @@ __global__ void __launch_bounds__(NT) polesum_fp32_kernel(
     {
       const int r = t / KS, k = t % KS;
       const int gi = bi * CB + r, gj = bj * CB + r;
-      Wi[r][k] = (gi < n) ? omega[(int64_t)(2 * gi) * Npad + k0 + k] : 0.0f;
-      Wj[r][k] = (gj < n) ? omega[(int64_t)(2 * gj) * Npad + k0 + k] : 0.0f;
+      const bool in_k = RM_CHECK(k0 + k < Npad);
+      Wi[r][k] = (gi < n && in_k) ? omega[(int64_t)(2 * gi) * Npad + k0 + k] : 0.0f;
+      Wj[r][k] = (gj < n && in_k) ? omega[(int64_t)(2 * gj) * Npad + k0 + k] : 0.0f;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(NT) polesum_fp32_kernel(
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int e = e0 + eg + 8 * s;
-      if (e < ne) R[(int64_t)e * np + p] = (double)acc[r][s] * f;
+      if (e < ne && RM_CHECK(p >= 0 && p < np)) R[(int64_t)e * np + p] = (double)acc[r][s] * f;
     }
   }
 }
@@ -115,5 +116,7 @@ cudaError_t launch_polesum_fp32(const WaveDev& w, int64_t e0, int ne, double* R,
                                           sd.khi + e0, sd.sigma, ne, 1.0 / (2.0 * w.a), R);
   return cudaGetLastError();
 }
+
+RM_CHECK_READER(polesum_fp32)
 
 }  // namespace rm

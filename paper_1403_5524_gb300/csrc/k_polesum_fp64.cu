@@ -51,8 +51,9 @@ __global__ void __launch_bounds__(NT) polesum_fp64_kernel(
     {
       const int r = t / KS, k = t % KS;  // 256 threads -> 16 x 16
       const int gi = bi * CB + r, gj = bj * CB + r;
-      Wi[r][k] = (gi < n) ? W[(int64_t)gi * Npad + k0 + k] : 0.0;
-      Wj[r][k] = (gj < n) ? W[(int64_t)gj * Npad + k0 + k] : 0.0;
+      const bool in_k = RM_CHECK(k0 + k < Npad);
+      Wi[r][k] = (gi < n && in_k) ? W[(int64_t)gi * Npad + k0 + k] : 0.0;
+      Wj[r][k] = (gj < n && in_k) ? W[(int64_t)gj * Npad + k0 + k] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(NT) polesum_fp64_kernel(
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const int e = e0 + eg + 8 * s;
-      if (e < ne) R[(int64_t)e * np + p] = acc[r][s] * inv2a;
+      if (e < ne && RM_CHECK(p >= 0 && p < np)) R[(int64_t)e * np + p] = acc[r][s] * inv2a;
     }
   }
 }
@@ -109,5 +110,7 @@ cudaError_t launch_polesum_fp64(const WaveDev& w, int64_t e0, int ne, double* R,
                                           1.0 / (2.0 * w.a), R);
   return cudaGetLastError();
 }
+
+RM_CHECK_READER(polesum_fp64)
 
 }  // namespace rm

@@ -417,9 +417,15 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
     // swizzled slice offsets of this thread's elements, the same in every k-step
     uint32_t offA[TA], offB[TB];
 #pragma unroll
-    for (int t = 0; t < TA; ++t) offA[t] = swz(ai * 16 + jbase + 2 * t, 2 * kpa);
+    for (int t = 0; t < TA; ++t) {
+      offA[t] = swz(ai * 16 + jbase + 2 * t, 2 * kpa);
+      if (!RM_CHECK(offA[t] + 4 <= (uint32_t)SLICE_BYTES)) offA[t] = 0;
+    }
 #pragma unroll
-    for (int t = 0; t < TB; ++t) offB[t] = swz(rb, 2 * (kpb + 4 * (kq0 + t)));
+    for (int t = 0; t < TB; ++t) {
+      offB[t] = swz(rb, 2 * (kpb + 4 * (kq0 + t)));
+      if (!RM_CHECK(offB[t] + 4 <= (uint32_t)SLICE_BYTES)) offB[t] = 0;
+    }
     const uint32_t trow = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(32 * (w >> 2));
     float Vh[32], Vl[32];  // running sums of this thread's 32 accumulator cells
 #pragma unroll
@@ -556,7 +562,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int e = n0 + 32 * (w >> 2) + c;
-          if (e < g.ne) g.R[(int64_t)e * np + p] = ((double)Vh[c] + (double)Vl[c]) * fp * g.tau[g.e_begin + e];
+          if (e < g.ne && RM_CHECK(p >= 0 && p < np))
+            g.R[(int64_t)e * np + p] = ((double)Vh[c] + (double)Vl[c]) * fp * g.tau[g.e_begin + e];
         }
       }
     }
@@ -760,6 +767,7 @@ __global__ void __launch_bounds__(256) dslice_grouped_kernel(const DSliceWave* _
   const int np2 = w.Npad >> 1;
   const int64_t plane = (int64_t)w.rows * np2;
   uint32_t* row = w.D + (int64_t)e * np2;
+  if (!RM_CHECK(np2 * 2 == w.Npad && w.N <= w.Npad)) return;
   for (int kp = threadIdx.x; kp < np2; kp += blockDim.x) {
     const int k = 2 * kp;
     const float2 ph = *reinterpret_cast<const float2*>(w.pol + k);
@@ -806,7 +814,7 @@ __device__ __forceinline__ void near_block(const double* __restrict__ W, int n, 
     const int ng = (min(NKP, Khi - Ks) + 7) >> 3;
     for (int idx = t; idx < n * NKP; idx += NNT) {
       const int i = idx / NKP, kk = idx % NKP;
-      Ws[i * (NKP + 1) + kk] = (Ks + kk < Khi) ? W[(int64_t)i * Npad + Ks + kk] : 0.0;
+      Ws[i * (NKP + 1) + kk] = (Ks + kk < Khi && RM_CHECK(Ks + kk < Npad)) ? W[(int64_t)i * Npad + Ks + kk] : 0.0;
     }
     for (int idx = t; idx < NEB * NKP; idx += NNT) {
       const int e = idx / NKP, kk = idx % NKP;
@@ -844,7 +852,7 @@ __device__ __forceinline__ void near_block(const double* __restrict__ W, int n, 
 #pragma unroll
               for (int q = 0; q < 8; ++q) acc = fma(P[8 * g8 + q], Dm[e * NKP + 8 * g8 + q], acc);
             }
-          R[(int64_t)(e0 + e) * np + p] += acc;
+          if (RM_CHECK(e0 + e < ne && p < np)) R[(int64_t)(e0 + e) * np + p] += acc;
         }
         j += NNT;
         while (j >= n && i < n - 1) {
@@ -1194,5 +1202,7 @@ cudaError_t launch_dslice_grouped(const Plan& p, int64_t e0, int ne, cudaStream_
                                                                ne);
   return cudaGetLastError();
 }
+
+RM_CHECK_READER(polesum_tc)
 
 }  // namespace rm

@@ -14,7 +14,7 @@ __global__ void validate_kernel(const int32_t* __restrict__ l, const double* __r
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nW * N; t += stride) {
     const int i = (int)(t / N), k = (int)(t % N);
-    if (!isfinite(W[(int64_t)i * Npad + k])) set_err(err, RM_ERR_ARG);
+    if (RM_CHECK(k < Npad) && !isfinite(W[(int64_t)i * Npad + k])) set_err(err, RM_ERR_ARG);
   }
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += stride) {
     const double p = poles[t];
@@ -50,6 +50,7 @@ __global__ void prep_kernel(const double* __restrict__ energies, int64_t n_e,
                             uint8_t* __restrict__ flags0, int32_t* __restrict__ n_open) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_e) return;
+  if (!RM_CHECK(N >= 1 && n >= 1)) return;
   double E = energies[e];
   double dmin = INFINITY, dthr = INFINITY;
   int k = lower_bound(poles, N, E);
@@ -86,5 +87,7 @@ cudaError_t launch_prep(const WaveDev& w, const double* energies, int64_t n_e, c
                                            w.flags0, w.n_open);
   return cudaGetLastError();
 }
+
+RM_CHECK_READER(prep)
 
 }  // namespace rm

@@ -918,6 +918,7 @@ struct SolveArgs {
   int64_t slot_doubles;
   int ldR;  // leading dimension of the real augmented matrix
   int ldC;  // leading dimension (complex elements) of the S-step matrix
+  int n_slots;  // solve workspaces: one per CTA of the launch
   SolveOut out;
 };
 
@@ -1142,7 +1143,7 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
       const int j = n - 1 - q;
       double v = Rrow[j - i];
       if (q == p && i >= no) v -= 1.0 / (g.a * lam[i]);
-      A[(int64_t)p * ld + q] = v;
+      if (RM_CHECK(q < ld && pair_index(n, i, j) < g.npR - g.roff)) A[(int64_t)p * ld + q] = v;
       gm = fmax(gm, fabs(v));
     }
   }
@@ -1177,7 +1178,7 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
     } else {
       v = cplx{A[(int64_t)(n - 1 - i) * ld + n], 0.0};
     }
-    C[(int64_t)i * g.ldC + j] = v;
+    if (RM_CHECK(j < g.ldC)) C[(int64_t)i * g.ldC + j] = v;
   }
   __syncthreads();
   // ------------------------------------- S'' = V G V - diag(c c' / (a |h'|^2)), in place, and its inertia
@@ -1303,6 +1304,11 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
   double* A = g.slot + (int64_t)blockIdx.x * g.slot_doubles;
   cplx* C = reinterpret_cast<cplx*>(A + (int64_t)n * g.ldR);
   const int t = threadIdx.x;
+  // this CTA's workspace and energy (uniform over the block): the real n x ldR matrix and the
+  // complex n x ldC one must fit the slot, the energy must lie in the launch's range
+  if (!RM_CHECK((int)blockIdx.x < g.n_slots && e >= 0 && e < g.ne && n <= g.ldR / 2 &&
+                (int64_t)n * g.ldR + 2 * (int64_t)n * g.ldC <= g.slot_doubles))
+    return;
 
   const int no = g.n_open_in[e];
   uint8_t fl = g.flags_in[e];
@@ -1367,7 +1373,7 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
       const double rim = Re[pair_index(n, min(i, mo), max(i, mo))];
       v = -(((i == mo) ? s[mo] : 0.0) - g.a * rim * sp[mo]);
     }
-    A[(int64_t)i * g.ldR + j] = v;
+    if (RM_CHECK(j < g.ldR)) A[(int64_t)i * g.ldR + j] = v;
   }
   __syncthreads();
   LUStat st;
@@ -1475,7 +1481,7 @@ __device__ void solve_energy(const SolveArgs& g, int e, unsigned char* smem_raw,
     } else {
       v = cplx{MK[i], 0.0};
     }
-    C[(int64_t)i * g.ldC + j] = v;
+    if (RM_CHECK(j < g.ldC)) C[(int64_t)i * g.ldC + j] = v;
   }
   __syncthreads();
   ldl_solve<cplx>(C, no, mc, g.ldC, panel_c, tile_c, tmp_c, tri_c, st);
@@ -1661,6 +1667,7 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   g.slot_doubles = p.slot_doubles;
   g.ldR = 2 * p.n_max;
   g.ldC = p.n_max + p.n_sel + 1;  // + the dipole right-hand side
+  g.n_slots = p.solve_slots;
   g.out = out;
   const size_t smem = solve_smem_bytes(p.n_max);
   auto kern = p.solve_mixed ? solve_kernel<true, 2> : (p.solve_bps >= 3 ? solve_kernel<false, 3> : solve_kernel<false, 2>);
@@ -1700,6 +1707,7 @@ cudaError_t group_setup_solve(Plan& p) {
     a.slot_doubles = p.slot_doubles;
     a.ldR = 2 * p.n_max;
     a.ldC = p.n_max + p.n_sel + 1;
+    a.n_slots = p.solve_slots;
     a.out = SolveOut();
     a.out.eta = w.eta;
     a.out.sig_tot = w.sig_tot;
@@ -1758,5 +1766,7 @@ cudaError_t launch_solve_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t
       reinterpret_cast<const SolveArgs*>(G.solve_waves), G.units, G.n_units, e0, ne, G.counter);
   return cudaGetLastError();
 }
+
+RM_CHECK_READER(solve)
 
 }  // namespace rm

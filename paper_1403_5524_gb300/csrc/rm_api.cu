@@ -1173,6 +1173,33 @@ rm_status_t rm_profile_read(rm_plan_t h, int32_t kernel, double* total_ms, int64
   return RM_OK;
 }
 
+rm_status_t rm_checked_report(int32_t* unit, int32_t* line) {
+  if (unit) *unit = -1;
+  if (line) *line = 0;
+#ifdef RM_CHECKED
+  int (*readers[])(bool) = {check_line_prep, check_line_polesum_tc, check_line_polesum_fp64,
+                            check_line_polesum_fp32, check_line_asym, check_line_solve,
+                            check_line_convolve, check_line_static};
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RM_ERR_CUDA, "rm_checked_report: device synchronisation failed");
+  }
+  bool found = false;
+  for (int u = 0; u < (int)(sizeof(readers) / sizeof(readers[0])); ++u) {
+    const int v = readers[u](true);
+    if (v < 0) return fail(RM_ERR_CUDA, "rm_checked_report: cannot read a check word");
+    if (v > 0 && !found) {
+      found = true;
+      if (unit) *unit = u;
+      if (line) *line = v;
+    }
+  }
+  return RM_OK;
+#else
+  return fail(RM_ERR_STATE, "library built without RM_CHECKED");
+#endif
+}
+
 rm_status_t rm_plan_destroy(rm_plan_t h) {
   Nvtx range("rm_plan_destroy");
   Plan* p = as_plan(h);

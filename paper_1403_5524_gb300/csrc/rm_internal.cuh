@@ -13,6 +13,49 @@
 namespace rm {
 
 // ---------------------------------------------------------------------------
+// bounds-checked build
+// ---------------------------------------------------------------------------
+// Built with -DRM_CHECKED (librm_checked.so), RM_CHECK(cond) guards a global or shared memory
+// access in the kernels: a false condition skips the access and records the source line of the
+// first failure in this translation unit's device word (no trap, the kernel carries on);
+// RM_CHECK_READER(unit) defines the host function that reads and clears that word, and
+// rm_checked_report() collects them.  In the normal build RM_CHECK(cond) is `true` and costs
+// nothing.
+#ifdef RM_CHECKED
+static __device__ int g_rm_check_line;
+__device__ __forceinline__ bool rm_check(bool ok, int line) {
+  if (!ok) atomicCAS(&g_rm_check_line, 0, line);
+  return ok;
+}
+#define RM_CHECK(cond) (::rm::rm_check((cond), __LINE__))
+#define RM_CHECK_READER(unit)                                            \
+  int check_line_##unit(bool reset) {                                    \
+    int v = 0;                                                           \
+    if (cudaMemcpyFromSymbol(&v, g_rm_check_line, sizeof(int)) != cudaSuccess) { \
+      cudaGetLastError();                                                \
+      return -1;                                                         \
+    }                                                                    \
+    if (reset) {                                                         \
+      const int z = 0;                                                   \
+      cudaMemcpyToSymbol(g_rm_check_line, &z, sizeof(int));              \
+    }                                                                    \
+    return v;                                                            \
+  }
+#else
+#define RM_CHECK(cond) true
+#define RM_CHECK_READER(unit)
+#endif
+// one reader per translation unit with kernels (checked build only)
+int check_line_prep(bool reset);
+int check_line_polesum_tc(bool reset);
+int check_line_polesum_fp64(bool reset);
+int check_line_polesum_fp32(bool reset);
+int check_line_asym(bool reset);
+int check_line_solve(bool reset);
+int check_line_convolve(bool reset);
+int check_line_static(bool reset);
+
+// ---------------------------------------------------------------------------
 // device-side helpers
 // ---------------------------------------------------------------------------
 struct cplx {

@@ -144,7 +144,16 @@ __global__ void static_flag_kernel(uint8_t* __restrict__ fl0, int ne, const int3
   if (e < ne && *bad) fl0[e] |= RM_FLAG_ASYM;
 }
 
+// the scratch carving must end inside the array (checked build)
+__global__ void static_extent_kernel(const unsigned char* end) {
+  RM_CHECK(end <= g_static_scratch + kScratchBytes);
+}
+
 }  // namespace
+
+namespace rm {
+RM_CHECK_READER(static)
+}  // namespace rm
 
 extern "C" rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_ch, int32_t n_poles, double a,
                                              const int32_t* l, const double* thresh, const double* pole_E,
@@ -201,6 +210,10 @@ extern "C" rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_c
   double* asym = reinterpret_cast<double*>(cur);
   cur += align256(sizeof(double) * 4 * (size_t)chunk * n);
   double* slot = reinterpret_cast<double*>(cur);
+#ifdef RM_CHECKED
+  static_extent_kernel<<<1, 1, 0, reinterpret_cast<cudaStream_t>(cuda_stream)>>>(
+      reinterpret_cast<unsigned char*>(slot + (int64_t)L.slots * L.slot_d));
+#endif
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   static_setup_kernel<<<1, 256, 0, s>>>(sel, n_sel, sel_dev, l, n, l_dev, bad);

@@ -13,7 +13,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librm.so")
+# RM_LIBRARY=checked selects the bounds-checked build (librm_checked.so)
+LIB_PATH = os.path.join(_HERE, "librm_checked.so" if os.environ.get("RM_LIBRARY") == "checked" else "librm.so")
 
 RM_OK, RM_ERR_ARG, RM_ERR_ORDER, RM_ERR_NOMEM, RM_ERR_CUDA, RM_ERR_TIMEOUT, RM_ERR_STATE = range(7)
 RM_MEM_HOST, RM_MEM_DEVICE = 0, 1
@@ -29,7 +30,7 @@ EXPORTS = ["rm_options_default", "rm_plan_create", "rm_plan_load", "rm_rmatrix",
            "rm_xsec", "rm_run", "rm_results", "rm_sync", "rm_plan_info", "rm_plan_launches",
            "rm_plan_destroy", "rm_status_str", "rm_last_error", "rm_profile_enable", "rm_profile_read",
            "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve", "rm_plan_slices",
-           "rm_xsec_from_r_static", "rm_static_last_error", "rm_static_layout"]
+           "rm_xsec_from_r_static", "rm_static_last_error", "rm_static_layout", "rm_checked_report"]
 
 KERNELS = {"polesum_fp64": 0, "polesum_split": 1, "near": 2, "asym": 3, "solve": 4, "dslice": 5}
 
@@ -87,6 +88,7 @@ def load_library(path: str = LIB_PATH):
     lib.rm_static_last_error.argtypes = []
     lib.rm_static_last_error.restype = C.c_char_p
     lib.rm_static_layout.argtypes = [i32, i32, C.POINTER(i32), C.POINTER(i32)]
+    lib.rm_checked_report.argtypes = [C.POINTER(i32), C.POINTER(i32)]
     lib.rm_plan_launches.argtypes = [P]
     lib.rm_plan_launches.restype = i64
     lib.rm_plan_destroy.argtypes = [P]
@@ -99,7 +101,7 @@ def load_library(path: str = LIB_PATH):
     for name in ["rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix", "rm_xsec", "rm_run",
                  "rm_results", "rm_sync", "rm_plan_info", "rm_plan_destroy", "rm_profile_enable",
                  "rm_profile_read", "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve",
-                 "rm_plan_slices", "rm_xsec_from_r_static", "rm_static_layout"]:
+                 "rm_plan_slices", "rm_xsec_from_r_static", "rm_static_layout", "rm_checked_report"]:
         getattr(lib, name).restype = C.c_int32
     _lib = lib
     return lib

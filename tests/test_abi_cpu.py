@@ -132,6 +132,20 @@ def test_static_entry_arguments_checked_on_host(lib):
     assert lib.rm_static_layout(4, 0, C.byref(c), C.byref(sl)) == rm.RM_ERR_ARG
 
 
+def test_checked_build_exports_and_normal_build_reports_state(lib):
+    # the normal library has no bounds checks to report; the checked build (built beside it by
+    # paper_1403_5524_gb300.build) loads and exports every declared function too
+    u, l = C.c_int32(7), C.c_int32(7)
+    assert lib.rm_checked_report(C.byref(u), C.byref(l)) == rm.RM_ERR_STATE
+    assert u.value == -1 and l.value == 0
+    path = os.path.join(ROOT, "paper_1403_5524_gb300", "librm_checked.so")
+    if not os.path.exists(path):
+        pytest.skip("checked library not built")
+    chk = C.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(chk, n), n
+
+
 def test_no_gpu_is_an_error_not_a_crash(lib):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
