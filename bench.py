@@ -35,7 +35,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU; the measured 
 # N=20000 wave, 1000-energy launch; scaled to a launch by its energies.  Kernels changed since
 # their capture have no entry (traffic null).
 DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.278e6}
-PRODUCT_SETS = (3, 6, 10, 13)
+PRODUCT_SETS = (3, 6, 10, 13, 15)
 
 
 def measured_peaks():
@@ -99,7 +99,7 @@ def parse():
     ap.add_argument("--slices", type=int, default=0, choices=(0,) + PRODUCT_SETS,
                     help="slice products per far term of the tensor-core pole sum (0: the library default)")
     ap.add_argument("--slices-study", action="store_true",
-                    help="accuracy and energies/s of every product set (3, 6, 10, 13) on this workload")
+                    help="accuracy and energies/s of every product set (3, 6, 10, 13, 15) on this workload")
     ap.add_argument("--accuracy-energies", type=int, default=64,
                     help="evenly spaced mesh energies checked against the oracle (plus near-threshold and "
                          "near-pole energies)")

@@ -151,12 +151,16 @@ typedef struct {
   int32_t prec;            /* rm_precision_t */
   double delta;            /* near-pole window half width (Ry) for split modes; > 0 */
   int32_t slices;          /* SPLIT_BF16 / SPLIT_FP16: slice products per far term P_pk D_ke.  Both
-                              operands are cut into up to four 8-bit slices q_0..q_3, r_0..r_3
-                              (orders of 2^-8); the product sums q_u r_v over
+                              operands are cut into up to five 8-bit slices q_0..q_4, r_0..r_4
+                              (orders of 2^-8; the last slice of a set is rounded); the product
+                              sums q_u r_v over
                                 3:  u + v <= 1 (two slices each),
                                 6:  u + v <= 2 (three slices each),
                                 10: u + v <= 3 (four slices each),
-                                13: u + v <= 3 and (1,3), (2,2), (3,1).
+                                13: u + v <= 3 and (1,3), (2,2), (3,1),
+                                15: u + v <= 4 (five slices each; SPLIT_BF16 only, two pipeline
+                                    stages instead of three).
+                              Relative error of one term about 2^-16, 2^-23, 2^-31, 2^-32, 2^-40.
                               0 = RM_DEFAULT_SLICES.  Fewer products are faster and less
                               accurate; other precisions take 0 only (else RM_ERR_ARG). */
   const int32_t* sel_init; /* host array of selected initial channels; NULL = {0} */
@@ -278,8 +282,8 @@ rm_status_t rm_plan_info(rm_plan_t plan, int32_t wave, int32_t* n_ch, int32_t* n
 /* Cluster shape of rm_run's tensor-core pole-sum launch (1 x 1 outside split modes). */
 rm_status_t rm_plan_cluster(rm_plan_t plan, int32_t* cluster_x, int32_t* cluster_y);
 
-/* Slice products per far term of the plan's tensor-core pole sum (3, 6, 10 or 13; 0 when the
-   plan's precision has no tensor-core pole sum). */
+/* Slice products per far term of the plan's tensor-core pole sum (3, 6, 10, 13 or 15; 0 when
+   the plan's precision has no tensor-core pole sum). */
 rm_status_t rm_plan_slices(rm_plan_t plan, int32_t* products);
 
 /* Number of kernel launches this plan has issued since creation. */

@@ -42,20 +42,29 @@ namespace {
 constexpr int BM = 128;                 // pairs per tile: 8 i-channels x 16 j-channels
 constexpr int BN = 128;                 // energies per tile
 constexpr int KS = 32;                  // poles per k-step (64-byte BF16 rows)
-constexpr int STAGES = 3;
 constexpr int NWORK = 16;               // producer / drain warps
 constexpr int NTHREADS = (NWORK + 2) * 32;  // + MMA issue warp + cluster copy warp
 constexpr int DRAIN_KSTEPS = 64;        // drain every 2048 poles
 constexpr int SLICE_BYTES = BM * KS * 2;          // 8 KB: 128 rows x 64 B
-constexpr int A_BYTES = 4 * SLICE_BYTES;          // 4 slices of P
-constexpr int B_BYTES = 4 * SLICE_BYTES;          // 4 slices of D
 constexpr int WI_FLOATS = 16 * KS;   // 8 channels x (hi, lo) rows
 constexpr int WJ_FLOATS = 32 * KS;   // 16 channels x (hi, lo) rows
 constexpr int PO_FLOATS = 2 * KS;    // poles hi row, lo row
 constexpr int TX_BYTES = (WI_FLOATS + WJ_FLOATS + PO_FLOATS) * 4;  // 6400
-constexpr int STAGE_STRIDE = ((A_BYTES + B_BYTES + TX_BYTES + 1023) / 1024) * 1024;
-constexpr int NBARS = 5 * STAGES + 3;
-constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_STRIDE + 1024 + NBARS * 8 + 16;
+// Shared-memory geometry for NS slices per operand: a stage holds NS slices of P (A), NS of D
+// (B) and the staged W rows and poles.  Four slices fit three stages in the 227 KB of a CTA, five
+// only two.
+template <int NS>
+struct TcGeo {
+  static constexpr int A_BYTES = NS * SLICE_BYTES;
+  static constexpr int B_BYTES = NS * SLICE_BYTES;
+  static constexpr int STAGES = NS == 5 ? 2 : 3;
+  static constexpr int STAGE_STRIDE = ((A_BYTES + B_BYTES + TX_BYTES + 1023) / 1024) * 1024;
+  static constexpr int NBARS = 5 * STAGES + 3;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_STRIDE + 1024 + NBARS * 8 + 16;
+};
+static_assert(TcGeo<4>::SMEM <= 232448 && TcGeo<5>::SMEM <= 232448, "a CTA's shared memory");
+// slices per operand of a product set: 3 products use two, 6 three, 10 and 13 four, 15 five
+__host__ __device__ constexpr int slices_of(int nprod) { return nprod == 3 ? 2 : (nprod == 6 ? 3 : (nprod == 15 ? 5 : 4)); }
 constexpr long long WAIT_BUDGET = 4000000000LL;   // clock cycles (~2 s) per mbarrier wait
 
 static_assert(BM == 128 && BN == 128, "TMEM layout assumes 128 x 128 tiles");
@@ -108,6 +117,24 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// x = xh + xl (double-float, |x| <= 256) -> five slices: the nearest integer, then multiples of
+// 2^-8, 2^-16 and 2^-24, then the rest.  s0..s3 hold at most 8 significant bits each and are
+// exact in BF16; s4 (|s4| <= 2^-25) is rounded to BF16 when packed (error 2^-34, 2^-42 of the
+// scale).  The remainder after s1 is carried as an exact double-float (TwoSum), so that the
+// 2^-24 slice is not limited by the rounding of one FP32 addition.
+__device__ __forceinline__ void slice5(float xh, float xl, float (&s)[5]) {
+  const float h0 = __fsub_rn(__fadd_rn(xh, 12582912.0f), 12582912.0f);  // nearest integer
+  const float h1 = __fsub_rn(__fadd_rn(xh, 49152.0f), 49152.0f);        // nearest multiple of 2^-8
+  s[0] = h0;
+  s[1] = __fsub_rn(h1, h0);
+  float rh, rl;
+  two_sum(__fsub_rn(xh, h1), xl, rh, rl);                                // rh + rl = x - h1 exactly
+  s[2] = __fsub_rn(__fadd_rn(rh, 192.0f), 192.0f);                       // nearest multiple of 2^-16
+  const float r2 = __fadd_rn(__fsub_rn(rh, s[2]), rl);                   // |r2| <= 2^-17
+  s[3] = __fsub_rn(__fadd_rn(r2, 0.75f), 0.75f);                         // nearest multiple of 2^-24
+  s[4] = __fsub_rn(r2, s[3]);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
@@ -139,6 +166,19 @@ __device__ __forceinline__ void d_pack(float ph0, float pl0, float ph1, float pl
   slice4(__fmul_rn(rh1, m1), __fmul_rn(rl1, m1), s1);
 #pragma unroll
   for (int v = 0; v < 4; ++v) w[v] = pack_slice(s0[v], s1[v], f16);
+}
+
+// As d_pack with five BF16 slices (the 15-product set).
+__device__ __forceinline__ void d_pack5(float ph0, float pl0, float ph1, float pl1, float eh, float el, float m0,
+                                        float m1, uint32_t (&w)[5]) {
+  float rh0, rl0, rh1, rl1;
+  df_recip_diff(ph0, pl0, eh, el, rh0, rl0);
+  df_recip_diff(ph1, pl1, eh, el, rh1, rl1);
+  float s0[5], s1[5];
+  slice5(__fmul_rn(rh0, m0), __fmul_rn(rl0, m0), s0);
+  slice5(__fmul_rn(rh1, m1), __fmul_rn(rl1, m1), s1);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) w[v] = pack_bf16x2(s0[v], s1[v]);
 }
 
 struct TCArgs {
@@ -183,11 +223,20 @@ struct TCArgs {
 // poles x 128 energies x 4 slices) per k-step, issued by one producer thread
 // once the stage is empty and completing on dfull; the producers form only P,
 // and clusters share P alone (CX = 1).
-template <int CX, int CY, bool DT>
+//
+// NS: slices per operand the tile's shared memory holds (4: the 3-, 6-, 10- and 13-product sets,
+// three stages; 5: the 15-product set, two stages).
+template <int CX, int CY, bool DT, int NS>
 __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUtensorMap* map_pol,
                                         const CUtensorMap* map_d, const TCArgs& g, int I0, int J0, int n0,
                                         unsigned char* smem_raw) {
   using namespace ptx;
+  static_assert(NS == 4 || NS == 5, "four or five slices per operand");
+  constexpr int STAGES = TcGeo<NS>::STAGES;
+  constexpr int A_BYTES = TcGeo<NS>::A_BYTES;
+  constexpr int B_BYTES = TcGeo<NS>::B_BYTES;
+  constexpr int STAGE_STRIDE = TcGeo<NS>::STAGE_STRIDE;
+  constexpr int NBARS = TcGeo<NS>::NBARS;
   constexpr int CL = CX * CY;
   static_assert(!DT || CX == 1, "TMA-staged D slices are not shared across the cluster");
   static_assert(CX == 1 || CX == 2 || CX == 4, "CX in {1, 2, 4}");
@@ -294,7 +343,19 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           // q_u x [r_v | r_v+1] writes orders u+v and u+v+1 at once.  The first product into
           // each used accumulator of a drain period starts it (f = 0).
           mma_bf16_ss(tmem + 0, A(0), B(0), idN256, f);  // (0,0) (0,1)
-          if (nprod == 3) {
+          if constexpr (NS == 5) {
+            // all 15 products with u + v <= 4; order 4 shares the order-3 accumulator
+            mma_bf16_ss(tmem + 256, A(0), B(2), idN256, f);   // (0,2) (0,3)
+            mma_bf16_ss(tmem + 384, A(0), B(4), idN128, 1u);  // (0,4)
+            mma_bf16_ss(tmem + 128, A(1), B(0), idN256, 1u);  // (1,0) (1,1)
+            mma_bf16_ss(tmem + 384, A(1), B(2), idN128, 1u);  // (1,2)
+            mma_bf16_ss(tmem + 384, A(1), B(3), idN128, 1u);  // (1,3)
+            mma_bf16_ss(tmem + 256, A(2), B(0), idN256, 1u);  // (2,0) (2,1)
+            mma_bf16_ss(tmem + 384, A(2), B(2), idN128, 1u);  // (2,2)
+            mma_bf16_ss(tmem + 384, A(3), B(0), idN128, 1u);  // (3,0)
+            mma_bf16_ss(tmem + 384, A(3), B(1), idN128, 1u);  // (3,1)
+            mma_bf16_ss(tmem + 384, A(4), B(0), idN128, 1u);  // (4,0)
+          } else if (nprod == 3) {
             mma_bf16_ss(tmem + 128, A(1), B(0), idN128, 1u);  // (1,0)
           } else if (nprod == 6) {
             mma_bf16_ss(tmem + 256, A(0), B(2), idN128, f);   // (0,2)
@@ -347,7 +408,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
     // ------------------------------------- cluster copies (1 thread; CL > 1 only)
     if (CL > 1 && lane == 0) {
       constexpr uint32_t ABLK = SLICE_BYTES / CY, BBLK = SLICE_BYTES / CX;
-      constexpr uint32_t IN_BYTES = (DT ? 0u : (CX - 1) * 4 * BBLK) + (CY - 1) * 4 * ABLK;
+      constexpr uint32_t IN_BYTES = (DT ? 0u : (CX - 1) * NS * BBLK) + (CY - 1) * NS * ABLK;
       const uint32_t sbase = smem_u32(smem);
       for (int j = 0; j < nK; ++j) {
         const int s = j % STAGES;
@@ -360,7 +421,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           const uint32_t peer = (uint32_t)(q + CX * ry);
           const uint32_t bar = mapa(smem_u32(full + s), peer);
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
+          for (int v = 0; v < NS; ++v) {
             const uint32_t src = st + A_BYTES + v * SLICE_BYTES + rx * BBLK;
             bulk_copy_to_peer(mapa(src, peer), src, BBLK, bar);
           }
@@ -371,7 +432,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           const uint32_t peer = (uint32_t)(rx + CX * q);
           const uint32_t bar = mapa(smem_u32(full + s), peer);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < NS; ++u) {
             const uint32_t src = st + u * SLICE_BYTES + ry * ABLK;
             bulk_copy_to_peer(mapa(src, peer), src, ABLK, bar);
           }
@@ -384,8 +445,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
     const int w = warp;
     const bool f16 = g.f16 != 0;
     // slices per operand and accumulator orders the product set uses
-    const int nsl = g.nprod == 3 ? 2 : (g.nprod == 6 ? 3 : 4);
-    const int nord = nsl;
+    const int nsl = NS == 5 ? 5 : slices_of(g.nprod);
+    const int nord = nsl < 4 ? nsl : 4;  // order 4 shares the order-3 accumulator
     // A role (pair rows of i-blocks ry*8/CY .. +8/CY): i-row ai, j-rows
     // jj = jbase + 2t, k-pair kpa; a half-warp writes one full slice row.
     constexpr int TA = 4 / CY;   // j-rows per thread
@@ -474,12 +535,21 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         float ph0, pl0, ph1, pl1;
         df_mul(wih.x, wil.x, wjh.x, wjl.x, ph0, pl0);
         df_mul(wih.y, wil.y, wjh.y, wjl.y, ph1, pl1);
-        float s0[4], s1[4];
-        slice4(__fmul_rn(ph0, mp[t]), __fmul_rn(pl0, mp[t]), s0);
-        slice4(__fmul_rn(ph1, mp[t]), __fmul_rn(pl1, mp[t]), s1);
+        if constexpr (NS == 5) {
+          float s0[5], s1[5];
+          slice5(__fmul_rn(ph0, mp[t]), __fmul_rn(pl0, mp[t]), s0);
+          slice5(__fmul_rn(ph1, mp[t]), __fmul_rn(pl1, mp[t]), s1);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (u < nsl) *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + offA[t]) = pack_slice(s0[u], s1[u], f16);
+          for (int u = 0; u < 5; ++u)
+            *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + offA[t]) = pack_bf16x2(s0[u], s1[u]);
+        } else {
+          float s0[4], s1[4];
+          slice4(__fmul_rn(ph0, mp[t]), __fmul_rn(pl0, mp[t]), s0);
+          slice4(__fmul_rn(ph1, mp[t]), __fmul_rn(pl1, mp[t]), s1);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (u < nsl) *reinterpret_cast<uint32_t*>(Ab + u * SLICE_BYTES + offA[t]) = pack_slice(s0[u], s1[u], f16);
+        }
       }
       if constexpr (!DT) {
         const int k0 = j * KS;
@@ -494,11 +564,18 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           const float2 pl = *reinterpret_cast<const float2*>(PO + KS + k);
           const bool far0 = all_far || ((kg < klo || kg >= khi) && kg < g.N);
           const bool far1 = all_far || ((kg + 1 < klo || kg + 1 >= khi) && kg + 1 < g.N);
-          uint32_t wd[4];
-          d_pack(ph.x, pl.x, ph.y, pl.y, eh, el, far0 ? me : 0.0f, far1 ? me : 0.0f, f16, wd);
+          if constexpr (NS == 5) {
+            uint32_t wd[5];
+            d_pack5(ph.x, pl.x, ph.y, pl.y, eh, el, far0 ? me : 0.0f, far1 ? me : 0.0f, wd);
 #pragma unroll
-          for (int v = 0; v < 4; ++v)
-            if (v < nsl) *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + offB[t]) = wd[v];
+            for (int v = 0; v < 5; ++v) *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + offB[t]) = wd[v];
+          } else {
+            uint32_t wd[4];
+            d_pack(ph.x, pl.x, ph.y, pl.y, eh, el, far0 ? me : 0.0f, far1 ? me : 0.0f, f16, wd);
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              if (v < nsl) *reinterpret_cast<uint32_t*>(Bb + v * SLICE_BYTES + offB[t]) = wd[v];
+          }
         }
       }
       // the MMAs (and, in clusters, the bulk copies) read these slices through the async proxy
@@ -578,12 +655,13 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
   if (threadIdx.x == 0 && *abort_flag) atomicMax(g.err, (int)RM_ERR_TIMEOUT);
 }
 
+template <int NS>
 __global__ void __launch_bounds__(NTHREADS, 1)
     polesum_tc_kernel(const __grid_constant__ CUtensorMap map_omega, const __grid_constant__ CUtensorMap map_pol,
                       TCArgs g) {
   extern __shared__ unsigned char smem_raw[];
   const int2 tile = g.tiles[blockIdx.x];
-  tc_tile<1, 1, false>(&map_omega, &map_pol, nullptr, g, tile.x * 8, tile.y * 16, blockIdx.y * BN, smem_raw);
+  tc_tile<1, 1, false, NS>(&map_omega, &map_pol, nullptr, g, tile.x * 8, tile.y * 16, blockIdx.y * BN, smem_raw);
 }
 
 // Every wave of a plan in one launch: tile list entries (wave, i-block, j-block),
@@ -591,7 +669,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // range is shared by all waves.  Launched in clusters of CX x CY CTAs: the tile
 // list holds each wave's tiles padded to a multiple of CX, and grid.y is a
 // multiple of CY.
-template <int CX, int CY, bool DT>
+template <int CX, int CY, bool DT, int NS>
 __global__ void __launch_bounds__(NTHREADS, 1)
     polesum_tc_grouped_kernel(const TCArgs* __restrict__ waves, const CUtensorMap* __restrict__ maps,
                               const int4* __restrict__ tiles, int64_t e_begin, int ne) {
@@ -600,8 +678,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   TCArgs g = waves[t.x];
   g.e_begin = e_begin;
   g.ne = ne;
-  tc_tile<CX, CY, DT>(maps + 3 * t.x, maps + 3 * t.x + 1, maps + 3 * t.x + 2, g, t.y * 8, t.z * 16,
-                      blockIdx.y * BN, smem_raw);
+  tc_tile<CX, CY, DT, NS>(maps + 3 * t.x, maps + 3 * t.x + 1, maps + 3 * t.x + 2, g, t.y * 8, t.z * 16,
+                          blockIdx.y * BN, smem_raw);
 }
 
 // ------------------------------------------------------------ preparation
@@ -745,8 +823,9 @@ struct DSliceWave {
   const float* mult_e;
   const int32_t* klo;
   const int32_t* khi;
-  uint32_t* D;          // [4][rows][Npad / 2]
+  uint32_t* D;          // [ns][rows][Npad / 2]
   int N, Npad, rows, f16;
+  int ns;               // slices per operand: 4, or 5 for the 15-product set
 };
 
 __global__ void __launch_bounds__(256) dslice_grouped_kernel(const DSliceWave* __restrict__ waves, int64_t e_begin,
@@ -774,10 +853,17 @@ __global__ void __launch_bounds__(256) dslice_grouped_kernel(const DSliceWave* _
     const float2 pl = *reinterpret_cast<const float2*>(w.pol + w.Npad + k);
     const bool far0 = (k < klo || k >= khi) && k < w.N;
     const bool far1 = (k + 1 < klo || k + 1 >= khi) && k + 1 < w.N;
-    uint32_t wd[4];
-    d_pack(ph.x, pl.x, ph.y, pl.y, eh, el, far0 ? me : 0.0f, far1 ? me : 0.0f, w.f16 != 0, wd);
+    if (w.ns == 5) {
+      uint32_t wd[5];
+      d_pack5(ph.x, pl.x, ph.y, pl.y, eh, el, far0 ? me : 0.0f, far1 ? me : 0.0f, wd);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) row[v * plane + kp] = wd[v];
+      for (int v = 0; v < 5; ++v) row[v * plane + kp] = wd[v];
+    } else {
+      uint32_t wd[4];
+      d_pack(ph.x, pl.x, ph.y, pl.y, eh, el, far0 ? me : 0.0f, far1 ? me : 0.0f, w.f16 != 0, wd);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) row[v * plane + kp] = wd[v];
+    }
   }
 }
 
@@ -913,7 +999,8 @@ bool encode_2d_f32(CUtensorMap* map, const float* base, uint64_t cols, uint64_t 
 
 }  // namespace
 
-size_t polesum_tc_smem_bytes() { return TC_SMEM; }
+size_t polesum_tc_smem_bytes() { return TcGeo<4>::SMEM > TcGeo<5>::SMEM ? TcGeo<4>::SMEM : TcGeo<5>::SMEM; }
+int polesum_slice_planes(int nprod) { return slices_of(nprod) == 5 ? 5 : 4; }
 
 std::vector<int2> split_tiles(int n) {
   std::vector<int2> t;
@@ -966,10 +1053,18 @@ cudaError_t launch_polesum_split(const Plan& p, const WaveDev& w, int64_t e0, in
   g.ne = ne;
   g.R = R;
   g.err = p.err_word;
-  cudaError_t err = cudaFuncSetAttribute(polesum_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-  if (err != cudaSuccess) return err;
   dim3 grid(sd.n_tiles, (ne + BN - 1) / BN);
-  polesum_tc_kernel<<<grid, NTHREADS, TC_SMEM, s>>>(sd.map_omega, sd.map_pol, g);
+  if (slices_of(p.slices) == 5) {
+    cudaError_t err = cudaFuncSetAttribute(polesum_tc_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)TcGeo<5>::SMEM);
+    if (err != cudaSuccess) return err;
+    polesum_tc_kernel<5><<<grid, NTHREADS, TcGeo<5>::SMEM, s>>>(sd.map_omega, sd.map_pol, g);
+  } else {
+    cudaError_t err = cudaFuncSetAttribute(polesum_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)TcGeo<4>::SMEM);
+    if (err != cudaSuccess) return err;
+    polesum_tc_kernel<4><<<grid, NTHREADS, TcGeo<4>::SMEM, s>>>(sd.map_omega, sd.map_pol, g);
+  }
   return cudaGetLastError();
 }
 
@@ -994,44 +1089,53 @@ namespace {
 
 using GroupedFn = void (*)(const TCArgs*, const CUtensorMap*, const int4*, int64_t, int);
 
-GroupedFn grouped_fn(int cx, int cy, bool dt) {
+template <int NS>
+GroupedFn grouped_fn_ns(int cx, int cy, bool dt) {
   if (dt) {
-    if (cx == 1 && cy == 1) return polesum_tc_grouped_kernel<1, 1, true>;
-    if (cx == 1 && cy == 2) return polesum_tc_grouped_kernel<1, 2, true>;
-    if (cx == 1 && cy == 4) return polesum_tc_grouped_kernel<1, 4, true>;
+    if (cx == 1 && cy == 1) return polesum_tc_grouped_kernel<1, 1, true, NS>;
+    if (cx == 1 && cy == 2) return polesum_tc_grouped_kernel<1, 2, true, NS>;
+    if (cx == 1 && cy == 4) return polesum_tc_grouped_kernel<1, 4, true, NS>;
     return nullptr;
   }
-  if (cx == 1 && cy == 1) return polesum_tc_grouped_kernel<1, 1, false>;
-  if (cx == 2 && cy == 1) return polesum_tc_grouped_kernel<2, 1, false>;
-  if (cx == 4 && cy == 1) return polesum_tc_grouped_kernel<4, 1, false>;
-  if (cx == 1 && cy == 2) return polesum_tc_grouped_kernel<1, 2, false>;
-  if (cx == 2 && cy == 2) return polesum_tc_grouped_kernel<2, 2, false>;
-  if (cx == 4 && cy == 2) return polesum_tc_grouped_kernel<4, 2, false>;
-  if (cx == 2 && cy == 4) return polesum_tc_grouped_kernel<2, 4, false>;
-  if (cx == 1 && cy == 4) return polesum_tc_grouped_kernel<1, 4, false>;
+  if (cx == 1 && cy == 1) return polesum_tc_grouped_kernel<1, 1, false, NS>;
+  if (cx == 2 && cy == 1) return polesum_tc_grouped_kernel<2, 1, false, NS>;
+  if (cx == 4 && cy == 1) return polesum_tc_grouped_kernel<4, 1, false, NS>;
+  if (cx == 1 && cy == 2) return polesum_tc_grouped_kernel<1, 2, false, NS>;
+  if (cx == 2 && cy == 2) return polesum_tc_grouped_kernel<2, 2, false, NS>;
+  if (cx == 4 && cy == 2) return polesum_tc_grouped_kernel<4, 2, false, NS>;
+  if (cx == 2 && cy == 4) return polesum_tc_grouped_kernel<2, 4, false, NS>;
+  if (cx == 1 && cy == 4) return polesum_tc_grouped_kernel<1, 4, false, NS>;
   return nullptr;
 }
 
+// the grouped kernel for a cluster shape, D staging and slice count (4 or 5 per operand)
+GroupedFn grouped_fn(int cx, int cy, bool dt, int ns) {
+  return ns == 5 ? grouped_fn_ns<5>(cx, cy, dt) : grouped_fn_ns<4>(cx, cy, dt);
+}
+
+size_t grouped_smem(int ns) { return ns == 5 ? TcGeo<5>::SMEM : TcGeo<4>::SMEM; }
+
 cudaError_t set_tc_smem() {
   const int shapes[8][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 2}, {2, 2}, {4, 2}, {2, 4}, {1, 4}};
-  for (int dt = 0; dt < 2; ++dt)
-    for (const auto& sh : shapes) {
-      GroupedFn fn = grouped_fn(sh[0], sh[1], dt != 0);
-      if (!fn) continue;
-      cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-      if (err != cudaSuccess) return err;
-    }
+  for (int ns = 4; ns <= 5; ++ns)
+    for (int dt = 0; dt < 2; ++dt)
+      for (const auto& sh : shapes) {
+        GroupedFn fn = grouped_fn(sh[0], sh[1], dt != 0, ns);
+        if (!fn) continue;
+        cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grouped_smem(ns));
+        if (err != cudaSuccess) return err;
+      }
   return cudaSuccess;
 }
 
-// 16-bit [4][rows][Npad] array of D slices, 32-pole x 128-energy x 4-slice boxes in the 64-byte
+// 16-bit [ns][rows][Npad] array of D slices, 32-pole x 128-energy x ns-slice boxes in the 64-byte
 // swizzle the MMA descriptors expect (the producers' layout, swz)
-bool encode_3d_d(CUtensorMap* map, const uint32_t* base, uint64_t npad, uint64_t rows) {
+bool encode_3d_d(CUtensorMap* map, const uint32_t* base, uint64_t npad, uint64_t rows, int ns) {
   auto enc = get_encoder();
   if (!enc) return false;
-  cuuint64_t dims[3] = {npad, rows, 4};
+  cuuint64_t dims[3] = {npad, rows, (cuuint64_t)ns};
   cuuint64_t strides[2] = {npad * 2, rows * npad * 2};
-  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)BN, 4};
+  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)BN, (cuuint32_t)ns};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint32_t*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1080,10 +1184,11 @@ cudaError_t group_setup_split(Plan& p) {
     maps[3 * g + 1] = sd.map_pol;
     std::memset(&maps[3 * g + 2], 0, sizeof(CUtensorMap));
     if (G.d_rows > 0 && G.D[g]) {
-      if (!encode_3d_d(&maps[3 * g + 2], G.D[g], (uint64_t)w.Npad, (uint64_t)G.d_rows)) return cudaErrorInvalidValue;
+      if (!encode_3d_d(&maps[3 * g + 2], G.D[g], (uint64_t)w.Npad, (uint64_t)G.d_rows, polesum_slice_planes(p.slices)))
+        return cudaErrorInvalidValue;
     }
     dw[g] = DSliceWave{sd.pol, sd.Eh, sd.El, sd.mult_e, sd.klo, sd.khi, G.D[g], w.N, w.Npad, G.d_rows,
-                       p.prec == RM_PREC_SPLIT_FP16 ? 1 : 0};
+                       p.prec == RM_PREC_SPLIT_FP16 ? 1 : 0, polesum_slice_planes(p.slices)};
     const std::vector<int2> wt = split_tiles(w.nR);
     for (const int2& t : wt) tiles.push_back(make_int4(g, t.x, t.y, w.Npad / KS));
     // pad to a multiple of the cluster width with empty tiles (i-block past the last channel)
@@ -1136,15 +1241,15 @@ cudaError_t group_setup_split(Plan& p) {
                               (int)near_smem_bytes(p.nR_max));
 }
 
-bool polesum_cluster_ok(int cx, int cy) {
-  GroupedFn fn = grouped_fn(cx, cy, cx == 1);
+bool polesum_cluster_ok(int cx, int cy, int ns) {
+  GroupedFn fn = grouped_fn(cx, cy, cx == 1, ns);
   if (!fn) return false;
   if (cx * cy == 1) return true;
   if (set_tc_smem() != cudaSuccess) return false;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cx * 8, cy * 8, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = TC_SMEM;
+  cfg.dynamicSmemBytes = grouped_smem(ns);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cx;
@@ -1163,13 +1268,14 @@ bool polesum_cluster_ok(int cx, int cy) {
 cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s) {
   if (ne <= 0) return cudaSuccess;
   const GroupDev& G = p.grp;
-  GroupedFn fn = grouped_fn(G.tc_cx, G.tc_cy, G.dt());
+  const int ns = polesum_slice_planes(p.slices);
+  GroupedFn fn = grouped_fn(G.tc_cx, G.tc_cy, G.dt(), ns);
   if (!fn) return cudaErrorInvalidValue;
   const int ny = (ne + BN - 1) / BN;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G.n_tiles, (ny + G.tc_cy - 1) / G.tc_cy * G.tc_cy, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = TC_SMEM;
+  cfg.dynamicSmemBytes = grouped_smem(ns);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

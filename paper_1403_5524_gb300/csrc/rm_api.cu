@@ -518,7 +518,7 @@ rm_status_t autotune(Plan* p, const char* cache, int chunk_max, bool tune_chunk,
   const std::string key = tune_key(p);
   Tuned t;
   if (cache_lookup(cache, key, t) && t.chunk > 0 && t.chunk <= chunk_max &&
-      (!tune_cluster || polesum_cluster_ok(t.cx, t.cy))) {
+      (!tune_cluster || polesum_cluster_ok(t.cx, t.cy, polesum_slice_planes(p->slices)))) {
     if (tune_chunk) G.chunk = t.chunk;
     if (tune_cluster) {
       G.tc_cx = t.cx;
@@ -538,7 +538,7 @@ rm_status_t autotune(Plan* p, const char* cache, int chunk_max, bool tune_chunk,
     double best_t = 1e300;
     int bx = G.tc_cx, by = G.tc_cy;
     for (const auto& sh : kShapes) {
-      if (!polesum_cluster_ok(sh[0], sh[1])) continue;
+      if (!polesum_cluster_ok(sh[0], sh[1], polesum_slice_planes(p->slices))) continue;
       G.tc_cx = sh[0];
       G.tc_cy = sh[1];
       float ms = 0.f;
@@ -629,10 +629,12 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     if (o.prec < RM_PREC_FP64 || o.prec > RM_PREC_FP32_SIMT) return fail(RM_ERR_ARG, "bad precision mode");
     if (o.prec != RM_PREC_FP64 && !(o.delta > 0.0)) return fail(RM_ERR_ARG, "delta must be > 0");
     if (o.chunk < 0) return fail(RM_ERR_ARG, "chunk must be >= 0");
-    if (!(o.slices == 0 || o.slices == 3 || o.slices == 6 || o.slices == 10 || o.slices == 13))
-      return fail(RM_ERR_ARG, "slices must be 0 (default), 3, 6, 10 or 13 slice products");
+    if (!(o.slices == 0 || o.slices == 3 || o.slices == 6 || o.slices == 10 || o.slices == 13 || o.slices == 15))
+      return fail(RM_ERR_ARG, "slices must be 0 (default), 3, 6, 10, 13 or 15 slice products");
     if (o.slices != 0 && o.prec != RM_PREC_SPLIT_BF16 && o.prec != RM_PREC_SPLIT_FP16)
       return fail(RM_ERR_ARG, "slices applies to the tensor-core modes (SPLIT_BF16, SPLIT_FP16) only");
+    if (o.slices == 15 && o.prec != RM_PREC_SPLIT_BF16)
+      return fail(RM_ERR_ARG, "slices = 15 needs BF16 slices (FP16 cannot hold the fifth, 2^-25 small)");
     if (o.solve_prec != RM_SOLVE_FP64 && o.solve_prec != RM_SOLVE_MIXED && o.solve_prec != RM_SOLVE_FP64_LU)
       return fail(RM_ERR_ARG, "bad solve precision");
     if (!(o.cluster_x == 0 || o.cluster_x == 1 || o.cluster_x == 2 || o.cluster_x == 4) ||
@@ -755,10 +757,12 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       // fits min(24 GiB, a third of free device memory): one launch per kernel
       // and sweep, no chunk tails; otherwise chunks (autotuned when asked).
       // per energy and wave: R, the asymptotic data and (tensor-core modes) the D slices,
-      // 4 x 2 bytes per pole
+      // 4 or 5 x 2 bytes per pole (in units of 8 bytes)
       const bool dslices = is_split_like(o.prec) && o.prec != RM_PREC_FP32_SIMT;
+      const int planes = polesum_slice_planes(p->slices);
       int64_t per_e = 0;
-      for (const auto& w : p->waves) per_e += w.npR() + 4ll * w.n + (dslices ? (int64_t)w.Npad : 0);
+      for (const auto& w : p->waves)
+        per_e += w.npR() + 4ll * w.n + (dslices ? ((int64_t)w.Npad * planes + 3) / 4 : 0);
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 2ull << 30; }
       int64_t budget = (int64_t)(free_b / 3);
@@ -776,7 +780,8 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
         const WaveDev& d = p->waves[g];
         st = dalloc(p, &p->grp.R[g], cmax * d.npR());
         if (st == RM_OK) st = dalloc(p, &p->grp.asym[g], 4ll * cmax * d.n);
-        if (st == RM_OK && dslices) st = dalloc(p, &p->grp.D[g], 2ll * cmax * d.Npad);  // 4 x Npad/2 words
+        if (st == RM_OK && dslices)
+          st = dalloc(p, &p->grp.D[g], (int64_t)planes * cmax * (d.Npad / 2));  // planes x Npad/2 words
       }
       p->grp.d_rows = (st == RM_OK && dslices) ? (int)cmax : 0;
     }
@@ -796,13 +801,13 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if (o.cluster_x > 0 || o.cluster_y > 0) {
         p->grp.tc_cx = o.cluster_x > 0 ? o.cluster_x : 1;
         p->grp.tc_cy = o.cluster_y > 0 ? o.cluster_y : 1;
-        if (!polesum_cluster_ok(p->grp.tc_cx, p->grp.tc_cy))
+        if (!polesum_cluster_ok(p->grp.tc_cx, p->grp.tc_cy, polesum_slice_planes(p->slices)))
           st = fail(RM_ERR_ARG, "cluster shape cannot be co-scheduled on this device");
       } else {
         p->grp.tc_cx = 1;
         p->grp.tc_cy = 1;
         for (const auto& sh : kShapes) {
-          if (polesum_cluster_ok(sh[0], sh[1])) {
+          if (polesum_cluster_ok(sh[0], sh[1], polesum_slice_planes(p->slices))) {
             p->grp.tc_cx = sh[0];
             p->grp.tc_cy = sh[1];
             break;

@@ -137,7 +137,7 @@ struct GroupDev {
   int4* tiles = nullptr;      // (wave, i-block, j-block), longest K first
   int n_tiles = 0;
   int tc_cx = 1, tc_cy = 1;   // tensor-core cluster shape (pair tiles x energy tiles)
-  std::vector<uint32_t*> D;   // per wave [4 slices][d_rows energies][Npad / 2 pole pairs] packed D slices
+  std::vector<uint32_t*> D;   // per wave [4 or 5 slices][d_rows energies][Npad / 2 pole pairs] packed D slices
   int d_rows = 0;             // energy rows of each D buffer (the largest chunk); 0: none allocated
   void* dslice_waves = nullptr;
   // D slices staged by TMA (written by the D-slice kernel) instead of formed by the producers:
@@ -165,7 +165,7 @@ struct Plan {
   int64_t n_e = 0;
   int prec = RM_PREC_FP64;
   double delta = 0.05;
-  int slices = 13;  // slice products per far term of the tensor-core pole sum: 3, 6, 10 or 13
+  int slices = 13;  // slice products per far term of the tensor-core pole sum: 3, 6, 10, 13 or 15
   int n_sel = 1;
   int32_t sel[RM_MAX_SEL] = {0};
   int32_t* sel_dev = nullptr;
@@ -257,8 +257,10 @@ cudaError_t group_setup_solve(Plan& p);
 cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
 // D slices of the chunk [e0, e0 + ne) for every wave (shapes with cluster_x = 1)
 cudaError_t launch_dslice_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
-// clusters of this shape can be resident (grouped tensor-core kernel)
-bool polesum_cluster_ok(int cx, int cy);
+// clusters of this shape can be resident (grouped tensor-core kernel with ns slices per operand)
+bool polesum_cluster_ok(int cx, int cy, int ns);
+// slices per operand the tensor-core kernel stages for a product set (4, or 5 for 15 products)
+int polesum_slice_planes(int nprod);
 cudaError_t launch_near_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
 cudaError_t launch_asym_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
 cudaError_t launch_solve_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);

@@ -102,6 +102,9 @@ def test_slices_option_checked_on_host(lib):
     for prec in (rm.RM_PREC_FP64, rm.RM_PREC_FP32_SIMT):
         o.prec, o.slices = prec, 6
         assert _create(lib, wl.waves, wl.energies, o)[0] == rm.RM_ERR_ARG
+    o.prec, o.slices = rm.RM_PREC_SPLIT_FP16, 15  # the fifth slice is below FP16's range
+    assert _create(lib, wl.waves, wl.energies, o)[0] == rm.RM_ERR_ARG
+    assert b"15" in lib.rm_last_error()
     v = C.c_int32(-7)
     assert lib.rm_plan_slices(None, C.byref(v)) == rm.RM_ERR_ARG
 
@@ -193,7 +196,7 @@ def test_binding_constants_match_the_header():
     for k, v in rm.KERNELS.items():
         assert defs["RM_KERNEL_" + kern[k]] == v, k
     assert defs["RM_KERNEL_COUNT"] == len(rm.KERNELS)
-    assert defs["RM_DEFAULT_SLICES"] in (3, 6, 10, 13)
+    assert defs["RM_DEFAULT_SLICES"] in (3, 6, 10, 13, 15)
     enum = re.search(r"typedef enum \{([^}]*)\} rm_solve_precision_t;", txt).group(1)
     vals = {m.group(1): int(m.group(2)) for m in re.finditer(r"RM_SOLVE_(\w+) = (\d+)", enum)}
     assert vals == {"FP64": rm.SOLVE["fp64"], "MIXED": rm.SOLVE["mixed"], "FP64_LU": rm.SOLVE["fp64_lu"]}
