@@ -100,6 +100,7 @@ def parse():
                     help="slice products per far term of the tensor-core pole sum (0: the library default)")
     ap.add_argument("--slices-study", action="store_true",
                     help="accuracy and energies/s of every product set (3, 6, 10, 13, 15) on this workload")
+    ap.add_argument("--study-sets", default="", help="comma-separated product sets of --slices-study (default: all)")
     ap.add_argument("--accuracy-energies", type=int, default=64,
                     help="evenly spaced mesh energies checked against the oracle (plus near-threshold and "
                          "near-pole energies)")
@@ -722,7 +723,8 @@ def run_slices_study(args):
     ref_x = orc.sweep(wl.waves[0], extra, sel=sel)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     prec = args.prec if args.prec in ("split_bf16", "split_fp16") else "split_bf16"
-    for products in PRODUCT_SETS:
+    sets = tuple(int(x) for x in args.study_sets.split(",")) if args.study_sets else PRODUCT_SETS
+    for products in sets:
         with rm.Plan(dwaves, dE, prec=prec, delta=wl.delta, sel=sel, stream=stream, autotune=True,
                      slices=products, solve=args.solve) as p:
             p.run()

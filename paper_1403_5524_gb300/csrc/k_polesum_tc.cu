@@ -50,19 +50,25 @@ constexpr int WI_FLOATS = 16 * KS;   // 8 channels x (hi, lo) rows
 constexpr int WJ_FLOATS = 32 * KS;   // 16 channels x (hi, lo) rows
 constexpr int PO_FLOATS = 2 * KS;    // poles hi row, lo row
 constexpr int TX_BYTES = (WI_FLOATS + WJ_FLOATS + PO_FLOATS) * 4;  // 6400
-// Shared-memory geometry for NS slices per operand: a stage holds NS slices of P (A), NS of D
-// (B) and the staged W rows and poles.  Four slices fit three stages in the 227 KB of a CTA, five
-// only two.
-template <int NS>
+// Shared-memory geometry for NS slices per operand.  Without RING a stage holds NS slices of P
+// (A), NS of D (B) and the staged W rows and poles: four slices fit three stages in the 227 KB
+// of a CTA, five only two.  With RING (five slices, D by TMA) the D slices live in a ring of
+// their own, two deep, and the stages (P slices + W rows) stay three deep: 3 x 47 + 2 x 40 KB.
+template <int NS, bool RING = false>
 struct TcGeo {
   static constexpr int A_BYTES = NS * SLICE_BYTES;
   static constexpr int B_BYTES = NS * SLICE_BYTES;
-  static constexpr int STAGES = NS == 5 ? 2 : 3;
-  static constexpr int STAGE_STRIDE = ((A_BYTES + B_BYTES + TX_BYTES + 1023) / 1024) * 1024;
-  static constexpr int NBARS = 5 * STAGES + 3;
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE_STRIDE + 1024 + NBARS * 8 + 16;
+  static constexpr int STAGES = (NS == 5 && !RING) ? 2 : 3;
+  static constexpr int BSTAGES = RING ? 2 : STAGES;  // D-slice buffers
+  static constexpr int W_OFF = RING ? A_BYTES : A_BYTES + B_BYTES;  // W rows within a stage
+  static constexpr int STAGE_STRIDE = ((W_OFF + TX_BYTES + 1023) / 1024) * 1024;
+  static constexpr int B_RING = RING ? STAGES * STAGE_STRIDE : 0;  // offset of the D ring
+  static constexpr int BARS_OFF = STAGES * STAGE_STRIDE + (RING ? BSTAGES * B_BYTES : 0);
+  static constexpr int NBARS = 5 * STAGES + 3 + (RING ? BSTAGES : 0);
+  static constexpr size_t SMEM = (size_t)BARS_OFF + 1024 + NBARS * 8 + 16;
 };
-static_assert(TcGeo<4>::SMEM <= 232448 && TcGeo<5>::SMEM <= 232448, "a CTA's shared memory");
+static_assert(TcGeo<4>::SMEM <= 232448 && TcGeo<5>::SMEM <= 232448 && TcGeo<5, true>::SMEM <= 232448,
+              "a CTA's shared memory");
 // slices per operand of a product set: 3 products use two, 6 three, 10 and 13 four, 15 five
 __host__ __device__ constexpr int slices_of(int nprod) { return nprod == 3 ? 2 : (nprod == 6 ? 3 : (nprod == 15 ? 5 : 4)); }
 constexpr long long WAIT_BUDGET = 4000000000LL;   // clock cycles (~2 s) per mbarrier wait
@@ -225,25 +231,32 @@ struct TCArgs {
 // and clusters share P alone (CX = 1).
 //
 // NS: slices per operand the tile's shared memory holds (4: the 3-, 6-, 10- and 13-product sets,
-// three stages; 5: the 15-product set, two stages).
+// three stages; 5: the 15-product set, two stages, or with D by TMA three stages of P and W rows
+// and a two-deep ring of D buffers, refilled by the loading producer thread once the MMAs of the
+// step two back are done).
 template <int CX, int CY, bool DT, int NS>
 __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUtensorMap* map_pol,
                                         const CUtensorMap* map_d, const TCArgs& g, int I0, int J0, int n0,
                                         unsigned char* smem_raw) {
   using namespace ptx;
   static_assert(NS == 4 || NS == 5, "four or five slices per operand");
-  constexpr int STAGES = TcGeo<NS>::STAGES;
-  constexpr int A_BYTES = TcGeo<NS>::A_BYTES;
-  constexpr int B_BYTES = TcGeo<NS>::B_BYTES;
-  constexpr int STAGE_STRIDE = TcGeo<NS>::STAGE_STRIDE;
-  constexpr int NBARS = TcGeo<NS>::NBARS;
+  constexpr bool RING = NS == 5 && DT;  // D slices in a two-deep ring of their own
+  using Geo = TcGeo<NS, RING>;
+  constexpr int STAGES = Geo::STAGES;
+  constexpr int BST = Geo::BSTAGES;
+  static_assert(!RING || BST == 2, "the D ring is two deep");
+  constexpr int A_BYTES = Geo::A_BYTES;
+  constexpr int B_BYTES = Geo::B_BYTES;
+  constexpr int W_OFF = Geo::W_OFF;
+  constexpr int STAGE_STRIDE = Geo::STAGE_STRIDE;
+  constexpr int NBARS = Geo::NBARS;
   constexpr int CL = CX * CY;
   static_assert(!DT || CX == 1, "TMA-staged D slices are not shared across the cluster");
   static_assert(CX == 1 || CX == 2 || CX == 4, "CX in {1, 2, 4}");
   static_assert(CY == 1 || CY == 2 || CY == 4, "CY in {1, 2, 4}");
   static_assert(CX * CY <= 8, "portable cluster size");
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_STRIDE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Geo::BARS_OFF);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* wfull = bars + 2 * STAGES;
@@ -252,6 +265,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
   uint64_t* acc_full = bars + 5 * STAGES;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* done = acc_full + 2;
+  uint64_t* emptyB = acc_full + 3;  // RING: the MMAs of a step are done with its D buffer
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBARS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -280,6 +294,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NWORK);
     mbar_init(done, 1);
+    if constexpr (RING)
+      for (int q = 0; q < BST; ++q) mbar_init(emptyB + q, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -300,7 +316,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       for (int s = 0; s < STAGES; ++s) tma_last[s] = -1;
       auto issue_tma = [&](int s, int j) {
         uint8_t* st = smem + s * STAGE_STRIDE;
-        float* WI = reinterpret_cast<float*>(st + A_BYTES + B_BYTES);
+        float* WI = reinterpret_cast<float*>(st + W_OFF);
         float* WJ = WI + WI_FLOATS;
         float* PO = WJ + WJ_FLOATS;
         mbar_arrive_expect_tx(wfull + s, TX_BYTES);
@@ -322,7 +338,11 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         bool got;
         if constexpr (CL > 1) got = mbar_wait_cluster(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget);
         else got = mbar_wait(full + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget);
-        if (got && DT) got = mbar_wait(dfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget);
+        if constexpr (RING) {
+          if (got) got = mbar_wait(dfull + j % BST, (uint32_t)((j / BST) & 1), abort_flag, g.wait_budget);
+        } else {
+          if (got && DT) got = mbar_wait(dfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget);
+        }
         if (!got) { ok = false; break; }
         if (j + STAGES < nK) issue_tma(s, j + STAGES);
         const int d = j / DRAIN_KSTEPS;
@@ -332,7 +352,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         }
         tc_fence_after();
         const uint32_t a = smem_u32(smem + s * STAGE_STRIDE);
-        const uint32_t b = a + A_BYTES;
+        const uint32_t b = RING ? smem_u32(smem + Geo::B_RING + (j % BST) * B_BYTES) : a + A_BYTES;
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
           const uint32_t ko = kk * 32;
@@ -379,6 +399,7 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         if constexpr (CL > 1) mma_commit_mc(empty + s, (uint16_t)peer_mask);
         else mma_commit(empty + s);
         if ((j + 1) % DRAIN_KSTEPS == 0 || j == nK - 1) mma_commit(acc_full);
+        if constexpr (RING) mma_commit(emptyB + j % BST);  // this step's D buffer may be refilled
       }
       if (ok && CL > 1) {
         // every peer's commit for the last use of each stage has landed here, so no
@@ -508,17 +529,29 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           break;
         }
       }
-      if (dloader) {  // the stage's B area is free: fetch this k-step's D slices
-        mbar_arrive_expect_tx(dfull + s, (uint32_t)B_BYTES);
-        tma_load_3d(smem + s * STAGE_STRIDE + A_BYTES, map_d, dfull + s, j * KS, n0, 0);
-        d_last[s] = j;
+      if (dloader) {
+        if constexpr (RING) {
+          // the D buffer of step j - 2 is free once that step's MMAs are done: fetch this step's D
+          const int q = j % BST;
+          if (j >= BST && !mbar_wait(emptyB + q, (uint32_t)(((j / BST) - 1) & 1), abort_flag, g.wait_budget)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(dfull + q, (uint32_t)B_BYTES);
+          tma_load_3d(smem + Geo::B_RING + q * B_BYTES, map_d, dfull + q, j * KS, n0, 0);
+          d_last[q] = j;
+        } else {  // the stage's B area is free: fetch this k-step's D slices
+          mbar_arrive_expect_tx(dfull + s, (uint32_t)B_BYTES);
+          tma_load_3d(smem + s * STAGE_STRIDE + A_BYTES, map_d, dfull + s, j * KS, n0, 0);
+          d_last[s] = j;
+        }
       }
       if (!mbar_wait(wfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget)) {
         ok = false;
         break;
       }
       uint8_t* st = smem + s * STAGE_STRIDE;
-      const float* WI = reinterpret_cast<const float*>(st + A_BYTES + B_BYTES);
+      const float* WI = reinterpret_cast<const float*>(st + W_OFF);
       const float* WJ = WI + WI_FLOATS;
       const float* PO = WJ + WJ_FLOATS;
       uint8_t* Ab = st;
@@ -624,7 +657,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       for (int q = 0; q < STAGES; ++q) {
         if (d_last[q] < 0) continue;
         const long long t0 = clock64();
-        while (!mbar_try_wait(dfull + q, (uint32_t)((d_last[q] / STAGES) & 1)) && clock64() - t0 < cleanup) {
+        while (!mbar_try_wait(dfull + q, (uint32_t)((d_last[q] / (RING ? BST : STAGES)) & 1)) &&
+               clock64() - t0 < cleanup) {
         }
       }
     }
@@ -999,7 +1033,12 @@ bool encode_2d_f32(CUtensorMap* map, const float* base, uint64_t cols, uint64_t 
 
 }  // namespace
 
-size_t polesum_tc_smem_bytes() { return TcGeo<4>::SMEM > TcGeo<5>::SMEM ? TcGeo<4>::SMEM : TcGeo<5>::SMEM; }
+size_t polesum_tc_smem_bytes() {
+  size_t m = TcGeo<4>::SMEM;
+  if (TcGeo<5>::SMEM > m) m = TcGeo<5>::SMEM;
+  if (TcGeo<5, true>::SMEM > m) m = TcGeo<5, true>::SMEM;
+  return m;
+}
 int polesum_slice_planes(int nprod) { return slices_of(nprod) == 5 ? 5 : 4; }
 
 std::vector<int2> split_tiles(int n) {
@@ -1113,7 +1152,10 @@ GroupedFn grouped_fn(int cx, int cy, bool dt, int ns) {
   return ns == 5 ? grouped_fn_ns<5>(cx, cy, dt) : grouped_fn_ns<4>(cx, cy, dt);
 }
 
-size_t grouped_smem(int ns) { return ns == 5 ? TcGeo<5>::SMEM : TcGeo<4>::SMEM; }
+// dynamic shared memory of a grouped kernel (five slices with D by TMA: the two-deep D ring)
+size_t grouped_smem(int ns, bool dt) {
+  return ns == 5 ? (dt ? TcGeo<5, true>::SMEM : TcGeo<5>::SMEM) : TcGeo<4>::SMEM;
+}
 
 cudaError_t set_tc_smem() {
   const int shapes[8][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 2}, {2, 2}, {4, 2}, {2, 4}, {1, 4}};
@@ -1122,7 +1164,8 @@ cudaError_t set_tc_smem() {
       for (const auto& sh : shapes) {
         GroupedFn fn = grouped_fn(sh[0], sh[1], dt != 0, ns);
         if (!fn) continue;
-        cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grouped_smem(ns));
+        cudaError_t err =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grouped_smem(ns, dt != 0));
         if (err != cudaSuccess) return err;
       }
   return cudaSuccess;
@@ -1249,7 +1292,7 @@ bool polesum_cluster_ok(int cx, int cy, int ns) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cx * 8, cy * 8, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = grouped_smem(ns);
+  cfg.dynamicSmemBytes = grouped_smem(ns, cx == 1);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cx;
@@ -1275,7 +1318,7 @@ cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cuda
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G.n_tiles, (ny + G.tc_cy - 1) / G.tc_cy * G.tc_cy, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = grouped_smem(ns);
+  cfg.dynamicSmemBytes = grouped_smem(ns, G.dt());
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
