@@ -104,7 +104,10 @@ typedef enum {
                                        are reported, and judged, apart from the rest of the mesh */
 
 #define RM_LMAX 32           /* largest supported channel angular momentum */
-#define RM_DEFAULT_SLICES 13 /* slice products of the tensor-core pole sum when rm_options.slices = 0 */
+#define RM_DEFAULT_SLICES 15 /* slice products of the tensor-core pole sum when rm_options.slices = 0:
+                                the cheapest set that keeps R and K within 1e-6 and cross sections
+                                within 1e-8 of the FP64 oracle on the sampled n_ch = 256 mesh
+                                (SPLIT_FP16, which cannot hold five slices, defaults to 13) */
 #define RM_MAX_SEL 64        /* largest number of selected initial channels */
 
 /* Matching solve.  FP64: rm_kmatrix solves for K by LU

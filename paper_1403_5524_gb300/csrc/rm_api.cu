@@ -671,7 +671,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     p->n_e = n_e;
     p->prec = o.prec;
     p->delta = o.delta;
-    p->slices = o.slices ? o.slices : RM_DEFAULT_SLICES;
+    p->slices = o.slices ? o.slices : (o.prec == RM_PREC_SPLIT_FP16 ? 13 : RM_DEFAULT_SLICES);
     p->fault_wait = env_ll("RM_FAULT_WAIT_CYCLES");
     p->n_sel = n_sel;
     std::memcpy(p->sel, sel, sizeof(sel));

@@ -108,15 +108,18 @@ def test_autotune_and_cache(rm, tmp_path):
 CLUSTERS = [(1, 1), (2, 1), (4, 1), (1, 2), (2, 2), (1, 4), (4, 2), (2, 4)]
 
 
-@pytest.fixture(scope="module")
-def cluster_case(rm):
+@pytest.fixture(scope="module", params=[0, 13], ids=["default-products", "13-products"])
+def cluster_case(rm, request):
     # uneven waves (odd tile counts per wave, so clusters need padding), a mesh
-    # that is not a multiple of 128 energies, two selected channels
+    # that is not a multiple of 128 energies, two selected channels; the default
+    # product set (five slices: a separate D ring with D by TMA, two stages with D
+    # formed in the kernel) and the 13-product set (four slices, three stages)
     waves = [synth.small(500 + g, n, 40 * n, 1, pole_lo=-3, pole_hi=12, a=20.0).waves[0]
              for g, n in enumerate([5, 23, 9, 40, 17])]
     E = np.linspace(0.04, 3.3, 333)
     sel = (0, 1)
-    with rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, chunk=200, cluster=(1, 1)) as p:
+    slices = request.param
+    with rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, chunk=200, cluster=(1, 1), slices=slices) as p:
         assert p.cluster() == (1, 1)
         p.run()
         base = []
@@ -124,16 +127,16 @@ def cluster_case(rm):
             o = rm.host_outputs(E.size, w.n, 2)
             p.results(g, 0, E.size, **o)
             base.append(o)
-    return waves, E, sel, base
+    return waves, E, sel, base, slices
 
 
 @pytest.mark.parametrize("shape", CLUSTERS, ids=["%dx%d" % c for c in CLUSTERS])
 def test_cluster_shapes_identical(rm, cluster_case, shape):
     # every CTA forms the same slices whichever CTA of a cluster stores them, so
     # the sums (and everything after them) are bit-identical across cluster shapes
-    waves, E, sel, base = cluster_case
+    waves, E, sel, base, slices = cluster_case
     try:
-        p = rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, chunk=200, cluster=shape)
+        p = rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, chunk=200, cluster=shape, slices=slices)
     except rm.RMError as ex:
         pytest.skip(f"cluster shape {shape} not co-schedulable here: {ex}")
     with p:

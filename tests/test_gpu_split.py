@@ -2,10 +2,12 @@
 near-pole window + FP64 solves) with the FP64 CPU oracle (needs a GPU).
 
 Tolerances:
-* R per element: each far term P_pk D_ke carries the FP32 rounding of omega_i,
-  omega_j, their product and of D (difference and reciprocal), at most about
-  6 * 2^-24 relative; slicing and accumulation are exact.  So
-  |R - R*| <= 4e-7 (1/2a) sum_k |w_ik w_jk / (E_k - E)|, checked per element.
+* R per element (the default product set): P and D are formed in double-float
+  (about 2^-46), and the slicing leaves at most 2^-31 of the product of the two
+  scales per far term (test_split_product_sets bounds each set separately); the
+  per-element check |R - R*| <= 4e-7 (1/2a) sum_k |w_ik w_jk / (E_k - E)| is the
+  bound of an FP32 formation of every term, which all sets of 10 products or more
+  stay far inside.
 * R, K normwise <= 1e-6 and sigma <= 1e-8 (normalised by sigma_tot of the
   initial channel): the accuracy targets of the method's split form, on
   energies the oracle does not flag ILLCOND.
@@ -195,7 +197,7 @@ def test_split_config3_sampled(rm):
                                          (13, "split_bf16"), (15, "split_bf16"), (10, "split_fp16")])
 def test_split_product_sets(rm, slices, prec):
     # each product set of the tensor-core pole sum against the oracle, R per element within the
-    # set's truncation bound; the sets that reach the method's targets (10 and 13 products) are
+    # set's truncation bound; the sets that reach the method's targets here (10, 13, 15 products) are
     # also held to them for K, sigma and eta, through the per-range calls and through rm_run
     wl = synth.small(31, 24, 3000, 36, e_lo=0.05, e_hi=3.4, pole_lo=-3.0, pole_hi=12.0, a=20.0, delta=0.05)
     w = wl.waves[0]
