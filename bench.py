@@ -263,6 +263,12 @@ def oracle_sample(wl, sel, budget_s=15.0, max_e=64, keep=False):
     return done, dt, idx[:done], out
 
 
+def workload_config(wl, stride, sel):
+    """The workload keys of the JSON line's config, the same in both arms."""
+    return {"workload": wl.name, "mesh_stride": stride, "energies_per_step": wl.n_e, "waves": len(wl.waves),
+            "n_ch": [w.n for w in wl.waves][:4], "n_poles": [w.N for w in wl.waves][:4], "n_sel": len(sel)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -282,8 +288,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
-            "config": {"workload": wl.name, "mesh_stride": stride,
-                       "sample": f"{per} evenly spaced energies of the mesh per step"},
+            "config": workload_config(wl, stride, sel),
+            "sample": f"{per} evenly spaced energies of the mesh per step",
             "cpu_baseline": {"value": val, "unit": "energies/s", "cores": cores, "kind": "oracle",
                              "sample": f"{total_e} energies over {args.steps} steps"},
             "e2e": {"value": val, "unit": "energies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -560,15 +566,12 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.prec == "fp64" else "bf16-split+f64",
                 "data": "synthetic (seeded, workload distributions of the paper's problem class)",
-                "config": {"workload": wl.name, "prec": args.prec, "mesh_stride": stride,
-                           "energy_chunk": plan.info(0)["chunk"],
-                           "tc_cluster": "%dx%d" % plan.cluster(), "solve": args.solve,
-                           "fp64_fallback_energies": fallback,
-                           "lu_path_energies": lu_fallback if args.solve == "fp64" else None,
-                           "energies_per_step": wl.n_e, "waves": len(wl.waves),
-                           "n_ch": [w.n for w in wl.waves][:4], "n_poles": [w.N for w in wl.waves][:4],
-                           "n_sel": len(sel), "l2": "flushed (512 MB write) between timed steps",
-                           "parallelism": f"replicas x{world}"},
+                "config": dict(workload_config(wl, stride, sel),
+                               l2="flushed (512 MB write) between timed steps", parallelism=f"replicas x{world}"),
+                "impl_config": {"prec": args.prec, "slice_products": plan.slices(),
+                                "energy_chunk": plan.info(0)["chunk"], "tc_cluster": "%dx%d" % plan.cluster(),
+                                "solve": args.solve, "fp64_fallback_energies": fallback,
+                                "lu_path_energies": lu_fallback if args.solve == "fp64" else None},
                 "roofline": roof, "roofline_tensor": roof_tc, "kernels": kern, "gpu_launches": int(launches),
                 "fp64_gpu": fp64, "k_formed": k_formed, "post_convolve": post,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "errors": errors}

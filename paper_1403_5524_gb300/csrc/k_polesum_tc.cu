@@ -517,6 +517,10 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
     int d_last[STAGES];
 #pragma unroll
     for (int q = 0; q < STAGES; ++q) d_last[q] = -1;
+    // Every way out of this loop is taken by whole warps, so that no lane is left at the
+    // __syncwarp below while another has gone on to the final barrier: the waits are polled by
+    // all lanes of a converged warp in the same instructions (the same barrier phase, abort flag
+    // and clock), and the one wait made by a single lane (the D loader's) is broadcast first.
     for (int j = 0; j < nK && ok; ++j) {
       const int s = j % STAGES;
       if (j >= STAGES) {
@@ -529,21 +533,27 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           break;
         }
       }
-      if (dloader) {
-        if constexpr (RING) {
-          // the D buffer of step j - 2 is free once that step's MMAs are done: fetch this step's D
-          const int q = j % BST;
-          if (j >= BST && !mbar_wait(emptyB + q, (uint32_t)(((j / BST) - 1) & 1), abort_flag, g.wait_budget)) {
-            ok = false;
-            break;
+      if (DT && w == 0) {
+        bool dl_ok = true;
+        if (lane == 0) {
+          if constexpr (RING) {
+            // the D buffer of step j - 2 is free once that step's MMAs are done: fetch this step's D
+            const int q = j % BST;
+            if (j >= BST) dl_ok = mbar_wait(emptyB + q, (uint32_t)(((j / BST) - 1) & 1), abort_flag, g.wait_budget);
+            if (dl_ok) {
+              mbar_arrive_expect_tx(dfull + q, (uint32_t)B_BYTES);
+              tma_load_3d(smem + Geo::B_RING + q * B_BYTES, map_d, dfull + q, j * KS, n0, 0);
+              d_last[q] = j;
+            }
+          } else {  // the stage's B area is free: fetch this k-step's D slices
+            mbar_arrive_expect_tx(dfull + s, (uint32_t)B_BYTES);
+            tma_load_3d(smem + s * STAGE_STRIDE + A_BYTES, map_d, dfull + s, j * KS, n0, 0);
+            d_last[s] = j;
           }
-          mbar_arrive_expect_tx(dfull + q, (uint32_t)B_BYTES);
-          tma_load_3d(smem + Geo::B_RING + q * B_BYTES, map_d, dfull + q, j * KS, n0, 0);
-          d_last[q] = j;
-        } else {  // the stage's B area is free: fetch this k-step's D slices
-          mbar_arrive_expect_tx(dfull + s, (uint32_t)B_BYTES);
-          tma_load_3d(smem + s * STAGE_STRIDE + A_BYTES, map_d, dfull + s, j * KS, n0, 0);
-          d_last[s] = j;
+        }
+        if (!__shfl_sync(0xffffffffu, dl_ok, 0)) {
+          ok = false;
+          break;
         }
       }
       if (!mbar_wait(wfull + s, (uint32_t)((j / STAGES) & 1), abort_flag, g.wait_budget)) {
