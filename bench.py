@@ -31,10 +31,11 @@ from paper_1403_5524_gb300 import synth  # noqa: E402
 
 METRIC = "energies/sec (R+K+σ) split-precision vs FP64 GPU at n_ch=256; max rel err"
 FP64_NOMINAL_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU; the measured probe is the peak used
-# DRAM bytes (read + write) per energy of the solve kernel, from one ncu capture of the n_ch=256 /
-# N=20000 wave, 1000-energy launch; scaled to a launch by its energies.  Kernels changed since
-# their capture have no entry (traffic null).
-DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.278e6}
+# DRAM bytes (read + write) per energy, from one ncu capture each of the n_ch=256 / N=20000 wave,
+# 1000-energy launch (the solve, and the tensor-core pole sum with its default 15 slice products);
+# scaled to a launch by its energies.  A kernel changed since its capture has no entry (traffic
+# null), and so has the pole sum with another product set.
+DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.277e6, "polesum_split": 1.653e6}
 PRODUCT_SETS = (3, 6, 10, 13, 15)
 
 
@@ -381,6 +382,8 @@ def run_ours(args):
     def traffic(kernel):
         # per-launch DRAM bytes, scaled from the capture (same kernel code, same wave shape)
         if not single_n256 or kernel not in DRAM_BYTES_PER_ENERGY_N256:
+            return None
+        if kernel == "polesum_split" and plan.slices() != 15:
             return None
         e_per_launch = wl.n_e * args.steps / kern[kernel]["launches"]
         return DRAM_BYTES_PER_ENERGY_N256[kernel] * e_per_launch
