@@ -127,6 +127,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over the job's ranks: a job's time is that of its slowest replica."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput of independent replicas (weak scaling): every rank's units over the
+    slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -351,13 +368,8 @@ def run_ours(args):
     prof = plan.profile_read()
     plan.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = world * len(wl.waves) * wl.n_e * args.steps
-    value = units / (total_ms / 1000.0)
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
+    value = job_rate(world, len(wl.waves) * wl.n_e * args.steps, total_ms / 1000.0)
 
     # open-channel counts and per-energy solve paths for the FLOP model
     n_open, flags = [], []
@@ -491,12 +503,8 @@ def run_ours(args):
                 if pis[g] is not None:
                     plan.results_photo(g, 0, wl.n_e, sig_pi=pis[g])
         barrier()
-        dt = (time.perf_counter() - t0) / e2e_steps
-        if world > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * len(wl.waves) * wl.n_e / dt, "unit": "energies/s",
+        dt = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+        e2e = {"value": job_rate(world, len(wl.waves) * wl.n_e, dt), "unit": "energies/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
 
     # the plain FP64 GPU form on a sub-mesh of the same workload that spans the whole mesh (the same
