@@ -361,7 +361,9 @@ const char* rm_last_error(void);
  * attributes; make that first call before any stream capture.  All calls
  * share the one scratch array and every call overwrites it, so calls that may
  * overlap on the GPU (different streams, or threads) race and must be
- * serialised by the caller.  Errors: rm_static_last_error().
+ * serialised by the caller.  Errors: rm_static_last_error(), the message of the last failure of
+ * this entry point in any thread (a fixed process-wide buffer, so that failing allocates nothing
+ * either; failures in two threads at once may overwrite each other's message).
  */
 #define RM_STATIC_SCRATCH_BYTES (64ll << 20)
 rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_ch, int32_t n_poles, double a,

@@ -13,8 +13,8 @@
 // that array; two small kernels of this file fill in what a plan would have
 // copied from the host (the selected channels, passed by value as a kernel
 // argument, and the channels' l clamped to [0, RM_LMAX]).
+#include <cstring>
 #include <mutex>
-#include <string>
 
 #include "rm_internal.cuh"
 
@@ -34,10 +34,23 @@ struct DeviceSetup {
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[kMaxDevices];
 
-thread_local std::string g_static_err;
+// The last failure's message: a fixed process-wide buffer (a std::string, or thread-local
+// storage in a loaded library, could allocate); concurrent failures may overwrite each other.
+std::mutex g_err_mutex;
+char g_static_err[256] = "";
 
-rm_status_t static_fail(rm_status_t s, const std::string& m) {
-  g_static_err = m;
+rm_status_t static_fail(rm_status_t s, const char* m, const char* detail = nullptr) {
+  std::lock_guard<std::mutex> lock(g_err_mutex);
+  size_t k = 0;
+  for (const char* p : {m, detail}) {
+    if (!p) continue;
+    const size_t len = std::strlen(p);
+    const size_t room = sizeof(g_static_err) - 1 - k;
+    const size_t c = len < room ? len : room;
+    std::memcpy(g_static_err + k, p, c);
+    k += c;
+  }
+  g_static_err[k] = 0;
   return s;
 }
 
@@ -61,7 +74,7 @@ rm_status_t device_setup(int dev, DeviceSetup* out) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess || p == nullptr) {
       cudaGetLastError();
-      return static_fail(RM_ERR_CUDA, std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+      return static_fail(RM_ERR_CUDA, "cudaGetSymbolAddress failed: ", cudaGetErrorString(e));
     }
     d.sm103 = (major == 10 && minor == 3);
     d.sm_count = sms;
@@ -218,7 +231,7 @@ extern "C" rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_c
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   static_setup_kernel<<<1, 256, 0, s>>>(sel, n_sel, sel_dev, l, n, l_dev, bad);
   cudaError_t e0 = cudaGetLastError();
-  if (e0 != cudaSuccess) return static_fail(RM_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e0));
+  if (e0 != cudaSuccess) return static_fail(RM_ERR_CUDA, "kernel launch failed: ", cudaGetErrorString(e0));
 
   Plan p;  // host-side description only; every pointer is inside the scratch array
   p.device = dev;
@@ -262,13 +275,13 @@ extern "C" rm_status_t rm_xsec_from_r_static(const double* R_packed, int32_t n_c
     if (e == cudaSuccess) e = launch_solve(p, w, 0, ne, R_packed + c0 * np, asym, chunk * n, so, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return static_fail(RM_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+      return static_fail(RM_ERR_CUDA, "kernel launch failed: ", cudaGetErrorString(e));
     }
   }
   return RM_OK;
 }
 
-extern "C" const char* rm_static_last_error(void) { return g_static_err.c_str(); }
+extern "C" const char* rm_static_last_error(void) { return g_static_err; }
 
 // Chunk and solve-slot counts the call would use for n_ch channels and n_sel selected channels on
 // the current device (for tests and capacity planning; no device work).  Returns RM_ERR_ARG where
