@@ -22,29 +22,55 @@ def rm():
 
 
 def test_forty_waves_against_oracle(rm):
-    # the 40-wave workload (n_ch 9..387, N = 40 n_ch) on a 600-energy mesh
+    # the 40-wave workload (n_ch 9..387, N = 40 n_ch) on a 600-energy mesh, through rm_run:
+    # per wave five energies (spread over the mesh, one just above a threshold), sigma from two
+    # initial channels and the totals, eta, the open-channel count and flags; and R per element of
+    # one energy per wave through rm_rmatrix, within the split form's bound
     wl = synth.config(4)
     E = np.linspace(0.01, 5.0, 600)
-    sel = (0,)
+    sel = (0, 1)
     with rm.Plan(wl.waves, E, prec="split_bf16", delta=0.05, sel=sel) as p:
         p.run()
         outs = []
         for g, w in enumerate(wl.waves):
-            o = rm.host_outputs(E.size, w.n, 1)
+            o = rm.host_outputs(E.size, w.n, len(sel))
             p.results(g, 0, E.size, **o)
             outs.append(o)
+        Rs = []
+        for g, w in enumerate(wl.waves):
+            e = (37 * g + 11) % E.size
+            R = np.zeros((1, w.n * (w.n + 1) // 2))
+            p.rmatrix(g, e, e + 1, R)
+            Rs.append((e, R[0]))
+    checked = 0
     for g, w in enumerate(wl.waves):
-        idx = np.array([7 + 13 * g % 580, 599 - 7 * g % 300])
+        thr = w.thresh[min(3, w.n - 1)]
+        e_thr = int(np.searchsorted(E, thr, side="right"))
+        idx = np.unique(np.array([7 + 13 * g % 580, 599 - 7 * g % 300, 150 + 5 * g, 420 - 3 * g,
+                                  min(e_thr, E.size - 1)]))
         ref = orc.sweep(w, E, sel=sel, energy_idx=idx, keep_R=False, keep_K=False)
         for t, e in enumerate(idx):
             assert outs[g]["n_open"][e] == ref["n_open"][t]
-            if ref["flags"][t] & orc.FLAG_ILLCOND:
+            assert (outs[g]["flags"][e] & orc.FLAG_NUDGED) == (ref["flags"][t] & orc.FLAG_NUDGED)
+            if ref["flags"][t] & (orc.FLAG_ILLCOND | orc.FLAG_NO_OPEN):
                 continue
-            st = ref["sig_tot"][t, 0]
-            err = np.abs(outs[g]["sig_sel"][e, 0] - ref["sig_sel"][t, 0]).max() / st
-            assert err <= 1e-8, (g, w.n, e, err)
+            for q in range(len(sel)):
+                st = ref["sig_tot"][t, q]
+                if st == 0:
+                    assert np.all(outs[g]["sig_sel"][e, q] == 0)
+                    continue
+                err = np.abs(outs[g]["sig_sel"][e, q] - ref["sig_sel"][t, q]).max() / st
+                assert err <= 1e-8, (g, w.n, e, q, err)
+                assert abs(outs[g]["sig_tot"][e, q] - st) <= 1e-8 * st
             d = outs[g]["eigsum"][e] - ref["eta"][t]
             assert abs(np.mod(d + np.pi, 2 * np.pi) - np.pi) <= 1e-7, (g, e)
+            checked += 1
+        e, Rg = Rs[g]
+        Ro = orc.rmatrix(w.W, w.poles, orc.nudge_energies(E[e:e + 1], w.poles, w.thresh)[0][0], w.a)
+        d = np.abs(1.0 / (w.poles - orc.nudge_energies(E[e:e + 1], w.poles, w.thresh)[0][0]))
+        bound = 4e-7 * (np.abs(w.W) * d[None, :]) @ np.abs(w.W).T / (2.0 * w.a) + 1e-300
+        assert np.all(np.abs(orc.unpack_upper(Rg, w.n) - Ro) <= bound), (g, e)
+    assert checked >= 150
 
 
 def test_graph_replay_and_launch_count(rm):
