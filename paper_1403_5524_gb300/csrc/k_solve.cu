@@ -139,13 +139,18 @@ struct Red {
 };
 
 // Block-wide argmax of Ops::mag over panel column j, rows [j, rows); ties -> smallest row.
+// A NaN counts as the largest magnitude, and the result always lies in [j, rows): every later
+// index (the row interchanges, the permutation of the unit right-hand sides) comes from it, so
+// a column of NaN or garbage (an R-matrix a failed pole sum left unwritten) cannot send them
+// outside the matrix; such an energy ends with NaN outputs instead.
 template <typename T>
 __device__ int panel_argmax(const T* panel, int rows, int j, Red* red) {
   constexpr int NB = Blk<T>::NB;
   double best = -1.0;
   int bidx = rows;
   for (int r = j + threadIdx.x; r < rows; r += NT) {
-    const double v = Ops<T>::mag(panel[r * NB + j]);
+    double v = Ops<T>::mag(panel[r * NB + j]);
+    if (v != v) v = INFINITY;
     if (v > best) { best = v; bidx = r; }
   }
 #pragma unroll
@@ -162,8 +167,9 @@ __device__ int panel_argmax(const T* panel, int rows, int j, Red* red) {
     int bi = red->i[0];
     for (int q = 1; q < NWARP; ++q)
       if (red->v[q] > b || (red->v[q] == b && red->i[q] < bi)) { b = red->v[q]; bi = red->i[q]; }
+    if (bi < j || bi >= rows) bi = j;  // nothing compared above -1 (rows <= j cannot occur)
     red->piv = bi;
-    // one reciprocal per pivot, shared by the block (bi < rows whenever rows > j)
+    // one reciprocal per pivot, shared by the block
     const T pv = (bi < rows) ? panel[bi * NB + j] : Ops<T>::zero();
     Ops<T>::put(red->pinv, (Ops<T>::mag(pv) == 0.0) ? Ops<T>::zero() : Ops<T>::inv(pv));
   }

@@ -168,3 +168,27 @@ def test_static_entry_rejects_oversize(lib):
     assert code == 1
     assert b"640" in lib.rm_static_last_error()
     assert layout(lib, 641, 1)[0] == 1 and layout(lib, 640, 1)[0] == 0
+
+
+def test_static_entry_survives_nan_r(lib):
+    # the entry point does not validate the caller's R-matrices: an energy whose R is NaN must
+    # come out as NaN (flagged ILLCOND by its LU), never as an index outside the workspace, and
+    # the other energies of the call must be unaffected
+    dev = torch.device("cuda:0")
+    wl = synth.small(24, 11, 300, 60)
+    w = wl.waves[0]
+    sel = [0, 1]
+    R, K0, ref = plan_reference(wl, sel, dev)
+    bad = [3, 17, 41]
+    Rn = R.clone()
+    Rn[bad] = float("nan")
+    E = torch.from_numpy(wl.energies).to(dev)
+    g = static_call(lib, Rn, w, E, sel, dev)
+    good = np.array([e for e in range(wl.n_e) if e not in bad])
+    for e in bad:
+        if g["no"][e] > 0:
+            assert np.isnan(g["eta"][e]) and np.all(np.isnan(g["st"][e]))
+    keep = {"eigsum": ref["eigsum"][good], "sig_tot": ref["sig_tot"][good], "sig_sel": ref["sig_sel"][good]}
+    check_against({k: v[good] for k, v in g.items()}, K0[good], keep)
+    g2 = static_call(lib, R, w, E, sel, dev)  # and the next call is clean
+    check_against(g2, K0, ref)
