@@ -104,6 +104,55 @@ struct Ops<cplx> {
   __device__ static cplx get(const double* d) { return cplx{d[0], d[1]}; }
 };
 
+// Double-float: a value hi + lo of two FP32 numbers (about 48 bits), with error-free products
+// (FMA) and sums (Knuth's TwoSum) on the FP32 pipe, which GB300 runs about 64 times faster than
+// its FP64 pipe.  Used for the one factorisation whose results only decide signs: the inertia
+// LDL^T of S'' (sym_xsec).  Same size as a double, so it factors in place of the FP64 matrix.
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl df_quick(float a, float b) {  // |a| >= |b| (or a = 0): a + b exactly
+  const float s = __fadd_rn(a, b);
+  return dfl{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_from(double v) {
+  const float h = __double2float_rn(v);
+  return dfl{h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl x) { return (double)x.hi + (double)x.lo; }
+
+template <>
+struct Ops<dfl> {
+  __device__ static dfl zero() { return dfl{0.0f, 0.0f}; }
+  __device__ static dfl one() { return dfl{1.0f, 0.0f}; }
+  __device__ static double mag(dfl x) { return fabs(df_to(x)); }
+  __device__ static dfl inv(dfl x) {
+    const float r = __fdiv_rn(1.0f, x.hi);
+    float e = __fmaf_rn(-x.hi, r, 1.0f);  // exact residual of the FP32 reciprocal
+    e = __fmaf_rn(-x.lo, r, e);
+    return df_quick(r, __fmul_rn(r, e));
+  }
+  __device__ static dfl mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);  // exact rounding error of the product
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return df_quick(p, e);
+  }
+  // acc - a b: the product's error-free part and the two high parts summed by TwoSum
+  __device__ static dfl fms(dfl acc, dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);
+    pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, pe));
+    const float s = __fsub_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(-p, bb));
+    return df_quick(s, __fadd_rn(err, __fsub_rn(acc.lo, pe)));
+  }
+  __device__ static dfl fma_acc(dfl acc, dfl a, dfl b) { return fms(acc, dfl{-a.hi, -a.lo}, b); }
+  __device__ static void put(double* d, dfl x) { d[0] = x.hi; d[1] = x.lo; }
+  __device__ static dfl get(const double* d) { return dfl{(float)d[0], (float)d[1]}; }
+};
+
 // Panel width: 16 columns for the real LU, 8 for the complex one, so that a
 // panel row is 128 bytes either way and both LUs do the same FMAs per byte of
 // trailing-matrix traffic (16 real or 8 complex multiply-adds per element).
@@ -116,6 +165,7 @@ constexpr int TILE_BYTES = Blk<double>::NB * TC * 8;  // NB x TC elements, eithe
 constexpr int TRI_BYTES = Blk<float>::NB * Blk<float>::NB * 4;  // the largest of the three types
 static_assert(Blk<cplx>::NB * TC * (int)sizeof(cplx) == TILE_BYTES, "tile bytes");
 static_assert(Blk<float>::NB * TC * (int)sizeof(float) == TILE_BYTES, "tile bytes");
+static_assert(sizeof(dfl) == sizeof(double) && Blk<dfl>::NB == Blk<double>::NB, "double-float in place of FP64");
 
 // smallest power of two >= min(TC, w), at least 1
 __device__ __forceinline__ int tile_width_pow2(int w) {
@@ -1048,13 +1098,16 @@ __device__ bool mixed_matching(const SolveArgs& g, double* A, int n, int m, int 
 // row p, and scales like the matrix under a diagonal congruence), max_p D_pp
 // must stay within 1e4 of the largest entry of M for the closed elimination,
 // which feeds Z (a backward error of at most about n u 1e4, below the split
-// pole sum's error in R), and within 1e6 of that of S'' for the inertia (an
-// eigenvalue within about 3e-8 of zero would be needed to flip a sign), and
-// every pivot must keep |d_p| >= 1e-8 D_pp, far above its rounding error of
-// about n u D_pp, so that no pivot is lost to cancellation.  An energy that
-// fails a test is solved by the LU path.
+// pole sum's error in R).  S'' decides only a sign, so it is factored in
+// double-float (pairs of floats, unit roundoff u_df = 2^-46 or so, on the
+// FP32 pipe): its growth must stay within 1e4 of max|S''|, which keeps the
+// backward error at about n u_df 1e4 and an eigenvalue would need to lie
+// within about 4e-8 of zero (relative to max|S''|) to flip a sign.  Every
+// pivot must keep |d_p| >= 1e-8 D_pp, far above its rounding error of about
+// n u D_pp, so that no pivot is lost to cancellation.  An energy that fails a
+// test is solved by the LU path.
 constexpr double SYM_GROWTH_MAX = 1e4;          // closed elimination: max_p D_pp / max|M|
-constexpr double SYM_GROWTH_MAX_INERTIA = 1e6;  // S'': max_p D_pp / max|S''|
+constexpr double SYM_GROWTH_MAX_INERTIA = 1e4;  // S'' (double-float): max_p D_pp / max|S''|
 constexpr double SYM_PIVOT_MIN = 1e-8;          // either: |d_p| / D_pp
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1210,8 +1263,19 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
     }
   }
   sm = block_max(sm, red);
-  ldl_solve<double>(As, no, no, ld, reinterpret_cast<double*>(panel_b), reinterpret_cast<double*>(tile_b),
-                    reinterpret_cast<double*>(tmp_b), reinterpret_cast<double*>(tri_b), st);
+  // S'' decides only signs (its inertia), with pivot and growth tests that leave a margin far
+  // above double-float rounding (|d_p| >= 1e-8 D_pp against a backward error of about
+  // n 2^-46 D_pp), so it is factored in double-float on the FP32 pipe, in place (same size),
+  // then turned back into FP64 for the tests and the sign count
+  dfl* Ad = reinterpret_cast<dfl*>(As);
+  for (int p = t >> 5; p < no; p += NWARP)
+    for (int q = lane; q <= p; q += 32) Ad[(int64_t)p * ld + q] = df_from(As[(int64_t)p * ld + q]);
+  __syncthreads();
+  ldl_solve<dfl>(Ad, no, no, ld, reinterpret_cast<dfl*>(panel_b), reinterpret_cast<dfl*>(tile_b),
+                 reinterpret_cast<dfl*>(tmp_b), reinterpret_cast<dfl*>(tri_b), st);
+  for (int p = t >> 5; p < no; p += NWARP)
+    for (int q = lane; q <= p; q += 32) As[(int64_t)p * ld + q] = df_to(Ad[(int64_t)p * ld + q]);
+  __syncthreads();
   double growth_s, piv_s;
   ldl_check(As, no, no, ld, red, growth_s, piv_s);
   growth_s /= sm;
