@@ -1099,16 +1099,19 @@ __device__ bool mixed_matching(const SolveArgs& g, double* A, int n, int m, int 
 // must stay within 1e4 of the largest entry of M for the closed elimination,
 // which feeds Z (a backward error of at most about n u 1e4, below the split
 // pole sum's error in R).  S'' decides only a sign, so it is factored in
-// double-float (pairs of floats, unit roundoff u_df = 2^-46 or so, on the
-// FP32 pipe): its growth must stay within 1e4 of max|S''|, which keeps the
-// backward error at about n u_df 1e4 and an eigenvalue would need to lie
-// within about 4e-8 of zero (relative to max|S''|) to flip a sign.  Every
-// pivot must keep |d_p| >= 1e-8 D_pp, far above its rounding error of about
-// n u D_pp, so that no pivot is lost to cancellation.  An energy that fails a
-// test is solved by the LU path.
-constexpr double SYM_GROWTH_MAX = 1e4;          // closed elimination: max_p D_pp / max|M|
-constexpr double SYM_GROWTH_MAX_INERTIA = 1e4;  // S'' (double-float): max_p D_pp / max|S''|
-constexpr double SYM_PIVOT_MIN = 1e-8;          // either: |d_p| / D_pp
+// double-float first (pairs of floats, unit roundoff u_df = 2^-46 or so, on
+// the FP32 pipe): its growth must stay within 1e4 of max|S''|, which keeps the
+// backward error at about n u_df 1e4, so an eigenvalue would need to lie
+// within about 4e-8 of zero (relative to max|S''|) to flip a sign.  If that
+// fails, S'' is formed again and factored in FP64, where growth within 1e6
+// gives the same margin (n u 1e6, about 3e-8).  Every pivot must keep
+// |d_p| >= 1e-8 D_pp, far above its rounding error of about n u D_pp, so that
+// no pivot is lost to cancellation.  An energy that fails a test is solved by
+// the LU path.
+constexpr double SYM_GROWTH_MAX = 1e4;             // closed elimination: max_p D_pp / max|M|
+constexpr double SYM_GROWTH_MAX_INERTIA_DF = 1e4;  // S'' in double-float: max_p D_pp / max|S''|
+constexpr double SYM_GROWTH_MAX_INERTIA = 1e6;     // S'' in FP64 (the retry)
+constexpr double SYM_PIVOT_MIN = 1e-8;             // any of them: |d_p| / D_pp
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -1243,26 +1246,41 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
   // ------------------------------------- S'' = V G V - diag(c c' / (a |h'|^2)), in place, and its inertia
   double* As = A + (int64_t)nc * ld + nc;
   double* vsc = reinterpret_cast<double*>(tile_b);  // V_jj = c'_j / |h'_j| (tile area free until the LDL^T)
-  for (int j = t; j < no; j += NT) {
-    const double cp = lam[j] * c[j];
-    vsc[j] = cp / sqrt(cp * cp + sp[j] * sp[j]);
-  }
-  __syncthreads();
-  double sm = 0.0;
-  for (int p = t >> 5; p < no; p += NWARP) {
-    const int i = no - 1 - p;
-    for (int q = lane; q <= p; q += 32) {
-      const int j = no - 1 - q;
-      double v = vsc[i] * As[(int64_t)p * ld + q] * vsc[j];
-      if (q == p) {
-        const double cp = lam[i] * c[i];
-        v -= c[i] * cp / (g.a * (cp * cp + sp[i] * sp[i]));
-      }
-      As[(int64_t)p * ld + q] = v;
-      sm = fmax(sm, fabs(v));
+  // from_z: S_oo taken from Z's real part (C, not yet factored) instead of the eliminated block
+  auto form_s2 = [&](bool from_z) {
+    for (int j = t; j < no; j += NT) {
+      const double cp = lam[j] * c[j];
+      vsc[j] = cp / sqrt(cp * cp + sp[j] * sp[j]);
     }
-  }
-  sm = block_max(sm, red);
+    __syncthreads();
+    double m = 0.0;
+    for (int p = t >> 5; p < no; p += NWARP) {
+      const int i = no - 1 - p;
+      for (int q = lane; q <= p; q += 32) {
+        const int j = no - 1 - q;
+        double x = from_z ? C[(int64_t)j * g.ldC + i].re : As[(int64_t)p * ld + q];
+        double v;
+        if (q == p) {
+          const double cp = lam[i] * c[i];
+          const double den = g.a * (cp * cp + sp[i] * sp[i]);
+          if (from_z) x += (c[i] * cp + s[i] * sp[i]) / den;  // undo Z's diagonal term h / (a h')
+          v = vsc[i] * x * vsc[j] - c[i] * cp / den;
+        } else {
+          v = vsc[i] * x * vsc[j];
+        }
+        As[(int64_t)p * ld + q] = v;
+        m = fmax(m, fabs(v));
+      }
+    }
+    return block_max(m, red);
+  };
+  double growth_s, piv_s;
+  auto negatives = [&]() {
+    int neg = 0;
+    for (int p = t; p < no; p += NT) neg += (As[(int64_t)p * ld + p] < 0.0) ? 1 : 0;
+    return block_sum((double)neg, red);
+  };
+  double sm = form_s2(false);
   // S'' decides only signs (its inertia), with pivot and growth tests that leave a margin far
   // above double-float rounding (|d_p| >= 1e-8 D_pp against a backward error of about
   // n 2^-46 D_pp), so it is factored in double-float on the FP32 pipe, in place (same size),
@@ -1276,14 +1294,20 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
   for (int p = t >> 5; p < no; p += NWARP)
     for (int q = lane; q <= p; q += 32) As[(int64_t)p * ld + q] = df_to(Ad[(int64_t)p * ld + q]);
   __syncthreads();
-  double growth_s, piv_s;
   ldl_check(As, no, no, ld, red, growth_s, piv_s);
   growth_s /= sm;
-  int neg = 0;
-  for (int p = t; p < no; p += NT) neg += (As[(int64_t)p * ld + p] < 0.0) ? 1 : 0;
-  const double negs = block_sum((double)neg, red);
-  const bool ok = (growth_c <= SYM_GROWTH_MAX) && (growth_s <= SYM_GROWTH_MAX_INERTIA) && (piv_c >= SYM_PIVOT_MIN) &&
-                  (piv_s >= SYM_PIVOT_MIN);
+  double negs = negatives();
+  const bool ok_c = (growth_c <= SYM_GROWTH_MAX) && (piv_c >= SYM_PIVOT_MIN);
+  if (ok_c && !(growth_s <= SYM_GROWTH_MAX_INERTIA_DF && piv_s >= SYM_PIVOT_MIN)) {
+    // the double-float factorisation is not trusted for this S'': form it again and factor in FP64
+    sm = form_s2(true);
+    ldl_solve<double>(As, no, no, ld, reinterpret_cast<double*>(panel_b), reinterpret_cast<double*>(tile_b),
+                      reinterpret_cast<double*>(tmp_b), reinterpret_cast<double*>(tri_b), st);
+    ldl_check(As, no, no, ld, red, growth_s, piv_s);
+    growth_s /= sm;
+    negs = negatives();
+  }
+  const bool ok = ok_c && (growth_s <= SYM_GROWTH_MAX_INERTIA) && (piv_s >= SYM_PIVOT_MIN);
   if (!ok) return false;  // uniform: the values come from block reductions
   // ------------------------------------- complex LDL^T of Z, x = Z^-1 e_sel
   ldl_solve<cplx>(C, no, mc, g.ldC, reinterpret_cast<cplx*>(panel_b), reinterpret_cast<cplx*>(tile_b),
