@@ -384,6 +384,8 @@ def run_ours(args):
         n_open.append(no)
         flags.append(fl)
     lu_fallback = int(sum(np.count_nonzero(f & 64) for f in flags))
+    # outgoing-wave solve: energies whose S'' inertia was factored in FP64 after the double-float checks failed
+    s2_fp64 = int(sum(np.count_nonzero((f & 32) != 0) for f in flags))
     pole_flops, solve_flops, df_flops = algorithmic_flops(wl, n_open, flags, len(sel), args.solve)
     kern = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
@@ -590,7 +592,8 @@ def run_ours(args):
                 "impl_config": {"prec": args.prec, "slice_products": plan.slices(),
                                 "energy_chunk": plan.info(0)["chunk"], "tc_cluster": "%dx%d" % plan.cluster(),
                                 "solve": args.solve, "fp64_fallback_energies": fallback,
-                                "lu_path_energies": lu_fallback if args.solve == "fp64" else None},
+                                "lu_path_energies": lu_fallback if args.solve == "fp64" else None,
+                                "s2_fp64_energies": s2_fp64 if args.solve == "fp64" else None},
                 "roofline": roof, "roofline_tensor": roof_tc, "kernels": kern, "gpu_launches": int(launches),
                 "fp64_gpu": fp64, "k_formed": k_formed, "post_convolve": post,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "errors": errors}

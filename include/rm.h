@@ -95,7 +95,10 @@ typedef enum {
                                 iteration cap for some channel (z > 0 only), or (rm_xsec_from_r_static
                                 only) a channel's l lay outside [0, RM_LMAX]; outputs are unreliable */
 #define RM_FLAG_FP64 32u     /* solve_prec = RM_SOLVE_MIXED: the FP32 refinement did not converge (or hit a
-                                zero pivot) and the matching system was solved in FP64 instead */
+                                zero pivot) and the matching system was solved in FP64 instead;
+                                RM_SOLVE_FP64 (rm_run / rm_xsec): the double-float LDL^T of S'' that gives
+                                the sign of det S_oo failed its growth or pivot check and S'' was
+                                factored in FP64 instead (same results) */
 #define RM_FLAG_LU 64u       /* rm_run / rm_xsec with solve_prec = RM_SOLVE_FP64: the outgoing-wave
                                 factorisation failed its growth or pivot check and the energy was solved
                                 by LU with partial pivoting instead (same results, more flops) */
@@ -116,6 +119,8 @@ typedef enum {
    eliminated by a real LDL^T, then one complex symmetric LDL^T of
    Z = G - diag(h / (a h')), h = c + i s, on the open channels (about half the flops; an energy
    whose real elimination shows large growth or a tiny pivot goes through LU, RM_FLAG_LU);
+   the sign of det S_oo comes from the inertia of S'' = V S_oo V (V = diag(c' / |h'|)), factored
+   in double-float on the FP32 pipe, or in FP64 where that fails its checks (RM_FLAG_FP64);
    dipole waves' photoionisation amplitudes come from one more right-hand side of Z.
    FP64_LU: the LU path for every energy.  MIXED: LU in FP32, then iterative refinement
    with residuals r = -B - M Y in double-float (FP32 hi + lo, error-free products and sums, about

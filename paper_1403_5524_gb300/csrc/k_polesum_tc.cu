@@ -43,7 +43,7 @@ constexpr int BM = 128;                 // pairs per tile: 8 i-channels x 16 j-c
 constexpr int BN = 128;                 // energies per tile
 constexpr int KS = 32;                  // poles per k-step (64-byte BF16 rows)
 constexpr int NWORK = 16;               // producer / drain warps
-constexpr int NTHREADS = (NWORK + 2) * 32;  // + MMA issue warp + cluster copy warp
+constexpr int NTHREADS = (NWORK + 3) * 32;  // + MMA issue warp + cluster copy warp + D-slice loader warp
 constexpr int DRAIN_KSTEPS = 64;        // drain every 2048 poles
 constexpr int SLICE_BYTES = BM * KS * 2;          // 8 KB: 128 rows x 64 B
 constexpr int WI_FLOATS = 16 * KS;   // 8 channels x (hi, lo) rows
@@ -461,6 +461,40 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       }
     }
     __syncwarp();
+  } else if (warp == NWORK + 2) {
+    // ------------------------------------- D-slice loads (1 thread; D by TMA only)
+    // A k-step's D slices are fetched as soon as their buffer is free (RING: the MMAs of step
+    // j - 2 are done; otherwise the stage's), independently of the producers, which may then run
+    // up to the full stage depth ahead of the MMAs.
+    if (DT && lane == 0) {
+      int d_last[BST];
+#pragma unroll
+      for (int q = 0; q < BST; ++q) d_last[q] = -1;
+      for (int j = 0; j < nK; ++j) {
+        const int q = j % BST;
+        bool free_ = true;
+        if (j >= BST) {
+          const uint32_t par = (uint32_t)(((j / BST) - 1) & 1);
+          if constexpr (RING) free_ = mbar_wait(emptyB + q, par, abort_flag, g.wait_budget);
+          else if constexpr (CL > 1) free_ = mbar_wait_cluster(empty + q, par, abort_flag, g.wait_budget);
+          else free_ = mbar_wait(empty + q, par, abort_flag, g.wait_budget);
+        }
+        if (!free_) break;
+        uint8_t* dst = RING ? smem + Geo::B_RING + q * B_BYTES : smem + q * STAGE_STRIDE + A_BYTES;
+        mbar_arrive_expect_tx(dfull + q, (uint32_t)B_BYTES);
+        tma_load_3d(dst, map_d, dfull + q, j * KS, n0, 0);
+        d_last[q] = j;
+      }
+      // no D copy may still be landing when the CTA exits (completed ones return at once)
+      const long long cleanup = 400000000LL;
+      for (int q = 0; q < BST; ++q) {
+        if (d_last[q] < 0) continue;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(dfull + q, (uint32_t)((d_last[q] / BST) & 1)) && clock64() - t0 < cleanup) {
+        }
+      }
+    }
+    __syncwarp();
   } else {
     // -------------------------------------------------- producers and drains
     const int w = warp;
@@ -513,14 +547,10 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
 #pragma unroll
     for (int c = 0; c < 32; ++c) Vh[c] = Vl[c] = 0.0f;
     bool ok = true;
-    const bool dloader = DT && w == 0 && lane == 0;
-    int d_last[STAGES];
-#pragma unroll
-    for (int q = 0; q < STAGES; ++q) d_last[q] = -1;
     // Every way out of this loop is taken by whole warps, so that no lane is left at the
     // __syncwarp below while another has gone on to the final barrier: the waits are polled by
     // all lanes of a converged warp in the same instructions (the same barrier phase, abort flag
-    // and clock), and the one wait made by a single lane (the D loader's) is broadcast first.
+    // and clock).
     for (int j = 0; j < nK && ok; ++j) {
       const int s = j % STAGES;
       if (j >= STAGES) {
@@ -529,29 +559,6 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           got = mbar_wait_cluster(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, g.wait_budget);
         else got = mbar_wait(empty + s, (uint32_t)(((j / STAGES) - 1) & 1), abort_flag, g.wait_budget);
         if (!got) {
-          ok = false;
-          break;
-        }
-      }
-      if (DT && w == 0) {
-        bool dl_ok = true;
-        if (lane == 0) {
-          if constexpr (RING) {
-            // the D buffer of step j - 2 is free once that step's MMAs are done: fetch this step's D
-            const int q = j % BST;
-            if (j >= BST) dl_ok = mbar_wait(emptyB + q, (uint32_t)(((j / BST) - 1) & 1), abort_flag, g.wait_budget);
-            if (dl_ok) {
-              mbar_arrive_expect_tx(dfull + q, (uint32_t)B_BYTES);
-              tma_load_3d(smem + Geo::B_RING + q * B_BYTES, map_d, dfull + q, j * KS, n0, 0);
-              d_last[q] = j;
-            }
-          } else {  // the stage's B area is free: fetch this k-step's D slices
-            mbar_arrive_expect_tx(dfull + s, (uint32_t)B_BYTES);
-            tma_load_3d(smem + s * STAGE_STRIDE + A_BYTES, map_d, dfull + s, j * KS, n0, 0);
-            d_last[s] = j;
-          }
-        }
-        if (!__shfl_sync(0xffffffffu, dl_ok, 0)) {
           ok = false;
           break;
         }
@@ -659,17 +666,6 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty);
-      }
-    }
-    if (dloader) {
-      // no D copy may still be landing when the CTA exits (completed ones return at once)
-      const long long cleanup = 400000000LL;
-      for (int q = 0; q < STAGES; ++q) {
-        if (d_last[q] < 0) continue;
-        const long long t0 = clock64();
-        while (!mbar_try_wait(dfull + q, (uint32_t)((d_last[q] / (RING ? BST : STAGES)) & 1)) &&
-               clock64() - t0 < cleanup) {
-        }
       }
     }
     // ------------------------------------------------------------- epilogue

@@ -1306,6 +1306,7 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
     ldl_check(As, no, no, ld, red, growth_s, piv_s);
     growth_s /= sm;
     negs = negatives();
+    fl |= RM_FLAG_FP64;
   }
   const bool ok = ok_c && (growth_s <= SYM_GROWTH_MAX_INERTIA) && (piv_s >= SYM_PIVOT_MIN);
   if (!ok) return false;  // uniform: the values come from block reductions

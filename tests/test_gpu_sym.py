@@ -13,7 +13,9 @@ mod 2 pi).  Cases: a contiguous block of the n_ch = 64 mesh (thresholds up to
 closed pivot vanishes (must go through LU, RM_FLAG_LU), one where c'_0 = 0
 (K is regular there, but M and the unit-right-hand-side LU form divide by c'),
 photoionisation against the LU form, the largest channel count (640, FP64 and
-split BF16), and the two sides of a K pole (the inertia of S'' flips there).
+split BF16), the two sides of a K pole (the inertia of S'' flips there), and the
+energies of the n_ch = 256 mesh whose S'' fails the double-float checks and is
+factored again in FP64 (RM_FLAG_FP64).
 """
 import math
 
@@ -27,6 +29,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FLAG_LU = 64
+FLAG_FP64 = 32
 TOL = 1e-9
 
 
@@ -72,7 +75,7 @@ def test_config2_block_matches_lu_path(rm):
     a = run(rm, sub, "fp64", sel=(0, 3))
     b = run(rm, sub, "fp64_lu", sel=(0, 3))
     assert np.array_equal(a["n_open"], b["n_open"])
-    assert np.array_equal(a["flags"] & ~np.uint8(FLAG_LU), b["flags"])
+    assert np.array_equal(a["flags"] & ~np.uint8(FLAG_LU | FLAG_FP64), b["flags"])
     assert np.count_nonzero(a["flags"] & FLAG_LU) < sub.n_e // 20  # the LU fallback stays rare
     close(a, b)
     idx = np.arange(0, sub.n_e, 37)
@@ -244,3 +247,24 @@ def test_eta_across_a_k_pole(rm):
     ref = orc.sweep(w, E, sel=(0, 1), keep_R=False, keep_K=False)
     assert not np.any(a["flags"] & FLAG_LU)
     close(a, as_ref(ref), tol=1e-7)
+
+
+def test_s2_fp64_retry_energies(rm):
+    # S'' gives only the sign of det S_oo (eta mod 2 pi), so its LDL^T runs in double-float; where
+    # that fails its growth (1e4) or pivot check, S'' is formed again from Z and factored in FP64
+    # (RM_FLAG_FP64), a few energies in a thousand of the n_ch = 256 mesh.  Those energies must
+    # keep the outgoing-wave path (not LU) and match the LU path and the oracle like the rest: a
+    # wrong sign count would put eta off by pi.
+    wl = synth.config(3)
+    a = run(rm, wl, "fp64", prec="split_bf16")
+    retry = np.flatnonzero(a["flags"] & FLAG_FP64)
+    assert 0 < retry.size < wl.n_e // 100, retry.size
+    assert not np.any(a["flags"][retry] & FLAG_LU)
+    b = run(rm, wl, "fp64_lu", prec="split_bf16")  # the same R, solved by LU
+    lu_ok = retry[(b["flags"][retry] & orc.FLAG_ILLCOND) == 0]
+    close(a, b, idx=lu_ok, tol=1e-8)
+    pick = retry[np.linspace(0, retry.size - 1, 4).astype(int)]
+    ref = orc.sweep(wl.waves[0], wl.energies, sel=(0,), energy_idx=pick, keep_R=False, keep_K=False)
+    keep = np.array([t for t in range(pick.size) if not ref["flags"][t] & orc.FLAG_ILLCOND], dtype=np.int64)
+    assert keep.size
+    close({k: v[pick[keep]] for k, v in a.items()}, {k: v[keep] for k, v in as_ref(ref).items()}, tol=1e-8)
