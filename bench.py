@@ -35,7 +35,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU; the measured 
 # 1000-energy launch (the solve, and the tensor-core pole sum with its default 15 slice products);
 # scaled to a launch by its energies.  A kernel changed since its capture has no entry (traffic
 # null), and so has the pole sum with another product set.
-DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.777e6, "polesum_split": 1.653e6}
+DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.777e6, "polesum_split": 1.886e6}
 PRODUCT_SETS = (3, 6, 10, 13, 15)
 
 
