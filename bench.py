@@ -286,9 +286,17 @@ def oracle_sample(wl, sel, budget_s=15.0, max_e=64, keep=False):
 
 
 def workload_config(wl, stride, sel):
-    """The workload keys of the JSON line's config, the same in both arms."""
+    """The workload keys of the JSON line's config."""
     return {"workload": wl.name, "mesh_stride": stride, "energies_per_step": wl.n_e, "waves": len(wl.waves),
             "n_ch": [w.n for w in wl.waves][:4], "n_poles": [w.N for w in wl.waves][:4], "n_sel": len(sel)}
+
+
+def run_config(wl, stride, sel, world):
+    """The JSON line's config, identical in both arms: the workload, the cache policy of the timed
+    GPU steps (the oracle arm's working set, W and R of the mesh, is far beyond its host caches
+    too) and the replica layout."""
+    return dict(workload_config(wl, stride, sel), l2="flushed (512 MB write) between timed steps",
+                parallelism=f"replicas x{world}")
 
 
 def run_reference(args):
@@ -309,8 +317,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "energies/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)",
-            "config": workload_config(wl, stride, sel),
+            "data": "synthetic (seeded, workload distributions of the paper's problem class)",
+            "config": run_config(wl, stride, sel, world),
             "sample": f"{per} evenly spaced energies of the mesh per step",
             "cpu_baseline": {"value": val, "unit": "energies/s", "cores": cores, "kind": "oracle",
                              "sample": f"{total_e} energies over {args.steps} steps"},
@@ -587,8 +595,7 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.prec == "fp64" else "bf16-split+f64",
                 "data": "synthetic (seeded, workload distributions of the paper's problem class)",
-                "config": dict(workload_config(wl, stride, sel),
-                               l2="flushed (512 MB write) between timed steps", parallelism=f"replicas x{world}"),
+                "config": run_config(wl, stride, sel, world),
                 "impl_config": {"prec": args.prec, "slice_products": plan.slices(),
                                 "energy_chunk": plan.info(0)["chunk"], "tc_cluster": "%dx%d" % plan.cluster(),
                                 "solve": args.solve, "fp64_fallback_energies": fallback,
