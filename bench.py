@@ -32,9 +32,9 @@ from paper_1403_5524_gb300 import synth  # noqa: E402
 METRIC = "energies/sec (R+K+σ) split-precision vs FP64 GPU at n_ch=256; max rel err"
 FP64_NOMINAL_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU; the measured probe is the peak used
 # DRAM bytes (read + write) per energy, from one ncu capture each of the n_ch=256 / N=20000 wave,
-# 1000-energy launch (the solve, and the tensor-core pole sum with its default 15 slice products);
-# scaled to a launch by its energies.  A kernel changed since its capture has no entry (traffic
-# null), and so has the pole sum with another product set.
+# 1000-energy launch (the solve; the tensor-core pole sum with its default 15 slice products, as
+# one-SM MMAs); scaled to a launch by its energies.  A kernel changed since its capture has no
+# entry (traffic null), and so has the pole sum with another product set or MMA form.
 DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.777e6, "polesum_split": 1.886e6}
 PRODUCT_SETS = (3, 6, 10, 13, 15)
 
@@ -116,6 +116,8 @@ def parse():
     ap.add_argument("--dipole", action="store_true",
                     help="photoionisation: give every wave a bound-free dipole vector (sigma_PI per energy)")
     ap.add_argument("--cluster", default="", help="tensor-core cluster shape CXxCY (default: autotuned)")
+    ap.add_argument("--mma-pair", type=int, default=0, choices=[-1, 0, 1],
+                    help="1 x 2 clusters with 15 products: 0/1 = 2-SM MMAs (cta_group::2), -1 = one-SM MMAs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--k-formed", type=int, default=1,
                     help="1: also time the sweep with the K-matrix formed by LU (solve fp64_lu), as k_formed")
@@ -347,7 +349,7 @@ def run_ours(args):
     dE = torch.from_numpy(wl.energies).to(dev)
     cluster = tuple(int(x) for x in args.cluster.split("x")) if args.cluster else None
     plan = rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream, autotune=True,
-                   chunk=args.chunk, cluster=cluster, solve=args.solve, slices=args.slices)
+                   chunk=args.chunk, cluster=cluster, solve=args.solve, slices=args.slices, mma_pair=args.mma_pair)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
     def barrier():
@@ -409,7 +411,7 @@ def run_ours(args):
         # per-launch DRAM bytes, scaled from the capture (same kernel code, same wave shape)
         if not single_n256 or kernel not in DRAM_BYTES_PER_ENERGY_N256:
             return None
-        if kernel == "polesum_split" and plan.slices() != 15:
+        if kernel == "polesum_split" and (plan.slices() != 15 or plan.mma_pair()):
             return None
         e_per_launch = wl.n_e * args.steps / kern[kernel]["launches"]
         return DRAM_BYTES_PER_ENERGY_N256[kernel] * e_per_launch
@@ -555,7 +557,7 @@ def run_ours(args):
     k_formed = None
     if args.solve == "fp64" and args.k_formed and rank == 0:
         with rm.Plan(dwaves, dE, prec=args.prec, delta=wl.delta, sel=sel, stream=stream, solve="fp64_lu",
-                     cluster=plan.cluster() if args.prec != "fp64" else None) as pk:
+                     cluster=plan.cluster() if args.prec != "fp64" else None, mma_pair=args.mma_pair) as pk:
             pk.run()
             torch.cuda.synchronize(dev)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -586,7 +588,7 @@ def run_ours(args):
             ref_x = orc.sweep(wl.waves[0], extra, sel=sel)
             with rm.Plan(dwaves[:1], torch.from_numpy(extra).to(dev), prec=args.prec, delta=wl.delta, sel=sel,
                          stream=stream, solve=args.solve, slices=args.slices,
-                         cluster=plan.cluster() if args.prec != "fp64" else None) as px:
+                         cluster=plan.cluster() if args.prec != "fp64" else None, mma_pair=args.mma_pair) as px:
                 errors = accuracy(plan, wl, sel, idx, ref, extra, px, ref_x)
 
     if rank == 0:
@@ -598,6 +600,7 @@ def run_ours(args):
                 "config": run_config(wl, stride, sel, world),
                 "impl_config": {"prec": args.prec, "slice_products": plan.slices(),
                                 "energy_chunk": plan.info(0)["chunk"], "tc_cluster": "%dx%d" % plan.cluster(),
+                                "tc_mma_pair": plan.mma_pair() if args.prec != "fp64" else False,
                                 "solve": args.solve, "fp64_fallback_energies": fallback,
                                 "lu_path_energies": lu_fallback if args.solve == "fp64" else None,
                                 "s2_fp64_energies": s2_fp64 if args.solve == "fp64" else None},

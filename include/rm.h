@@ -192,6 +192,12 @@ typedef struct {
                               cluster; a shape the device cannot co-schedule is rejected with
                               RM_ERR_ARG. */
   int32_t solve_prec;      /* rm_solve_precision_t of the matching solve (default FP64) */
+  int32_t mma_pair;        /* split modes, rm_run, 1 x 2 clusters with D by TMA and 15 products:
+                              0 (default) or 1 = the pole sum's MMAs run on the CTA pair as one
+                              (tcgen05 cta_group::2, M = 256 energies, each SM reading its own D
+                              slices and the P slices of the 64 pairs it forms); -1 = one-SM MMAs
+                              with the two P halves exchanged between the CTAs.  Both compute
+                              the same sum of the same slice products (see rm_plan_mma_pair). */
 } rm_options;
 
 /* Fill *opt with defaults: FP64, delta 0.05, sel {0}, host inputs, auto chunk. */
@@ -289,6 +295,9 @@ rm_status_t rm_plan_info(rm_plan_t plan, int32_t wave, int32_t* n_ch, int32_t* n
 
 /* Cluster shape of rm_run's tensor-core pole-sum launch (1 x 1 outside split modes). */
 rm_status_t rm_plan_cluster(rm_plan_t plan, int32_t* cluster_x, int32_t* cluster_y);
+
+/* *on = 1 when rm_run's tensor-core pole sum runs as 2-SM MMAs (rm_options.mma_pair), else 0. */
+rm_status_t rm_plan_mma_pair(rm_plan_t plan, int32_t* on);
 
 /* Slice products per far term of the plan's tensor-core pole sum (3, 6, 10, 13 or 15; 0 when
    the plan's precision has no tensor-core pole sum). */

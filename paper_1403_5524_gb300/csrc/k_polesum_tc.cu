@@ -722,6 +722,388 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                           blockIdx.y * BN, smem_raw);
 }
 
+// ------------------------------------------------------ 2-SM pole sum (cta_group::2)
+//
+// The 15-product far sum on a CTA pair whose MMAs run as one: tcgen05.mma.cta_group::2 with
+// M = 256 energies (the A operand: each CTA's own 128 energies of D slices, staged by TMA from the
+// D-slice kernel's buffer), N = 128 pairs (the B operand: each CTA holds the P slices of the 64
+// pairs it forms) and K = 16.  Each SM's tensor core reads its A and its half of B from its own
+// shared memory, so per product the B reads halve against the one-SM kernel (6 KB instead of 8 KB
+// per SM and K = 16), and no P half travels between the CTAs.  Each CTA's TMEM holds its 128
+// energies (lanes) x 128 pairs (columns) per order: order o in columns [128 o, 128 o + 128),
+// order 4 sharing order 3, as in the one-SM kernel; pair column c is the pair
+// (I0 + c / 16, J0 + c % 16), columns 0-63 formed by the even CTA and 64-127 by the odd one.
+//
+// Warps (19 per CTA, the same in both CTAs unless stated):
+//   0-15  producers: the P slices of the CTA's 64 pairs per k-step; drains and the epilogue
+//   16    TMEM allocation (both CTAs, collective); lane 0 of the even CTA issues the MMAs
+//   17    lane 0: W-row loads, and the readiness of each k-step to the even CTA
+//   18    lane 0: D-slice loads
+// Barriers: wfull / dfull complete on the CTA's own loads, gen on its producers; full (even CTA,
+// two arrivals) when both CTAs' operands of a k-step are in place; empty, emptyB and acc_full are
+// signalled in both CTAs by the even CTA's commits; acc_empty (even CTA) by the drains of both.
+constexpr int PAIR_PSL = 64 * KS * 2;  // 4 KB: one P slice of 64 pairs (64 rows x 64 B)
+
+template <int PST, int DST>
+struct PairGeo {
+  static constexpr int D_BYTES = 5 * SLICE_BYTES;  // 40 KB: five D slices of 128 energies
+  static constexpr int P_BYTES = 5 * PAIR_PSL;     // 20 KB: five P slices of 64 pairs
+  static constexpr int D_OFF = 0;
+  static constexpr int P_OFF = DST * D_BYTES;
+  static constexpr int W_OFF = P_OFF + PST * P_BYTES;
+  static constexpr int BARS_OFF = W_OFF + PST * TX_BYTES;
+  static constexpr int NBARS = 4 * PST + 2 * DST + 3;
+  static constexpr size_t SMEM = (size_t)BARS_OFF + 1024 + NBARS * 8 + 16;
+};
+constexpr int PAIR_PST = 4;  // P-slice / W-row stages
+constexpr int PAIR_DST = 3;  // D-slice buffers
+static_assert(PairGeo<PAIR_PST, PAIR_DST>::SMEM <= 232448, "a CTA's shared memory");
+static_assert(TX_BYTES % 128 == 0 && PairGeo<PAIR_PST, PAIR_DST>::W_OFF % 1024 == 0,
+              "W rows and slices keep the alignment TMA and the swizzle need");
+
+// the 2-SM kernel runs for 1 x 2 clusters with D by TMA and five slices per operand
+bool pair_applies(int cx, int cy, bool dt, int ns, bool pair) { return pair && cx == 1 && cy == 2 && dt && ns == 5; }
+
+template <int PST, int DST>
+__device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const CUtensorMap* map_pol,
+                                             const CUtensorMap* map_d, const TCArgs& g, int I0, int J0, int n0,
+                                             unsigned char* smem_raw) {
+  using namespace ptx;
+  using Geo = PairGeo<PST, DST>;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Geo::BARS_OFF);
+  uint64_t* wfull = bars;
+  uint64_t* gen = bars + PST;
+  uint64_t* full = bars + 2 * PST;
+  uint64_t* empty = bars + 3 * PST;
+  uint64_t* dfull = bars + 4 * PST;
+  uint64_t* emptyB = dfull + DST;
+  uint64_t* acc_full = emptyB + DST;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* done = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + Geo::NBARS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nK = g.nK;
+  const int n = g.n;
+  const uint32_t rank = cluster_ctarank();  // 0: issues the pair's MMAs; 1: its peer
+  const bool lead = rank == 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PST; ++s) {
+      mbar_init(wfull + s, 1);
+      mbar_init(gen + s, NWORK);
+      mbar_init(full + s, 2);  // the readiness arrivals of both CTAs
+      mbar_init(empty + s, 1);
+    }
+    for (int q = 0; q < DST; ++q) {
+      mbar_init(dfull + q, 1);
+      mbar_init(emptyB + q, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 2 * NWORK);  // the drain warps of both CTAs
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == NWORK) {
+    tmem_alloc_pair(tmem_slot, 512);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  cluster_sync();  // both CTAs' barriers and TMEM exist before any remote arrive or MMA
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == NWORK) {
+    // ------------------------------------------- MMA issue (1 thread of the even CTA)
+    if (lead && lane == 0) {
+      const uint32_t idesc = idesc_bf16_f32(256, 128, false);
+      bool ok = true;
+      bool issued = false;
+      for (int j = 0; j < nK; ++j) {
+        const int s = j % PST, q = j % DST;
+        if (!mbar_wait_cluster(full + s, (uint32_t)((j / PST) & 1), abort_flag, g.wait_budget)) {
+          ok = false;
+          break;
+        }
+        const int d = j / DRAIN_KSTEPS;
+        const bool first = (j % DRAIN_KSTEPS) == 0;
+        if (first && d > 0 &&
+            !mbar_wait_cluster(acc_empty, (uint32_t)((d - 1) & 1), abort_flag, g.wait_budget)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a = smem_u32(smem + Geo::D_OFF + q * Geo::D_BYTES);
+        const uint32_t b = smem_u32(smem + Geo::P_OFF + s * Geo::P_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint32_t ko = kk * 32;
+          const uint32_t f = (first && kk == 0) ? 0u : 1u;
+          auto A = [&](int v) { return desc_kmajor_sw64(a + v * SLICE_BYTES + ko); };  // D slice v
+          auto B = [&](int u) { return desc_kmajor_sw64(b + u * PAIR_PSL + ko); };     // P slice u
+          // (u, v) = P slice u times D slice v into order u + v (4 into 3); the first product
+          // into each order of a drain period starts it.  Each order receives its products in
+          // the one-SM kernels' sequence, so the inexact FP32 sums of order 3 round alike and
+          // the two forms give the same bits.
+          mma_bf16_ss_pair(tmem + 0, A(0), B(0), idesc, f);    // (0,0)
+          mma_bf16_ss_pair(tmem + 128, A(1), B(0), idesc, f);  // (0,1)
+          mma_bf16_ss_pair(tmem + 128, A(0), B(1), idesc, 1u); // (1,0)
+          mma_bf16_ss_pair(tmem + 256, A(2), B(0), idesc, f);  // (0,2)
+          mma_bf16_ss_pair(tmem + 256, A(1), B(1), idesc, 1u); // (1,1)
+          mma_bf16_ss_pair(tmem + 256, A(0), B(2), idesc, 1u); // (2,0)
+          mma_bf16_ss_pair(tmem + 384, A(3), B(0), idesc, f);  // (0,3)
+          mma_bf16_ss_pair(tmem + 384, A(4), B(0), idesc, 1u); // (0,4)
+          mma_bf16_ss_pair(tmem + 384, A(2), B(1), idesc, 1u); // (1,2)
+          mma_bf16_ss_pair(tmem + 384, A(3), B(1), idesc, 1u); // (1,3)
+          mma_bf16_ss_pair(tmem + 384, A(1), B(2), idesc, 1u); // (2,1)
+          mma_bf16_ss_pair(tmem + 384, A(2), B(2), idesc, 1u); // (2,2)
+          mma_bf16_ss_pair(tmem + 384, A(0), B(3), idesc, 1u); // (3,0)
+          mma_bf16_ss_pair(tmem + 384, A(1), B(3), idesc, 1u); // (3,1)
+          mma_bf16_ss_pair(tmem + 384, A(0), B(4), idesc, 1u); // (4,0)
+        }
+        issued = true;
+        mma_commit_pair_mc(empty + s, (uint16_t)3);   // both CTAs may refill this P stage
+        mma_commit_pair_mc(emptyB + q, (uint16_t)3);  // and this D buffer
+        if ((j + 1) % DRAIN_KSTEPS == 0 || j == nK - 1) mma_commit_pair_mc(acc_full, (uint16_t)3);
+      }
+      if (!ok && issued) {
+        // abort path: the MMAs in flight read both CTAs' shared memory; let them finish
+        mma_commit_pair_mc(done, (uint16_t)1);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(done, 0u) && clock64() - t0 < 400000000LL) {
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == NWORK + 1) {
+    // ---------------------------- W-row loads and k-step readiness (1 thread per CTA)
+    if (lane == 0) {
+      int w_last[PST];
+#pragma unroll
+      for (int s = 0; s < PST; ++s) w_last[s] = -1;
+      auto issue_w = [&](int s, int j) {
+        float* WI = reinterpret_cast<float*>(smem + Geo::W_OFF + s * TX_BYTES);
+        float* WJ = WI + WI_FLOATS;
+        float* PO = WJ + WJ_FLOATS;
+        mbar_arrive_expect_tx(wfull + s, TX_BYTES);
+        const int x = j * KS;
+        tma_load_2d(WI, map_omega, wfull + s, x, 2 * I0);
+        tma_load_2d(WJ, map_omega, wfull + s, x, 2 * J0);
+        tma_load_2d(WJ + 16 * KS, map_omega, wfull + s, x, 2 * J0 + 16);
+        tma_load_2d(PO, map_pol, wfull + s, x, 0);
+        w_last[s] = j;
+      };
+      for (int s = 0; s < PST && s < nK; ++s) issue_w(s, s);
+      const uint32_t lead_full = mapa(smem_u32(full), 0u);
+      bool ok = true;
+      for (int j = 0; j < nK; ++j) {
+        const int s = j % PST, q = j % DST;
+        // this CTA's P slices of step j are formed (and its W rows read): refill the W rows
+        if (!mbar_wait(gen + s, (uint32_t)((j / PST) & 1), abort_flag, g.wait_budget)) {
+          ok = false;
+          break;
+        }
+        if (j + PST < nK) issue_w(s, j + PST);
+        if (!mbar_wait(dfull + q, (uint32_t)((j / DST) & 1), abort_flag, g.wait_budget)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_cluster(lead_full + (uint32_t)(8 * s));
+      }
+      if (ok) {
+        // the even CTA's commits for the last uses of every stage and D buffer have landed
+        // here, so none can reach this CTA's barriers after it exits
+        for (int j = (nK > PST ? nK - PST : 0); j < nK; ++j)
+          if (!mbar_wait_cluster(empty + j % PST, (uint32_t)((j / PST) & 1), abort_flag, g.wait_budget)) break;
+        for (int j = (nK > DST ? nK - DST : 0); j < nK; ++j)
+          if (!mbar_wait_cluster(emptyB + j % DST, (uint32_t)((j / DST) & 1), abort_flag, g.wait_budget)) break;
+      }
+      // no W copy may still be landing when the CTA exits
+      for (int s = 0; s < PST; ++s) {
+        if (w_last[s] < 0) continue;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(wfull + s, (uint32_t)((w_last[s] / PST) & 1)) && clock64() - t0 < 400000000LL) {
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == NWORK + 2) {
+    // ------------------------------------------- D-slice loads (1 thread per CTA)
+    if (lane == 0) {
+      int d_last[DST];
+#pragma unroll
+      for (int q = 0; q < DST; ++q) d_last[q] = -1;
+      for (int j = 0; j < nK; ++j) {
+        const int q = j % DST;
+        if (j >= DST &&
+            !mbar_wait_cluster(emptyB + q, (uint32_t)(((j / DST) - 1) & 1), abort_flag, g.wait_budget))
+          break;
+        mbar_arrive_expect_tx(dfull + q, (uint32_t)Geo::D_BYTES);
+        tma_load_3d(smem + Geo::D_OFF + q * Geo::D_BYTES, map_d, dfull + q, j * KS, n0, 0);
+        d_last[q] = j;
+      }
+      for (int q = 0; q < DST; ++q) {
+        if (d_last[q] < 0) continue;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(dfull + q, (uint32_t)((d_last[q] / DST) & 1)) && clock64() - t0 < 400000000LL) {
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------- producers and drains
+    const int w = warp;
+    // P rows of this CTA's 64 pairs: tile i-channel ai = 4 rank + w / 4, j-channels
+    // jj = jbase + 2t (t = 0, 1), pole pair kpa; a half-warp writes one full slice row
+    const int ail = w >> 2;
+    const int ai = 4 * (int)rank + ail;
+    const int kpa = lane & 15, jbase = 4 * (w & 3) + (lane >> 4);
+    const int gi = I0 + ai;
+    float mp[2];
+    uint32_t offP[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int jj = jbase + 2 * t;
+      const int gj = J0 + jj;
+      mp[t] = (gi < n && gj < n && gi <= gj) ? g.mult_p[pair_index(n, gi, gj)] : 0.0f;
+      offP[t] = swz(ail * 16 + jj, 2 * kpa);
+      if (!RM_CHECK(offP[t] + 4 <= (uint32_t)PAIR_PSL)) offP[t] = 0;
+    }
+    const uint32_t trow = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(32 * (w >> 2));
+    const uint32_t lead_acc_empty = mapa(smem_u32(acc_empty), 0u);
+    float Vh[32], Vl[32];  // running sums of this thread's 32 accumulator cells
+#pragma unroll
+    for (int c = 0; c < 32; ++c) Vh[c] = Vl[c] = 0.0f;
+    bool ok = true;
+    // A drain period's accumulators are read LAG k-steps after its last one is formed, so that
+    // the operands of the next period's first steps are in place when the MMAs resume.  Forming
+    // step j needs the MMAs of step j - PST done, which needed the drain of the period ending at
+    // step j - PST - 1 at the latest, run in iteration j - 2: LAG = PST - 1 cannot deadlock.
+    constexpr int LAG = PST - 1;
+    // every way out of this loop is taken by whole warps (converged polling of the same waits)
+    for (int j = 0; j < nK + LAG && ok; ++j) {
+      const int s = j % PST;
+      if (j < nK) {
+        if (j >= PST &&
+            !mbar_wait_cluster(empty + s, (uint32_t)(((j / PST) - 1) & 1), abort_flag, g.wait_budget)) {
+          ok = false;
+          break;
+        }
+        if (!mbar_wait(wfull + s, (uint32_t)((j / PST) & 1), abort_flag, g.wait_budget)) {
+          ok = false;
+          break;
+        }
+        const float* WI = reinterpret_cast<const float*>(smem + Geo::W_OFF + s * TX_BYTES);
+        const float* WJ = WI + WI_FLOATS;
+        uint8_t* Pb = smem + Geo::P_OFF + s * Geo::P_BYTES;
+        const int ka = 2 * kpa;
+        const float2 wih = *reinterpret_cast<const float2*>(WI + (2 * ai) * KS + ka);
+        const float2 wil = *reinterpret_cast<const float2*>(WI + (2 * ai + 1) * KS + ka);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int jj = jbase + 2 * t;
+          const float2 wjh = *reinterpret_cast<const float2*>(WJ + (2 * jj) * KS + ka);
+          const float2 wjl = *reinterpret_cast<const float2*>(WJ + (2 * jj + 1) * KS + ka);
+          float ph0, pl0, ph1, pl1;
+          df_mul(wih.x, wil.x, wjh.x, wjl.x, ph0, pl0);
+          df_mul(wih.y, wil.y, wjh.y, wjl.y, ph1, pl1);
+          float s0[5], s1[5];
+          slice5(__fmul_rn(ph0, mp[t]), __fmul_rn(pl0, mp[t]), s0);
+          slice5(__fmul_rn(ph1, mp[t]), __fmul_rn(pl1, mp[t]), s1);
+#pragma unroll
+          for (int u = 0; u < 5; ++u)
+            *reinterpret_cast<uint32_t*>(Pb + u * PAIR_PSL + offP[t]) = pack_bf16x2(s0[u], s1[u]);
+        }
+        // the tensor cores read these slices through the async proxy
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(gen + s);
+      }
+      const int je = j - LAG;  // last k-step of the drain period read in this iteration, if any
+      if (je >= 0 && ((je + 1) % DRAIN_KSTEPS == 0 || je == nK - 1)) {
+        const int d = je / DRAIN_KSTEPS;
+        if (!mbar_wait_cluster(acc_full, (uint32_t)(d & 1), abort_flag, g.wait_budget)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // orders 0-2 by TwoSum into (hi, lo); the order-3 sum is of the size of lo
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[16];
+            tmem_ld16(trow + (uint32_t)(o * 128 + h * 16), r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int i = h * 16 + c;
+              const float x = __uint_as_float(r[c]);
+              if (o < 3) {
+                float sh, se;
+                two_sum(Vh[i], x, sh, se);
+                Vh[i] = sh;
+                Vl[i] = __fadd_rn(Vl[i], se);
+              } else {
+                Vl[i] = __fadd_rn(Vl[i], x);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(lead_acc_empty);
+      }
+    }
+    // ------------------------------------------------------------- epilogue
+    // lane = energy row of this CTA's tile, columns = pairs
+    if (ok) {
+      const int e = n0 + 32 * (w & 3) + lane;
+      if (e < g.ne) {
+        const int64_t np = (int64_t)n * (n + 1) / 2;
+        const double te = g.tau[g.e_begin + e];
+        double* Re = g.R + (int64_t)e * np;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int col = 32 * (w >> 2) + c;
+          const int pi = I0 + col / 16, pj = J0 + col % 16;
+          if (pi < n && pj < n && pi <= pj) {
+            const int64_t p = pair_index(n, pi, pj);
+            if (RM_CHECK(p >= 0 && p < np)) Re[p] = ((double)Vh[c] + (double)Vl[c]) * g.f_p[p] * te;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  cluster_sync();  // neither CTA leaves while the pair's MMAs or the peer's arrivals may reach it
+  if (warp == NWORK) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, 512);
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicMax(g.err, (int)RM_ERR_TIMEOUT);
+}
+
+// Every wave of a plan in one launch.  A CTA pair is the two CTAs of a 2 x 1 x 1 cluster (the
+// pairing of cta_group::2 runs along the cluster's x): grid (2, tiles, energy-tile pairs), so that
+// blockIdx.x is the CTA's rank in its pair, blockIdx.y its pair tile and blockIdx.z the pair of
+// energy tiles; consecutive clusters hold consecutive pair tiles of the same energies, as in the
+// one-SM launch, and share their D slices in L2.
+__global__ void __launch_bounds__(NTHREADS, 1)
+    polesum_tc_pair_kernel(const TCArgs* __restrict__ waves, const CUtensorMap* __restrict__ maps,
+                           const int4* __restrict__ tiles, int64_t e_begin, int ne) {
+  extern __shared__ unsigned char smem_raw[];
+  const int4 t = tiles[blockIdx.y];
+  TCArgs g = waves[t.x];
+  g.e_begin = e_begin;
+  g.ne = ne;
+  tc_pair_tile<PAIR_PST, PAIR_DST>(maps + 3 * t.x, maps + 3 * t.x + 1, maps + 3 * t.x + 2, g, t.y * 8, t.z * 16,
+                                   (int)(2 * blockIdx.z + blockIdx.x) * BN, smem_raw);
+}
+
 // ------------------------------------------------------------ preparation
 // sigma_i = 2^ceil(log2 max_k |w_ik|); w_ik / sigma_i as FP32 hi (row 2i) + lo (row 2i+1)
 __global__ void prep_omega_kernel(const double* __restrict__ W, int n, int N, int Npad, double* __restrict__ sigma,
@@ -1043,9 +1425,14 @@ size_t polesum_tc_smem_bytes() {
   size_t m = TcGeo<4>::SMEM;
   if (TcGeo<5>::SMEM > m) m = TcGeo<5>::SMEM;
   if (TcGeo<5, true>::SMEM > m) m = TcGeo<5, true>::SMEM;
+  if (PairGeo<PAIR_PST, PAIR_DST>::SMEM > m) m = PairGeo<PAIR_PST, PAIR_DST>::SMEM;
   return m;
 }
 int polesum_slice_planes(int nprod) { return slices_of(nprod) == 5 ? 5 : 4; }
+bool polesum_pair_runs(const Plan& p) {
+  return pair_applies(p.grp.tc_cx, p.grp.tc_cy, p.grp.dt(), polesum_slice_planes(p.slices), p.grp.tc_pair) &&
+         p.prec == RM_PREC_SPLIT_BF16;
+}
 
 std::vector<int2> split_tiles(int n) {
   std::vector<int2> t;
@@ -1153,13 +1540,15 @@ GroupedFn grouped_fn_ns(int cx, int cy, bool dt) {
   return nullptr;
 }
 
-// the grouped kernel for a cluster shape, D staging and slice count (4 or 5 per operand)
-GroupedFn grouped_fn(int cx, int cy, bool dt, int ns) {
+// the grouped kernel for a cluster shape, D staging, slice count (4 or 5 per operand) and MMA form
+GroupedFn grouped_fn(int cx, int cy, bool dt, int ns, bool pair) {
+  if (pair_applies(cx, cy, dt, ns, pair)) return polesum_tc_pair_kernel;
   return ns == 5 ? grouped_fn_ns<5>(cx, cy, dt) : grouped_fn_ns<4>(cx, cy, dt);
 }
 
-// dynamic shared memory of a grouped kernel (five slices with D by TMA: the two-deep D ring)
-size_t grouped_smem(int ns, bool dt) {
+// dynamic shared memory of a grouped kernel (five slices with D by TMA: the D ring)
+size_t grouped_smem(int cx, int cy, bool dt, int ns, bool pair) {
+  if (pair_applies(cx, cy, dt, ns, pair)) return PairGeo<PAIR_PST, PAIR_DST>::SMEM;
   return ns == 5 ? (dt ? TcGeo<5, true>::SMEM : TcGeo<5>::SMEM) : TcGeo<4>::SMEM;
 }
 
@@ -1167,13 +1556,15 @@ cudaError_t set_tc_smem() {
   const int shapes[8][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 2}, {2, 2}, {4, 2}, {2, 4}, {1, 4}};
   for (int ns = 4; ns <= 5; ++ns)
     for (int dt = 0; dt < 2; ++dt)
-      for (const auto& sh : shapes) {
-        GroupedFn fn = grouped_fn(sh[0], sh[1], dt != 0, ns);
-        if (!fn) continue;
-        cudaError_t err =
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grouped_smem(ns, dt != 0));
-        if (err != cudaSuccess) return err;
-      }
+      for (int pair = 0; pair < 2; ++pair)
+        for (const auto& sh : shapes) {
+          if (pair && !pair_applies(sh[0], sh[1], dt != 0, ns, true)) continue;
+          GroupedFn fn = grouped_fn(sh[0], sh[1], dt != 0, ns, pair != 0);
+          if (!fn) continue;
+          cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)grouped_smem(sh[0], sh[1], dt != 0, ns, pair != 0));
+          if (err != cudaSuccess) return err;
+        }
   return cudaSuccess;
 }
 
@@ -1273,6 +1664,7 @@ cudaError_t group_setup_split(Plan& p) {
                     sizeof(int2) * G.n_near_jobs)) != cudaSuccess)
     return err;
   G.n_tiles = (int)tiles.size();
+  if (G.n_tiles > 65535) G.tc_pair = false;  // the 2-SM launch holds the pair tiles in grid.y
   G.n_near_jobs = (int)jobs.size();
   if ((err = cudaMemcpy(G.tc_waves, tw.data(), sizeof(TCArgs) * W, cudaMemcpyHostToDevice)) != cudaSuccess) return err;
   if ((err = cudaMemcpy(G.maps, maps.data(), sizeof(CUtensorMap) * 3 * W, cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -1290,19 +1682,20 @@ cudaError_t group_setup_split(Plan& p) {
                               (int)near_smem_bytes(p.nR_max));
 }
 
-bool polesum_cluster_ok(int cx, int cy, int ns) {
-  GroupedFn fn = grouped_fn(cx, cy, cx == 1, ns);
+bool polesum_cluster_ok(int cx, int cy, int ns, bool pair) {
+  GroupedFn fn = grouped_fn(cx, cy, cx == 1, ns, pair);
   if (!fn) return false;
   if (cx * cy == 1) return true;
   if (set_tc_smem() != cudaSuccess) return false;
+  const bool two_sm = pair_applies(cx, cy, cx == 1, ns, pair);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cx * 8, cy * 8, 1);
+  cfg.gridDim = two_sm ? dim3(2, 8, 8) : dim3(cx * 8, cy * 8, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = grouped_smem(ns, cx == 1);
+  cfg.dynamicSmemBytes = grouped_smem(cx, cy, cx == 1, ns, pair);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cx;
-  attr[0].val.clusterDim.y = cy;
+  attr[0].val.clusterDim.x = two_sm ? 2 : cx;
+  attr[0].val.clusterDim.y = two_sm ? 1 : cy;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -1318,18 +1711,21 @@ cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cuda
   if (ne <= 0) return cudaSuccess;
   const GroupDev& G = p.grp;
   const int ns = polesum_slice_planes(p.slices);
-  GroupedFn fn = grouped_fn(G.tc_cx, G.tc_cy, G.dt(), ns);
+  GroupedFn fn = grouped_fn(G.tc_cx, G.tc_cy, G.dt(), ns, G.tc_pair);
   if (!fn) return cudaErrorInvalidValue;
   const int ny = (ne + BN - 1) / BN;
+  const bool two_sm = pair_applies(G.tc_cx, G.tc_cy, G.dt(), ns, G.tc_pair);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(G.n_tiles, (ny + G.tc_cy - 1) / G.tc_cy * G.tc_cy, 1);
+  // the 2-SM kernel: grid (rank in pair, pair tile, energy-tile pair), clusters of 2 x 1 x 1
+  cfg.gridDim = two_sm ? dim3(2, G.n_tiles, (ny + 1) / 2)
+                       : dim3(G.n_tiles, (ny + G.tc_cy - 1) / G.tc_cy * G.tc_cy, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = grouped_smem(ns, G.dt());
+  cfg.dynamicSmemBytes = grouped_smem(G.tc_cx, G.tc_cy, G.dt(), ns, G.tc_pair);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = G.tc_cx;
-  attr[0].val.clusterDim.y = G.tc_cy;
+  attr[0].val.clusterDim.x = two_sm ? 2 : G.tc_cx;
+  attr[0].val.clusterDim.y = two_sm ? 1 : G.tc_cy;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (G.tc_cx * G.tc_cy > 1) ? 1 : 0;

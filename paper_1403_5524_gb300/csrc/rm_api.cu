@@ -445,7 +445,7 @@ rm_status_t build_graph(Plan* p) {
 // shape, keyed by the plan's sizes.
 std::string tune_key(const Plan* p) {
   std::string k = "rm3 prec=" + std::to_string(p->prec) + " prod=" + std::to_string(p->slices) +
-                  " ne=" + std::to_string(p->n_e) +
+                  " pair=" + std::to_string(p->grp.tc_pair ? 1 : 0) + " ne=" + std::to_string(p->n_e) +
                   " sel=" + std::to_string(p->n_sel);
   for (const auto& w : p->waves) k += " " + std::to_string(w.nR) + "x" + std::to_string(w.N);
   return k;
@@ -518,7 +518,7 @@ rm_status_t autotune(Plan* p, const char* cache, int chunk_max, bool tune_chunk,
   const std::string key = tune_key(p);
   Tuned t;
   if (cache_lookup(cache, key, t) && t.chunk > 0 && t.chunk <= chunk_max &&
-      (!tune_cluster || polesum_cluster_ok(t.cx, t.cy, polesum_slice_planes(p->slices)))) {
+      (!tune_cluster || polesum_cluster_ok(t.cx, t.cy, polesum_slice_planes(p->slices), p->grp.tc_pair))) {
     if (tune_chunk) G.chunk = t.chunk;
     if (tune_cluster) {
       G.tc_cx = t.cx;
@@ -538,7 +538,7 @@ rm_status_t autotune(Plan* p, const char* cache, int chunk_max, bool tune_chunk,
     double best_t = 1e300;
     int bx = G.tc_cx, by = G.tc_cy;
     for (const auto& sh : kShapes) {
-      if (!polesum_cluster_ok(sh[0], sh[1], polesum_slice_planes(p->slices))) continue;
+      if (!polesum_cluster_ok(sh[0], sh[1], polesum_slice_planes(p->slices), p->grp.tc_pair)) continue;
       G.tc_cx = sh[0];
       G.tc_cy = sh[1];
       float ms = 0.f;
@@ -637,6 +637,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       return fail(RM_ERR_ARG, "slices = 15 needs BF16 slices (FP16 cannot hold the fifth, 2^-25 small)");
     if (o.solve_prec != RM_SOLVE_FP64 && o.solve_prec != RM_SOLVE_MIXED && o.solve_prec != RM_SOLVE_FP64_LU)
       return fail(RM_ERR_ARG, "bad solve precision");
+    if (o.mma_pair < -1 || o.mma_pair > 1) return fail(RM_ERR_ARG, "mma_pair must be -1, 0 or 1");
     if (!(o.cluster_x == 0 || o.cluster_x == 1 || o.cluster_x == 2 || o.cluster_x == 4) ||
         !(o.cluster_y == 0 || o.cluster_y == 1 || o.cluster_y == 2 || o.cluster_y == 4) ||
         (o.cluster_x > 0 && o.cluster_y > 0 && o.cluster_x * o.cluster_y > 8))
@@ -672,6 +673,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     p->prec = o.prec;
     p->delta = o.delta;
     p->slices = o.slices ? o.slices : (o.prec == RM_PREC_SPLIT_FP16 ? 13 : RM_DEFAULT_SLICES);
+    p->grp.tc_pair = o.mma_pair >= 0;
     p->fault_wait = env_ll("RM_FAULT_WAIT_CYCLES");
     p->n_sel = n_sel;
     std::memcpy(p->sel, sel, sizeof(sel));
@@ -801,13 +803,13 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
       if (o.cluster_x > 0 || o.cluster_y > 0) {
         p->grp.tc_cx = o.cluster_x > 0 ? o.cluster_x : 1;
         p->grp.tc_cy = o.cluster_y > 0 ? o.cluster_y : 1;
-        if (!polesum_cluster_ok(p->grp.tc_cx, p->grp.tc_cy, polesum_slice_planes(p->slices)))
+        if (!polesum_cluster_ok(p->grp.tc_cx, p->grp.tc_cy, polesum_slice_planes(p->slices), p->grp.tc_pair))
           st = fail(RM_ERR_ARG, "cluster shape cannot be co-scheduled on this device");
       } else {
         p->grp.tc_cx = 1;
         p->grp.tc_cy = 1;
         for (const auto& sh : kShapes) {
-          if (polesum_cluster_ok(sh[0], sh[1], polesum_slice_planes(p->slices))) {
+          if (polesum_cluster_ok(sh[0], sh[1], polesum_slice_planes(p->slices), p->grp.tc_pair)) {
             p->grp.tc_cx = sh[0];
             p->grp.tc_cy = sh[1];
             break;
@@ -1143,6 +1145,13 @@ rm_status_t rm_plan_cluster(rm_plan_t h, int32_t* cx, int32_t* cy) {
   if (!p) return fail(RM_ERR_ARG, "null plan");
   if (cx) *cx = p->grp.tc_cx;
   if (cy) *cy = p->grp.tc_cy;
+  return RM_OK;
+}
+
+rm_status_t rm_plan_mma_pair(rm_plan_t h, int32_t* on) {
+  Plan* p = as_plan(h);
+  if (!p || !on) return fail(RM_ERR_ARG, "null argument");
+  *on = polesum_pair_runs(*p) ? 1 : 0;
   return RM_OK;
 }
 

@@ -137,6 +137,7 @@ struct GroupDev {
   int4* tiles = nullptr;      // (wave, i-block, j-block), longest K first
   int n_tiles = 0;
   int tc_cx = 1, tc_cy = 1;   // tensor-core cluster shape (pair tiles x energy tiles)
+  bool tc_pair = true;        // 1 x 2 clusters with D by TMA and 15 products: 2-SM MMAs
   std::vector<uint32_t*> D;   // per wave [4 or 5 slices][d_rows energies][Npad / 2 pole pairs] packed D slices
   int d_rows = 0;             // energy rows of each D buffer (the largest chunk); 0: none allocated
   void* dslice_waves = nullptr;
@@ -258,7 +259,9 @@ cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cuda
 // D slices of the chunk [e0, e0 + ne) for every wave (shapes with cluster_x = 1)
 cudaError_t launch_dslice_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);
 // clusters of this shape can be resident (grouped tensor-core kernel with ns slices per operand)
-bool polesum_cluster_ok(int cx, int cy, int ns);
+bool polesum_cluster_ok(int cx, int cy, int ns, bool pair);
+// the plan's rm_run pole sum is the 2-SM (cta_group::2) kernel
+bool polesum_pair_runs(const Plan& p);
 // slices per operand the tensor-core kernel stages for a product set (4, or 5 for 15 products)
 int polesum_slice_planes(int nprod);
 cudaError_t launch_near_grouped(const Plan& p, int64_t e0, int ne, cudaStream_t s);

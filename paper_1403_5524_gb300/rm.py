@@ -29,7 +29,7 @@ PREC = {"fp64": RM_PREC_FP64, "split_bf16": RM_PREC_SPLIT_BF16, "split_fp16": RM
 EXPORTS = ["rm_options_default", "rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix",
            "rm_xsec", "rm_run", "rm_results", "rm_sync", "rm_plan_info", "rm_plan_launches",
            "rm_plan_destroy", "rm_status_str", "rm_last_error", "rm_profile_enable", "rm_profile_read",
-           "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve", "rm_plan_slices",
+           "rm_plan_cluster", "rm_plan_mma_pair", "rm_photo", "rm_results_photo", "rm_convolve", "rm_plan_slices",
            "rm_xsec_from_r_static", "rm_static_last_error", "rm_static_layout", "rm_checked_report"]
 
 KERNELS = {"polesum_fp64": 0, "polesum_split": 1, "near": 2, "asym": 3, "solve": 4, "dslice": 5}
@@ -45,7 +45,8 @@ class rm_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("delta", C.c_double), ("slices", C.c_int32),
                 ("sel_init", C.c_void_p), ("n_sel", C.c_int32), ("mem", C.c_int32),
                 ("chunk", C.c_int32), ("autotune", C.c_int32), ("tune_cache", C.c_char_p),
-                ("cluster_x", C.c_int32), ("cluster_y", C.c_int32), ("solve_prec", C.c_int32)]
+                ("cluster_x", C.c_int32), ("cluster_y", C.c_int32), ("solve_prec", C.c_int32),
+                ("mma_pair", C.c_int32)]
 
 
 class RMError(RuntimeError):
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH):
     lib.rm_plan_info.argtypes = [P, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
                                  C.POINTER(i32), C.POINTER(i64)]
     lib.rm_plan_cluster.argtypes = [P, C.POINTER(i32), C.POINTER(i32)]
+    lib.rm_plan_mma_pair.argtypes = [P, C.POINTER(i32)]
     lib.rm_photo.argtypes = [P, i32, i64, i64, P, P, i32]
     lib.rm_results_photo.argtypes = [P, i32, i64, i64, P, P, i32]
     lib.rm_convolve.argtypes = [P, i64, P, i32, P, dbl, P, i32, P]
@@ -100,7 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.rm_last_error.restype = C.c_char_p
     for name in ["rm_plan_create", "rm_plan_load", "rm_rmatrix", "rm_kmatrix", "rm_xsec", "rm_run",
                  "rm_results", "rm_sync", "rm_plan_info", "rm_plan_destroy", "rm_profile_enable",
-                 "rm_profile_read", "rm_plan_cluster", "rm_photo", "rm_results_photo", "rm_convolve",
+                 "rm_profile_read", "rm_plan_cluster", "rm_plan_mma_pair", "rm_photo", "rm_results_photo",
+                 "rm_convolve",
                  "rm_plan_slices", "rm_xsec_from_r_static", "rm_static_layout", "rm_checked_report"]:
         getattr(lib, name).restype = C.c_int32
     _lib = lib
@@ -161,7 +164,7 @@ class Plan:
     def __init__(self, waves: Sequence, energies, prec: str = "fp64", delta: float = 0.05,
                  sel: Sequence[int] = (0,), chunk: int = 0, slices: int = 0, stream=None,
                  autotune: bool = False, tune_cache: Optional[str] = None,
-                 cluster: Optional[Sequence[int]] = None, solve: str = "fp64"):
+                 cluster: Optional[Sequence[int]] = None, solve: str = "fp64", mma_pair: int = 0):
         self.lib = load_library()
         self._keep = []
         self.mem = RM_MEM_DEVICE if _is_dev(energies) else RM_MEM_HOST
@@ -182,6 +185,7 @@ class Plan:
         if cluster is not None:
             opt.cluster_x, opt.cluster_y = int(cluster[0]), int(cluster[1])
         opt.solve_prec = SOLVE[solve]
+        opt.mma_pair = int(mma_pair)
         h = C.c_void_p()
         self.n_e = int(energies.shape[0])
         self.n_waves = len(waves)
@@ -236,6 +240,12 @@ class Plan:
         cx, cy = C.c_int32(), C.c_int32()
         _check(self.lib.rm_plan_cluster(self.h, C.byref(cx), C.byref(cy)))
         return int(cx.value), int(cy.value)
+
+    def mma_pair(self) -> bool:
+        """True when rm_run's tensor-core pole sum runs as 2-SM (cta_group::2) MMAs."""
+        v = C.c_int32()
+        _check(self.lib.rm_plan_mma_pair(self.h, C.byref(v)))
+        return bool(v.value)
 
     def slices(self) -> int:
         """Slice products per far term of the tensor-core pole sum (0 without one)."""

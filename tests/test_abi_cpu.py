@@ -42,6 +42,7 @@ def test_options_default(lib):
     lib.rm_options_default(C.byref(o))
     assert o.prec == rm.RM_PREC_FP64 and abs(o.delta - 0.05) < 1e-15 and o.mem == rm.RM_MEM_HOST
     assert o.chunk == 0 and o.n_sel == 0
+    assert o.mma_pair == 0  # the 2-SM pole sum where it applies
 
 
 def _create(lib, waves, energies, opt=None, n_waves=None):
@@ -107,6 +108,21 @@ def test_slices_option_checked_on_host(lib):
     assert b"15" in lib.rm_last_error()
     v = C.c_int32(-7)
     assert lib.rm_plan_slices(None, C.byref(v)) == rm.RM_ERR_ARG
+
+
+def test_mma_pair_option_checked_on_host(lib):
+    # mma_pair: -1 (one-SM MMAs), 0 or 1 (2-SM MMAs where they apply); anything else is rejected
+    # before the device is touched
+    wl = synth.small(1, 4, 20, 5)
+    o = rm.rm_options()
+    lib.rm_options_default(C.byref(o))
+    o.prec = rm.RM_PREC_SPLIT_BF16
+    for bad in (-2, 2, 7):
+        o.mma_pair = bad
+        assert _create(lib, wl.waves, wl.energies, o)[0] == rm.RM_ERR_ARG, bad
+        assert b"mma_pair" in lib.rm_last_error()
+    v = C.c_int32(-7)
+    assert lib.rm_plan_mma_pair(None, C.byref(v)) == rm.RM_ERR_ARG
 
 
 def test_static_entry_arguments_checked_on_host(lib):

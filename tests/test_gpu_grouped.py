@@ -184,3 +184,47 @@ def test_cluster_shapes_identical(rm, cluster_case, shape):
                 st = ref["sig_tot"][t, q]
                 if st > 0:
                     assert np.abs(base[g]["sig_sel"][e, q] - ref["sig_sel"][t, q]).max() / st <= 1e-8
+
+
+@pytest.mark.parametrize("n_e", [333, 130, 1])
+def test_mma_pair_matches_one_sm(rm, n_e):
+    # the 2-SM form (tcgen05 cta_group::2, M = 256 energies over the CTA pair, each CTA holding the
+    # P slices of the 64 pairs it forms) against the one-SM form of the same 1 x 2 cluster, on
+    # uneven waves and meshes of 3, 2 and 1 energy tiles (odd counts leave the second CTA of the
+    # last cluster past the mesh): the same slice products summed in the same order per
+    # accumulator give the same bits; and against the oracle on sampled energies
+    waves = [synth.small(700 + g, n, 40 * n, 1, pole_lo=-3, pole_hi=12, a=20.0).waves[0]
+             for g, n in enumerate([5, 23, 9, 40, 17, 64])]
+    E = np.linspace(0.04, 3.3, n_e)
+    sel = (0, 2)
+    outs = {}
+    for pair in (0, -1):
+        try:
+            p = rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, cluster=(1, 2), mma_pair=pair)
+        except rm.RMError as ex:
+            pytest.skip(f"1 x 2 clusters not co-schedulable here: {ex}")
+        with p:
+            assert p.mma_pair() == (pair == 0)
+            p.run()
+            res = []
+            for g, w in enumerate(waves):
+                o = rm.host_outputs(E.size, w.n, 2)
+                p.results(g, 0, E.size, **o)
+                res.append(o)
+            outs[pair] = res
+    for g in range(len(waves)):
+        for k in ("eigsum", "sig_tot", "sig_sel", "n_open", "flags"):
+            assert np.array_equal(outs[0][g][k], outs[-1][g][k]), (n_e, g, k)
+    for g, w in enumerate(waves):
+        idx = np.unique(np.array([0, n_e // 2, n_e - 1]))
+        ref = orc.sweep(w, E, sel=sel, energy_idx=idx, keep_R=False, keep_K=False)
+        for t, e in enumerate(idx):
+            if ref["flags"][t] & (orc.FLAG_ILLCOND | orc.FLAG_NO_OPEN):
+                continue
+            for q in range(2):
+                st = ref["sig_tot"][t, q]
+                if st > 0:
+                    err = np.abs(outs[0][g]["sig_sel"][e, q] - ref["sig_sel"][t, q]).max() / st
+                    assert err <= 1e-8, (g, e, q, err)
+            d = outs[0][g]["eigsum"][e] - ref["eta"][t]
+            assert abs(np.mod(d + np.pi, 2 * np.pi) - np.pi) <= 1e-7, (g, e)
