@@ -187,6 +187,33 @@ __device__ __forceinline__ void d_pack5(float ph0, float pl0, float ph1, float p
   for (int v = 0; v < 5; ++v) w[v] = pack_bf16x2(s0[v], s1[v]);
 }
 
+// One half h (16 cells) of a drain of the 15-product accumulators: the exact sums of orders 0-2
+// go into the high parts Vh[0..15] by TwoSum (error-free), and lo = (order-3 column) + the three TwoSum
+// errors, in that order.  The order-3 column holds the previous low part plus this period's
+// order-3 and order-4 products (the MMAs accumulate onto it), so the low parts never sit in
+// registers across the k-loop.
+__device__ __forceinline__ void drain_half(uint32_t trow, int h, float (&Vh)[16], float (&lo)[16]) {
+  float t[16];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    uint32_t r[16];
+    ptx::tmem_ld16(trow + (uint32_t)(o * 128 + h * 16), r);
+    ptx::tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      float sh, se;
+      two_sum(Vh[c], __uint_as_float(r[c]), sh, se);
+      Vh[c] = sh;
+      t[c] = o == 0 ? se : __fadd_rn(t[c], se);
+    }
+  }
+  uint32_t r[16];
+  ptx::tmem_ld16(trow + (uint32_t)(384 + h * 16), r);
+  ptx::tmem_wait_ld();
+#pragma unroll
+  for (int c = 0; c < 16; ++c) lo[c] = __fadd_rn(__uint_as_float(r[c]), t[c]);
+}
+
 struct TCArgs {
   const float* mult_p;
   const double* f_p;
@@ -364,8 +391,11 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           // each used accumulator of a drain period starts it (f = 0).
           mma_bf16_ss(tmem + 0, A(0), B(0), idN256, f);  // (0,0) (0,1)
           if constexpr (NS == 5) {
-            // all 15 products with u + v <= 4; order 4 shares the order-3 accumulator
-            mma_bf16_ss(tmem + 256, A(0), B(2), idN256, f);   // (0,2) (0,3)
+            // all 15 products with u + v <= 4; order 4 shares the order-3 accumulator, which
+            // also carries the running sums' low parts from drain to drain, so this product
+            // starts orders 2 and 3 only once (the drains zero order 2 instead)
+            const uint32_t f23 = (j == 0 && kk == 0) ? 0u : 1u;
+            mma_bf16_ss(tmem + 256, A(0), B(2), idN256, f23);  // (0,2) (0,3)
             mma_bf16_ss(tmem + 384, A(0), B(4), idN128, 1u);  // (0,4)
             mma_bf16_ss(tmem + 128, A(1), B(0), idN256, 1u);  // (1,0) (1,1)
             mma_bf16_ss(tmem + 384, A(1), B(2), idN128, 1u);  // (1,2)
@@ -543,9 +573,14 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       if (!RM_CHECK(offB[t] + 4 <= (uint32_t)SLICE_BYTES)) offB[t] = 0;
     }
     const uint32_t trow = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(32 * (w >> 2));
-    float Vh[32], Vl[32];  // running sums of this thread's 32 accumulator cells
+    // running sums of this thread's 32 accumulator cells (pair row 32 (w & 3) + lane, energy
+    // columns 32 (w >> 2) + c): high and low parts; with five slices the low parts live in the
+    // order-3 columns instead (drain_half), and Vl is unused
+    float Vh[32], Vl[NS == 5 ? 1 : 32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) Vh[c] = Vl[c] = 0.0f;
+    for (int c = 0; c < 32; ++c) Vh[c] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < (NS == 5 ? 1 : 32); ++c) Vl[c] = 0.0f;
     bool ok = true;
     // Every way out of this loop is taken by whole warps, so that no lane is left at the
     // __syncwarp below while another has gone on to the final barrier: the waits are polled by
@@ -639,26 +674,63 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
           break;
         }
         tc_fence_after();
-        // orders 0-2 by TwoSum into (hi, lo); the order-3 sum is of the size of lo
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
+        if constexpr (NS == 5) {
+          const bool last = j == nK - 1;
+          const int row = 32 * (w & 3) + lane;
+          const int pi = I0 + row / 16, pj = J0 + row % 16;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            uint32_t r[16];
-            tmem_ld16(trow + (uint32_t)(o * 128 + h * 16), r);
-            tmem_wait_ld();
+            float lo[16], vh[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int i = h * 16 + c;
-              // an order the product set leaves unused holds stale TMEM: select it away
-              const float x = o < nord ? __uint_as_float(r[c]) : 0.0f;
-              if (o < 3) {
-                float sh, se;
-                two_sum(Vh[i], x, sh, se);
-                Vh[i] = sh;
-                Vl[i] = __fadd_rn(Vl[i], se);
-              } else {
-                Vl[i] = __fadd_rn(Vl[i], x);
+            for (int c = 0; c < 16; ++c) vh[c] = Vh[h * 16 + c];
+            drain_half(trow, h, vh, lo);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) Vh[h * 16 + c] = vh[c];
+            if (!last) {
+              // the new low parts go back to order 3, and order 2 restarts from zero
+              uint32_t r[16], z[16];
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                r[c] = __float_as_uint(lo[c]);
+                z[c] = 0u;
+              }
+              tmem_st16(trow + (uint32_t)(384 + h * 16), r);
+              tmem_st16(trow + (uint32_t)(256 + h * 16), z);
+            } else if (pi < n && pj < n && pi <= pj) {
+              const int64_t np = (int64_t)n * (n + 1) / 2;
+              const int64_t p = pair_index(n, pi, pj);
+              const double fp = g.f_p[p];
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                const int e = n0 + 32 * (w >> 2) + h * 16 + c;
+                if (e < g.ne && RM_CHECK(p >= 0 && p < np))
+                  g.R[(int64_t)e * np + p] = ((double)Vh[h * 16 + c] + (double)lo[c]) * fp * g.tau[g.e_begin + e];
+              }
+            }
+          }
+          if (!last) tmem_wait_st();
+        } else {
+          // orders 0-2 by TwoSum into (hi, lo); the order-3 sum is of the size of lo
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              uint32_t r[16];
+              tmem_ld16(trow + (uint32_t)(o * 128 + h * 16), r);
+              tmem_wait_ld();
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                const int i = h * 16 + c;
+                // an order the product set leaves unused holds stale TMEM: select it away
+                const float x = o < nord ? __uint_as_float(r[c]) : 0.0f;
+                if (o < 3) {
+                  float sh, se;
+                  two_sum(Vh[i], x, sh, se);
+                  Vh[i] = sh;
+                  Vl[i] = __fadd_rn(Vl[i], se);
+                } else {
+                  Vl[i] = __fadd_rn(Vl[i], x);
+                }
               }
             }
           }
@@ -669,18 +741,21 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* map_omega, const CUte
       }
     }
     // ------------------------------------------------------------- epilogue
-    if (ok) {
-      const int row = 32 * (w & 3) + lane;
-      const int pi = I0 + row / 16, pj = J0 + row % 16;
-      if (pi < n && pj < n && pi <= pj) {
-        const int64_t np = (int64_t)n * (n + 1) / 2;
-        const int64_t p = pair_index(n, pi, pj);
-        const double fp = g.f_p[p];
+    // (five slices: written by the last drain)
+    if constexpr (NS != 5) {
+      if (ok) {
+        const int row = 32 * (w & 3) + lane;
+        const int pi = I0 + row / 16, pj = J0 + row % 16;
+        if (pi < n && pj < n && pi <= pj) {
+          const int64_t np = (int64_t)n * (n + 1) / 2;
+          const int64_t p = pair_index(n, pi, pj);
+          const double fp = g.f_p[p];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int e = n0 + 32 * (w >> 2) + c;
-          if (e < g.ne && RM_CHECK(p >= 0 && p < np))
-            g.R[(int64_t)e * np + p] = ((double)Vh[c] + (double)Vl[c]) * fp * g.tau[g.e_begin + e];
+          for (int c = 0; c < 32; ++c) {
+            const int e = n0 + 32 * (w >> 2) + c;
+            if (e < g.ne && RM_CHECK(p >= 0 && p < np))
+              g.R[(int64_t)e * np + p] = ((double)Vh[c] + (double)Vl[c]) * fp * g.tau[g.e_begin + e];
+          }
         }
       }
     }
@@ -734,15 +809,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // order 4 sharing order 3, as in the one-SM kernel; pair column c is the pair
 // (I0 + c / 16, J0 + c % 16), columns 0-63 formed by the even CTA and 64-127 by the odd one.
 //
-// Warps (19 per CTA, the same in both CTAs unless stated):
+// Warps (18 per CTA, the same in both CTAs unless stated):
 //   0-15  producers: the P slices of the CTA's 64 pairs per k-step; drains and the epilogue
 //   16    TMEM allocation (both CTAs, collective); lane 0 of the even CTA issues the MMAs
-//   17    lane 0: W-row loads, and the readiness of each k-step to the even CTA
-//   18    lane 0: D-slice loads
+//   17    lane 0: W-row and D-slice loads, and the readiness of each k-step to the even CTA
 // Barriers: wfull / dfull complete on the CTA's own loads, gen on its producers; full (even CTA,
 // two arrivals) when both CTAs' operands of a k-step are in place; empty, emptyB and acc_full are
 // signalled in both CTAs by the even CTA's commits; acc_empty (even CTA) by the drains of both.
 constexpr int PAIR_PSL = 64 * KS * 2;  // 4 KB: one P slice of 64 pairs (64 rows x 64 B)
+constexpr int PAIR_NTHREADS = (NWORK + 2) * 32;  // producers + MMA warp + load/readiness warp
 
 template <int PST, int DST>
 struct PairGeo {
@@ -842,10 +917,12 @@ __device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const
         for (int kk = 0; kk < 2; ++kk) {
           const uint32_t ko = kk * 32;
           const uint32_t f = (first && kk == 0) ? 0u : 1u;
+          // order 3 carries the low parts of the running sums from drain to drain: it starts once
+          const uint32_t f3 = (j == 0 && kk == 0) ? 0u : 1u;
           auto A = [&](int v) { return desc_kmajor_sw64(a + v * SLICE_BYTES + ko); };  // D slice v
           auto B = [&](int u) { return desc_kmajor_sw64(b + u * PAIR_PSL + ko); };     // P slice u
           // (u, v) = P slice u times D slice v into order u + v (4 into 3); the first product
-          // into each order of a drain period starts it.  Each order receives its products in
+          // into each of orders 0-2 of a drain period starts it.  Each order receives its products in
           // the one-SM kernels' sequence, so the inexact FP32 sums of order 3 round alike and
           // the two forms give the same bits.
           mma_bf16_ss_pair(tmem + 0, A(0), B(0), idesc, f);    // (0,0)
@@ -854,7 +931,7 @@ __device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const
           mma_bf16_ss_pair(tmem + 256, A(2), B(0), idesc, f);  // (0,2)
           mma_bf16_ss_pair(tmem + 256, A(1), B(1), idesc, 1u); // (1,1)
           mma_bf16_ss_pair(tmem + 256, A(0), B(2), idesc, 1u); // (2,0)
-          mma_bf16_ss_pair(tmem + 384, A(3), B(0), idesc, f);  // (0,3)
+          mma_bf16_ss_pair(tmem + 384, A(3), B(0), idesc, f3); // (0,3)
           mma_bf16_ss_pair(tmem + 384, A(4), B(0), idesc, 1u); // (0,4)
           mma_bf16_ss_pair(tmem + 384, A(2), B(1), idesc, 1u); // (1,2)
           mma_bf16_ss_pair(tmem + 384, A(3), B(1), idesc, 1u); // (1,3)
@@ -879,11 +956,18 @@ __device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const
     }
     __syncwarp();
   } else if (warp == NWORK + 1) {
-    // ---------------------------- W-row loads and k-step readiness (1 thread per CTA)
+    // ------------------- W-row and D-slice loads, k-step readiness (1 thread per CTA)
+    // Step j is forwarded to the even CTA once this CTA's P slices are formed (gen) and its D
+    // slices have landed (dfull); the W rows of step j + PST then refill the stage, and once
+    // the MMAs of step j - 1 are done the D slices of step j - 1 + DST refill their buffer:
+    // MMA j is then running, so the tensor pipe keeps a step queued while this thread waits,
+    // and a D box is issued two MMA steps before its step.
     if (lane == 0) {
-      int w_last[PST];
+      int w_last[PST], d_last[DST];
 #pragma unroll
       for (int s = 0; s < PST; ++s) w_last[s] = -1;
+#pragma unroll
+      for (int q = 0; q < DST; ++q) d_last[q] = -1;
       auto issue_w = [&](int s, int j) {
         float* WI = reinterpret_cast<float*>(smem + Geo::W_OFF + s * TX_BYTES);
         float* WJ = WI + WI_FLOATS;
@@ -896,6 +980,13 @@ __device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const
         tma_load_2d(PO, map_pol, wfull + s, x, 0);
         w_last[s] = j;
       };
+      auto issue_d = [&](int j) {
+        const int q = j % DST;
+        mbar_arrive_expect_tx(dfull + q, (uint32_t)Geo::D_BYTES);
+        tma_load_3d(smem + Geo::D_OFF + q * Geo::D_BYTES, map_d, dfull + q, j * KS, n0, 0);
+        d_last[q] = j;
+      };
+      for (int j = 0; j < DST && j < nK; ++j) issue_d(j);
       for (int s = 0; s < PST && s < nK; ++s) issue_w(s, s);
       const uint32_t lead_full = mapa(smem_u32(full), 0u);
       bool ok = true;
@@ -912,6 +1003,15 @@ __device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const
           break;
         }
         mbar_arrive_cluster(lead_full + (uint32_t)(8 * s));
+        const int jd = j - 1 + DST;  // the D slices the MMAs of step j - 1 make room for
+        if (j >= 1 && jd < nK) {
+          const int qd = (j - 1) % DST;
+          if (!mbar_wait_cluster(emptyB + qd, (uint32_t)(((j - 1) / DST) & 1), abort_flag, g.wait_budget)) {
+            ok = false;
+            break;
+          }
+          issue_d(jd);
+        }
       }
       if (ok) {
         // the even CTA's commits for the last uses of every stage and D buffer have landed
@@ -921,29 +1021,12 @@ __device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const
         for (int j = (nK > DST ? nK - DST : 0); j < nK; ++j)
           if (!mbar_wait_cluster(emptyB + j % DST, (uint32_t)((j / DST) & 1), abort_flag, g.wait_budget)) break;
       }
-      // no W copy may still be landing when the CTA exits
+      // no W or D copy may still be landing when the CTA exits (completed ones return at once)
       for (int s = 0; s < PST; ++s) {
         if (w_last[s] < 0) continue;
         const long long t0 = clock64();
         while (!mbar_try_wait(wfull + s, (uint32_t)((w_last[s] / PST) & 1)) && clock64() - t0 < 400000000LL) {
         }
-      }
-    }
-    __syncwarp();
-  } else if (warp == NWORK + 2) {
-    // ------------------------------------------- D-slice loads (1 thread per CTA)
-    if (lane == 0) {
-      int d_last[DST];
-#pragma unroll
-      for (int q = 0; q < DST; ++q) d_last[q] = -1;
-      for (int j = 0; j < nK; ++j) {
-        const int q = j % DST;
-        if (j >= DST &&
-            !mbar_wait_cluster(emptyB + q, (uint32_t)(((j / DST) - 1) & 1), abort_flag, g.wait_budget))
-          break;
-        mbar_arrive_expect_tx(dfull + q, (uint32_t)Geo::D_BYTES);
-        tma_load_3d(smem + Geo::D_OFF + q * Geo::D_BYTES, map_d, dfull + q, j * KS, n0, 0);
-        d_last[q] = j;
       }
       for (int q = 0; q < DST; ++q) {
         if (d_last[q] < 0) continue;
@@ -974,9 +1057,11 @@ __device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const
     }
     const uint32_t trow = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(32 * (w >> 2));
     const uint32_t lead_acc_empty = mapa(smem_u32(acc_empty), 0u);
-    float Vh[32], Vl[32];  // running sums of this thread's 32 accumulator cells
+    // high parts of the running sums of this thread's 32 accumulator cells (lane = energy row
+    // 32 (w & 3) + lane, columns 32 (w >> 2) + c); the low parts live in the order-3 columns
+    float Vh[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) Vh[c] = Vl[c] = 0.0f;
+    for (int c = 0; c < 32; ++c) Vh[c] = 0.0f;
     bool ok = true;
     // A drain period's accumulators are read LAG k-steps after its last one is formed, so that
     // the operands of the next period's first steps are in place when the MMAs resume.  Forming
@@ -1030,51 +1115,44 @@ __device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const
           break;
         }
         tc_fence_after();
-        // orders 0-2 by TwoSum into (hi, lo); the order-3 sum is of the size of lo
+        const bool last = je == nK - 1;
+        const int e = n0 + 32 * (w & 3) + lane;  // this thread's energy row
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
+        for (int h = 0; h < 2; ++h) {
+          // orders 0-2 into the high parts by TwoSum; their errors and the order-3 column (the
+          // previous low part plus this period's order-3 and order-4 products) make the new low
+          // part, which goes back to the order-3 column, or with the last period to R
+          float lo[16], vh[16];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int c = 0; c < 16; ++c) vh[c] = Vh[h * 16 + c];
+          drain_half(trow, h, vh, lo);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) Vh[h * 16 + c] = vh[c];
+          if (!last) {
             uint32_t r[16];
-            tmem_ld16(trow + (uint32_t)(o * 128 + h * 16), r);
-            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) r[c] = __float_as_uint(lo[c]);
+            tmem_st16(trow + (uint32_t)(384 + h * 16), r);
+          } else if (e < g.ne) {
+            // cells h * 16 + c are the pairs (I0 + 2 (w >> 2) + h, J0 + c)
+            const int64_t np = (int64_t)n * (n + 1) / 2;
+            const int pi = I0 + 2 * (w >> 2) + h;
+            const double te = g.tau[g.e_begin + e];
+            double* Re = g.R + (int64_t)e * np;
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-              const int i = h * 16 + c;
-              const float x = __uint_as_float(r[c]);
-              if (o < 3) {
-                float sh, se;
-                two_sum(Vh[i], x, sh, se);
-                Vh[i] = sh;
-                Vl[i] = __fadd_rn(Vl[i], se);
-              } else {
-                Vl[i] = __fadd_rn(Vl[i], x);
+              const int pj = J0 + c;
+              if (pi < n && pj < n && pi <= pj) {
+                const int64_t p = pair_index(n, pi, pj);
+                if (RM_CHECK(p >= 0 && p < np)) Re[p] = ((double)Vh[h * 16 + c] + (double)lo[c]) * g.f_p[p] * te;
               }
             }
           }
         }
+        if (!last) tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive_cluster(lead_acc_empty);
-      }
-    }
-    // ------------------------------------------------------------- epilogue
-    // lane = energy row of this CTA's tile, columns = pairs
-    if (ok) {
-      const int e = n0 + 32 * (w & 3) + lane;
-      if (e < g.ne) {
-        const int64_t np = (int64_t)n * (n + 1) / 2;
-        const double te = g.tau[g.e_begin + e];
-        double* Re = g.R + (int64_t)e * np;
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int col = 32 * (w >> 2) + c;
-          const int pi = I0 + col / 16, pj = J0 + col % 16;
-          if (pi < n && pj < n && pi <= pj) {
-            const int64_t p = pair_index(n, pi, pj);
-            if (RM_CHECK(p >= 0 && p < np)) Re[p] = ((double)Vh[c] + (double)Vl[c]) * g.f_p[p] * te;
-          }
-        }
       }
     }
   }
@@ -1092,7 +1170,7 @@ __device__ __forceinline__ void tc_pair_tile(const CUtensorMap* map_omega, const
 // blockIdx.x is the CTA's rank in its pair, blockIdx.y its pair tile and blockIdx.z the pair of
 // energy tiles; consecutive clusters hold consecutive pair tiles of the same energies, as in the
 // one-SM launch, and share their D slices in L2.
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(PAIR_NTHREADS, 1)
     polesum_tc_pair_kernel(const TCArgs* __restrict__ waves, const CUtensorMap* __restrict__ maps,
                            const int4* __restrict__ tiles, int64_t e_begin, int ne) {
   extern __shared__ unsigned char smem_raw[];
@@ -1690,7 +1768,7 @@ bool polesum_cluster_ok(int cx, int cy, int ns, bool pair) {
   const bool two_sm = pair_applies(cx, cy, cx == 1, ns, pair);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = two_sm ? dim3(2, 8, 8) : dim3(cx * 8, cy * 8, 1);
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.blockDim = dim3(two_sm ? PAIR_NTHREADS : NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = grouped_smem(cx, cy, cx == 1, ns, pair);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1719,7 +1797,7 @@ cudaError_t launch_polesum_split_grouped(const Plan& p, int64_t e0, int ne, cuda
   // the 2-SM kernel: grid (rank in pair, pair tile, energy-tile pair), clusters of 2 x 1 x 1
   cfg.gridDim = two_sm ? dim3(2, G.n_tiles, (ny + 1) / 2)
                        : dim3(G.n_tiles, (ny + G.tc_cy - 1) / G.tc_cy * G.tc_cy, 1);
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.blockDim = dim3(two_sm ? PAIR_NTHREADS : NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = grouped_smem(G.tc_cx, G.tc_cy, G.dt(), ns, G.tc_pair);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
