@@ -20,7 +20,16 @@
 // fixed grid, so their FP32 sums are exact while below 2^24 of that grid.
 // Every 2048 poles the accumulators are drained into double-float running
 // sums (FP32 hi + lo) by error-free additions (TwoSum), on the FP32 pipe: the
-// sums keep about 48 bits, and the FP64 pipe stays out of the drain.
+// sums keep about 48 bits, and the FP64 pipe stays out of the drain.  With
+// five slices (15 products, the default) the low parts are kept in the
+// order-3 TMEM columns, which the next period's order-3 products add onto,
+// and only the high parts in registers.
+//
+// Two forms of the MMAs: one-SM (tcgen05 cta_group::1; CTA clusters share P or
+// D slices through distributed shared memory) and, for 1 x 2 clusters with D
+// by TMA and 15 products, 2-SM (cta_group::2 on a CTA pair: M = 256 energies,
+// each SM reading its own D slices and the P slices of the 64 pairs it forms).
+// Both sum the same products in the same order per accumulator.
 //
 // Poles with |E_k - E_e| < delta are excluded from the GEMM by per-energy pole
 // index ranges [klo, khi) and summed in FP64 by the near-window kernel, so the

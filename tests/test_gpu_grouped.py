@@ -199,10 +199,9 @@ def test_mma_pair_matches_one_sm(rm, n_e):
     sel = (0, 2)
     outs = {}
     for pair in (0, -1):
-        try:
-            p = rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, cluster=(1, 2), mma_pair=pair)
-        except rm.RMError as ex:
-            pytest.skip(f"1 x 2 clusters not co-schedulable here: {ex}")
+        # both forms must be resident on a GB300: a kernel that cannot be (registers, shared
+        # memory) would make the plan fall back to another shape silently, so this is a failure
+        p = rm.Plan(waves, E, prec="split_bf16", delta=0.05, sel=sel, cluster=(1, 2), mma_pair=pair)
         with p:
             assert p.mma_pair() == (pair == 0)
             p.run()
