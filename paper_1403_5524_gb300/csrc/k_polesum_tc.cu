@@ -197,10 +197,10 @@ __device__ __forceinline__ void d_pack5(float ph0, float pl0, float ph1, float p
 }
 
 // One half h (16 cells) of a drain of the 15-product accumulators: the exact sums of orders 0-2
-// go into the high parts Vh[0..15] by TwoSum (error-free), and lo = (order-3 column) + the three TwoSum
-// errors, in that order.  The order-3 column holds the previous low part plus this period's
-// order-3 and order-4 products (the MMAs accumulate onto it), so the low parts never sit in
-// registers across the k-loop.
+// go into the high parts Vh[0..15] by TwoSum (error-free), lo = (order-3 column) + the three
+// TwoSum errors, in that order, and (Vh, lo) is renormalised by one more TwoSum.  The order-3
+// column holds the previous low part plus this period's order-3 and order-4 products (the MMAs
+// accumulate onto it), so the low parts never sit in registers across the k-loop.
 __device__ __forceinline__ void drain_half(uint32_t trow, int h, float (&Vh)[16], float (&lo)[16]) {
   float t[16];
 #pragma unroll
@@ -220,7 +220,15 @@ __device__ __forceinline__ void drain_half(uint32_t trow, int h, float (&Vh)[16]
   ptx::tmem_ld16(trow + (uint32_t)(384 + h * 16), r);
   ptx::tmem_wait_ld();
 #pragma unroll
-  for (int c = 0; c < 16; ++c) lo[c] = __fadd_rn(__uint_as_float(r[c]), t[c]);
+  for (int c = 0; c < 16; ++c) {
+    // renormalised (exactly, TwoSum) so that the low part carried into the next period is at
+    // most half an ulp of the high part: the order-3 products then accumulate onto the smallest
+    // possible value (the tensor cores' FP32 accumulation loses more on a larger one)
+    float sh, se;
+    two_sum(Vh[c], __fadd_rn(__uint_as_float(r[c]), t[c]), sh, se);
+    Vh[c] = sh;
+    lo[c] = se;
+  }
 }
 
 struct TCArgs {
