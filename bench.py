@@ -33,9 +33,9 @@ METRIC = "energies/sec (R+K+σ) split-precision vs FP64 GPU at n_ch=256; max rel
 FP64_NOMINAL_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU; the measured probe is the peak used
 # DRAM bytes (read + write) per energy, from one ncu capture each of the n_ch=256 / N=20000 wave,
 # 1000-energy launch (the solve; the tensor-core pole sum with its default 15 slice products, as
-# one-SM MMAs); scaled to a launch by its energies.  A kernel changed since its capture has no
-# entry (traffic null), and so has the pole sum with another product set or MMA form.
-DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.777e6, "polesum_split": 1.886e6}
+# 2-SM and as one-SM MMAs); scaled to a launch by its energies.  A kernel changed since its capture
+# has no entry (traffic null), and so has the pole sum with another product set.
+DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.777e6, "polesum_split_pair": 1.721e6}
 PRODUCT_SETS = (3, 6, 10, 13, 15)
 
 
@@ -409,12 +409,15 @@ def run_ours(args):
 
     def traffic(kernel):
         # per-launch DRAM bytes, scaled from the capture (same kernel code, same wave shape)
-        if not single_n256 or kernel not in DRAM_BYTES_PER_ENERGY_N256:
-            return None
-        if kernel == "polesum_split" and (plan.slices() != 15 or plan.mma_pair()):
+        key = kernel
+        if kernel == "polesum_split":
+            if plan.slices() != 15:
+                return None
+            key = "polesum_split_pair" if plan.mma_pair() else "polesum_split_one_sm"
+        if not single_n256 or key not in DRAM_BYTES_PER_ENERGY_N256:
             return None
         e_per_launch = wl.n_e * args.steps / kern[kernel]["launches"]
-        return DRAM_BYTES_PER_ENERGY_N256[kernel] * e_per_launch
+        return DRAM_BYTES_PER_ENERGY_N256[key] * e_per_launch
 
     roof = None
     if dom in flops_per_step:
