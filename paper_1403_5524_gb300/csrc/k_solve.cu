@@ -153,6 +153,43 @@ struct Ops<dfl> {
   __device__ static dfl get(const double* d) { return dfl{(float)d[0], (float)d[1]}; }
 };
 
+// Complex double-float: real and imaginary parts as double-floats (16 bytes, the size of a complex
+// double, so Z factors in place of its FP64 copy).  Each complex multiply-subtract is four
+// double-float ones, about 48 FP32 instructions against 4 DFMA: on GB300 (128 FP32 lanes, 2 DFMA
+// a clock per SM) about five times the rate.  Used for the LDL^T of Z, whose solutions are then
+// refined against an FP64 residual (sym_xsec).
+struct cdf {
+  dfl re, im;
+};
+
+template <>
+struct Ops<cdf> {
+  using D = Ops<dfl>;
+  __device__ static cdf zero() { return cdf{D::zero(), D::zero()}; }
+  __device__ static cdf one() { return cdf{D::one(), D::zero()}; }
+  __device__ static double mag(cdf x) { return fabs(df_to(x.re)) + fabs(df_to(x.im)); }  // cabs1
+  __device__ static cdf inv(cdf x) {
+    // conj(x) / |x|^2, as for the FP64 pivots
+    const dfl q = D::inv(D::fma_acc(D::mul(x.re, x.re), x.im, x.im));
+    const dfl im = D::mul(x.im, q);
+    return cdf{D::mul(x.re, q), dfl{-im.hi, -im.lo}};
+  }
+  __device__ static cdf mul(cdf a, cdf b) {
+    return cdf{D::fms(D::mul(a.re, b.re), a.im, b.im), D::fma_acc(D::mul(a.re, b.im), a.im, b.re)};
+  }
+  // acc - a b
+  __device__ static cdf fms(cdf acc, cdf a, cdf b) {
+    return cdf{D::fma_acc(D::fms(acc.re, a.re, b.re), a.im, b.im), D::fms(D::fms(acc.im, a.re, b.im), a.im, b.re)};
+  }
+  // acc + a b
+  __device__ static cdf fma_acc(cdf acc, cdf a, cdf b) {
+    return cdf{D::fms(D::fma_acc(acc.re, a.re, b.re), a.im, b.im), D::fma_acc(D::fma_acc(acc.im, a.re, b.im), a.im, b.re)};
+  }
+  // a double holds hi + lo exactly (|lo| <= ulp(hi) / 2 leaves at most 48 significant bits)
+  __device__ static void put(double* d, cdf x) { d[0] = df_to(x.re); d[1] = df_to(x.im); }
+  __device__ static cdf get(const double* d) { return cdf{df_from(d[0]), df_from(d[1])}; }
+};
+
 // Panel width: 16 columns for the real LU, 8 for the complex one, so that a
 // panel row is 128 bytes either way and both LUs do the same FMAs per byte of
 // trailing-matrix traffic (16 real or 8 complex multiply-adds per element).
@@ -166,6 +203,7 @@ constexpr int TRI_BYTES = Blk<float>::NB * Blk<float>::NB * 4;  // the largest o
 static_assert(Blk<cplx>::NB * TC * (int)sizeof(cplx) == TILE_BYTES, "tile bytes");
 static_assert(Blk<float>::NB * TC * (int)sizeof(float) == TILE_BYTES, "tile bytes");
 static_assert(sizeof(dfl) == sizeof(double) && Blk<dfl>::NB == Blk<double>::NB, "double-float in place of FP64");
+static_assert(sizeof(cdf) == sizeof(cplx) && Blk<cdf>::NB == Blk<cplx>::NB, "complex double-float in place of FP64");
 
 // smallest power of two >= min(TC, w), at least 1
 __device__ __forceinline__ int tile_width_pow2(int w) {
@@ -1180,6 +1218,127 @@ __device__ void ldl_check(const double* A, int n, int nf, int ld, Red& red, doub
 // Returns true when energy e is finished (outputs written), false when its
 // real eliminations fail the growth / pivot check and the caller must solve it
 // by the LU path (the workspace is then free).
+constexpr double Z_DF_CORR_MAX = 1e-7;  // refined double-float Z solve: largest accepted |d| / |x|
+
+// Z x = e_sel (r unit right-hand sides) through the LDL^T of Z in double-float, then one step of
+// iterative refinement: res = e_sel - Z x in FP64, Z d = res with the double-float factors,
+// x += d.  Z is complex symmetric with a real off-diagonal part, so its FP64 copy is G (n x ld,
+// row i, lower triangle: Re Z) plus its imaginary diagonal, kept in column no of G.  The factors'
+// error in x is about n 2^-46 |K| (at a K pole |K| reaches 1e5, and double-float alone would leave
+// T about 1e-7 out); after the step it is about that squared, so a correction below
+// Z_DF_CORR_MAX of x leaves x at FP64 quality.  On success C holds, as FP64 complex values, what
+// the FP64 factorisation leaves where the caller reads it: the pivots on the diagonal and x in
+// columns no .. no + r.  Otherwise (false, uniform) C holds double-float factors and the caller
+// forms Z again from G.
+__device__ bool z_ldl_refined(cplx* C, int no, int r, int ldC, double* G, int ld, const int32_t* sel,
+                              unsigned char* panel_b, unsigned char* tile_b, unsigned char* tmp_b,
+                              unsigned char* tri_b, Red& red) {
+  using O = Ops<cdf>;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int mc = no + r;
+  // FP64 copy of Z: the real lower triangle and the imaginary diagonal
+  for (int64_t idx = t; idx < (int64_t)no * no; idx += NT) {
+    const int i = (int)(idx / no), j = (int)(idx % no);
+    if (j > i) continue;
+    const cplx v = C[(int64_t)i * ldC + j];
+    G[(int64_t)i * ld + j] = v.re;
+    if (j == i) G[(int64_t)i * ld + no] = v.im;
+  }
+  __syncthreads();
+  // Z and the right-hand sides into double-float, in place
+  cdf* Cd = reinterpret_cast<cdf*>(C);
+  for (int64_t idx = t; idx < (int64_t)no * mc; idx += NT) {
+    const int i = (int)(idx / mc), j = (int)(idx % mc);
+    if (j < no && j > i) continue;
+    const cplx v = C[(int64_t)i * ldC + j];
+    Cd[(int64_t)i * ldC + j] = cdf{df_from(v.re), df_from(v.im)};
+  }
+  __syncthreads();
+  LUStat st;
+  ldl_solve<cdf>(Cd, no, mc, ldC, reinterpret_cast<cdf*>(panel_b), reinterpret_cast<cdf*>(tile_b),
+                 reinterpret_cast<cdf*>(tmp_b), reinterpret_cast<cdf*>(tri_b), st);
+  __syncthreads();
+  // the panel area (a 128-byte row per channel) holds, per group of four right-hand sides,
+  // x in FP64 (slots 0-3) and the residual, then the correction, in double-float (slots 4-7)
+  cplx* xs = reinterpret_cast<cplx*>(panel_b);
+  cdf* ys = reinterpret_cast<cdf*>(panel_b);
+  bool good = true;
+  for (int q0 = 0; q0 < r; q0 += 4) {
+    const int nq = min(4, r - q0);
+    for (int idx = t; idx < no * nq; idx += NT) {
+      const int i = idx / nq, q = idx % nq;
+      const cdf v = Cd[(int64_t)i * ldC + no + q0 + q];
+      xs[i * 8 + q] = cplx{df_to(v.re), df_to(v.im)};
+    }
+    __syncthreads();
+    // res = e - Z x, a warp per row: (Z x)_i = sum_j Re Z_ij x_j + i Im Z_ii x_i
+    for (int i = warp; i < no; i += NWARP) {
+      for (int q = 0; q < nq; ++q) {
+        double ar = 0.0, ai = 0.0;
+        for (int j = lane; j < no; j += 32) {
+          const double z = (j <= i) ? G[(int64_t)i * ld + j] : G[(int64_t)j * ld + i];
+          const cplx xv = xs[j * 8 + q];
+          ar = fma(z, xv.re, ar);
+          ai = fma(z, xv.im, ai);
+        }
+        ar = warp_sum(ar);
+        ai = warp_sum(ai);
+        if (lane == 0) {
+          const double zi = G[(int64_t)i * ld + no];
+          const cplx xi = xs[i * 8 + q];
+          const double ev = (sel[q0 + q] == i) ? 1.0 : 0.0;
+          ys[i * 8 + 4 + q] = cdf{df_from(ev - fma(-zi, xi.im, ar)), df_from(-fma(zi, xi.re, ai))};
+        }
+      }
+    }
+    __syncthreads();
+    // d = L^-T D^-1 L^-1 res with the double-float factors (L unit lower, by columns, then rows)
+    for (int k = 0; k + 1 < no; ++k) {
+      for (int idx = t; idx < (no - 1 - k) * nq; idx += NT) {
+        const int i = k + 1 + idx / nq, q = idx % nq;
+        ys[i * 8 + 4 + q] = O::fms(ys[i * 8 + 4 + q], Cd[(int64_t)i * ldC + k], ys[k * 8 + 4 + q]);
+      }
+      __syncthreads();
+    }
+    for (int idx = t; idx < no * nq; idx += NT) {
+      const int i = idx / nq, q = idx % nq;
+      ys[i * 8 + 4 + q] = O::mul(ys[i * 8 + 4 + q], O::inv(Cd[(int64_t)i * ldC + i]));
+    }
+    __syncthreads();
+    for (int k = no - 1; k > 0; --k) {
+      for (int idx = t; idx < k * nq; idx += NT) {
+        const int i = idx / nq, q = idx % nq;
+        ys[i * 8 + 4 + q] = O::fms(ys[i * 8 + 4 + q], Cd[(int64_t)k * ldC + i], ys[k * 8 + 4 + q]);
+      }
+      __syncthreads();
+    }
+    // x += d, into C's solution columns (their double-float values are no longer needed)
+    double dmax = 0.0, xmax = 0.0;
+    for (int idx = t; idx < no * nq; idx += NT) {
+      const int i = idx / nq, q = idx % nq;
+      const cdf d = ys[i * 8 + 4 + q];
+      const double dr = df_to(d.re), di = df_to(d.im);
+      const cplx x = xs[i * 8 + q];
+      const cplx xn = cplx{x.re + dr, x.im + di};
+      dmax = fmax(dmax, fabs(dr) + fabs(di));
+      xmax = fmax(xmax, fabs(xn.re) + fabs(xn.im));
+      C[(int64_t)i * ldC + no + q0 + q] = xn;
+      if (!(fabs(dr) + fabs(di) <= 1e300)) dmax = INFINITY;  // NaN from a zero pivot
+    }
+    dmax = block_max(dmax, red);
+    xmax = block_max(xmax, red);
+    if (!(dmax <= Z_DF_CORR_MAX * xmax)) good = false;
+  }
+  if (!good) return false;
+  // the pivots, in FP64, on the diagonal
+  for (int i = t; i < no; i += NT) {
+    const cdf d = Cd[(int64_t)i * ldC + i];
+    C[(int64_t)i * ldC + i] = cplx{df_to(d.re), df_to(d.im)};
+  }
+  __syncthreads();
+  return true;
+}
+
 __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned char* smem_raw, Red& red) {
   const int n = g.n, nc = n - no, t = threadIdx.x, lane = t & 31;
   unsigned char* panel_b = smem_raw;
@@ -1311,8 +1470,31 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
   const bool ok = ok_c && (growth_s <= SYM_GROWTH_MAX_INERTIA) && (piv_s >= SYM_PIVOT_MIN);
   if (!ok) return false;  // uniform: the values come from block reductions
   // ------------------------------------- complex LDL^T of Z, x = Z^-1 e_sel
-  ldl_solve<cplx>(C, no, mc, g.ldC, reinterpret_cast<cplx*>(panel_b), reinterpret_cast<cplx*>(tile_b),
-                  reinterpret_cast<cplx*>(tmp_b), reinterpret_cast<cplx*>(tri_b), st);
+  // In double-float with one FP64 refinement step (z_ldl_refined; G: the S'' block, free once
+  // its inertia is counted); FP64 for dipole waves and where the refinement's correction is large.
+  bool z_done = false;
+  if (!photo) {
+    z_done = z_ldl_refined(C, no, r, g.ldC, As, ld, g.sel, panel_b, tile_b, tmp_b, tri_b, red);
+    if (!z_done) {
+      // Z again from its FP64 copy in G, with the unit right-hand sides
+      for (int64_t idx = t; idx < (int64_t)no * mc; idx += NT) {
+        const int i = (int)(idx / mc), j = (int)(idx % mc);
+        cplx v;
+        if (j < no) {
+          if (j > i) continue;
+          v = cplx{As[(int64_t)i * ld + j], (j == i) ? As[(int64_t)i * ld + no] : 0.0};
+        } else {
+          v = cplx{(g.sel[j - no] == i) ? 1.0 : 0.0, 0.0};
+        }
+        C[(int64_t)i * g.ldC + j] = v;
+      }
+      __syncthreads();
+      fl |= RM_FLAG_FP64;
+    }
+  }
+  if (!z_done)
+    ldl_solve<cplx>(C, no, mc, g.ldC, reinterpret_cast<cplx*>(panel_b), reinterpret_cast<cplx*>(tile_b),
+                    reinterpret_cast<cplx*>(tmp_b), reinterpret_cast<cplx*>(tri_b), st);
   // eta = -arg det(I - iK) = -(sum_j [arg h'_j + arg d_j + pi (c'_j < 0)] - pi neg(S''))  (mod 2 pi)
   double ph = 0.0;
   for (int j = t; j < no; j += NT) {
