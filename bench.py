@@ -37,6 +37,9 @@ FP64_NOMINAL_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU; the measured 
 # has no entry (traffic null), and so has the pole sum with another product set.
 DRAM_BYTES_PER_ENERGY_N256 = {"solve": 9.777e6, "polesum_split_pair": 1.721e6}
 PRODUCT_SETS = (3, 6, 10, 13, 15)
+# FP32 instructions per flop of the solve's double-float arithmetic: a double-float multiply-subtract
+# (an error-free product by FMA, TwoSum, renormalisation) is 15 FP32 instructions for 2 flops
+DF_INSTR_PER_FLOP = 7.5
 
 
 def measured_peaks():
@@ -179,17 +182,20 @@ def workload(args):
 def algorithmic_flops(wl, n_open_by_wave, flags_by_wave, n_sel, solve):
     """Per-step FLOP counts of the method (not counting slice products).
 
-    Pole sum 2 n_p N per energy.  Solve, per energy, the FP64 flops of the path
-    the energy took:
-    * outgoing-wave path (solve "fp64"): real LDL^T over the closed channels,
-      (n^3 - n_o^3) / 3, then the complex symmetric LDL^T of Z, (4/3) n_o^3
-      (n_o^3 / 6 complex multiply-adds), and its r unit right-hand sides,
-      8 n_o^2 r.  The real LDL^T of S'' (n_o^3 / 3), whose pivots give only
-      the sign of det S''_oo, runs in double-float on the FP32 pipe: it is
-      returned apart (``df``) and not counted as FP64 work;
+    Pole sum 2 n_p N per energy.  Solve, per energy, the flops of the path the
+    energy took, FP64 and double-float (FP32 pipe) apart:
+    * outgoing-wave path (solve "fp64"): in FP64 the real LDL^T over the closed
+      channels, (n^3 - n_o^3) / 3, and the refinement residual of Z's solutions,
+      4 n_o^2 r; in double-float the real LDL^T of S'' (n_o^3 / 3, the sign of
+      det S''_oo; energies flagged RM_FLAG_FP64 redo it in FP64), the complex
+      symmetric LDL^T of Z, (4/3) n_o^3 (n_o^3 / 6 complex multiply-adds), with
+      its r unit right-hand sides and the refinement's correction solves,
+      16 n_o^2 r.  Waves with a dipole vector factor Z in FP64 ((4/3) n_o^3 +
+      8 n_o^2 (r + 1));
     * LU path ("fp64_lu", "mixed", or RM_FLAG_LU energies, which also paid for
-      the outgoing-wave attempt): LU (2/3) n^3 + 2 n^2 n_o with dense
+      the outgoing-wave attempt up to S''): LU (2/3) n^3 + 2 n^2 n_o with dense
       right-hand sides, then the LDL^T of I - iK, (4/3) n_o^3 + 8 n_o^2 r.
+    Returns (pole, FP64 solve flops, double-float solve flops).
     """
     pole = 0.0
     solve_fl = 0.0
@@ -200,14 +206,24 @@ def algorithmic_flops(wl, n_open_by_wave, flags_by_wave, n_sel, solve):
         pole += 2.0 * npair * w.N * wl.n_e
         no = no.astype(np.float64)
         live = no > 0
-        sym = (n ** 3 - no ** 3) / 3.0 + (4.0 / 3.0) * no ** 3 + 8.0 * no * no * n_sel
         lu = (2.0 / 3.0) * n ** 3 + 2.0 * n * n * no + (4.0 / 3.0) * no ** 3 + 8.0 * no * no * n_sel
         if solve == "fp64":
-            per = np.where((fl & 64) != 0, sym + lu, sym)
-            df += float(np.sum(np.where(live, no ** 3 / 3.0, 0.0)))
+            closed = (n ** 3 - no ** 3) / 3.0
+            s2 = no ** 3 / 3.0
+            s2_fp64 = (fl & 32) != 0
+            on_lu = (fl & 64) != 0
+            if getattr(w, "dip", None) is not None:
+                z64 = (4.0 / 3.0) * no ** 3 + 8.0 * no * no * (n_sel + 1)
+                zdf = 0.0 * no
+            else:
+                z64 = 4.0 * no * no * n_sel
+                zdf = (4.0 / 3.0) * no ** 3 + 16.0 * no * no * n_sel
+            per64 = closed + np.where(s2_fp64, s2, 0.0) + np.where(on_lu, lu, z64)
+            perdf = np.where(s2_fp64, 0.0, s2) + np.where(on_lu, 0.0, zdf)
+            df += float(np.sum(np.where(live, perdf, 0.0)))
         else:
-            per = lu
-        solve_fl += float(np.sum(np.where(live, per, 0.0)))
+            per64 = lu
+        solve_fl += float(np.sum(np.where(live, per64, 0.0)))
     return pole, solve_fl, df
 
 
@@ -404,6 +420,11 @@ def run_ours(args):
     for k in kern:
         if k in flops_per_step:
             kern[k]["tflops_algorithmic"] = flops_per_step[k] * args.steps / (kern[k]["ms_total"] / 1000.0) / 1e12
+    if "solve" in kern and args.solve == "fp64":
+        # FP64 and double-float flops together; tflops_fp64: the FP64 part alone
+        kern["solve"]["tflops_fp64"] = kern["solve"]["tflops_algorithmic"]
+        kern["solve"]["tflops_algorithmic"] = ((solve_flops + df_flops) * args.steps
+                                               / (kern["solve"]["ms_total"] / 1000.0) / 1e12)
     peaks = measured_peaks()
     single_n256 = len(wl.waves) == 1 and wl.waves[0].n == 256 and wl.waves[0].N == 20000
 
@@ -420,7 +441,41 @@ def run_ours(args):
         return DRAM_BYTES_PER_ENERGY_N256[key] * e_per_launch
 
     roof = None
-    if dom in flops_per_step:
+    if dom == "solve" and args.solve == "fp64":
+        # two pipes: FP64 work at the probe's rate, double-float work at DF_INSTR_PER_FLOP FP32
+        # instructions per flop, 128 FP32 lanes per SM at the clock sampled under load; frac is
+        # the time the work would take with each pipe at its peak, one after the other, over the
+        # kernel's time
+        n_l = kern[dom]["launches"]
+        avg_ms = kern[dom]["ms_total"] / n_l
+        fl64 = solve_flops * args.steps / n_l
+        fldf = df_flops * args.steps / n_l
+        pk64 = peak64["tflops"] if peak64 else FP64_NOMINAL_TFLOPS
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+        pk32 = 128.0 * sms * mhz * 1e6 / 1e12  # FP32 instructions, tera per second
+        t64 = fl64 / (pk64 * 1e12)
+        tdf = fldf * DF_INSTR_PER_FLOP / (pk32 * 1e12)
+        t = avg_ms / 1000.0
+        roof = {"kernel": dom, "bound": "alu", "achieved": (fl64 + fldf) / t / 1e12,
+                "peak": (fl64 + fldf) / (t64 + tdf) / 1e12, "unit": "TFLOP/s", "frac": (t64 + tdf) / t,
+                "traffic": traffic(dom),
+                "peak_source": ("the work's mix at its pipes' peaks: FP64 at the DFMA probe's rate measured in "
+                                "this run (libpeak.so, burst), double-float at %.1f FP32 instructions per flop "
+                                "on 128 FP32 lanes x %d SMs at %.0f MHz (the SM clock sampled under load)"
+                                % (DF_INSTR_PER_FLOP, sms, mhz)
+                                if peak64 else "FP64 nominal 1.25 TFLOP/s (the probe could not run); "
+                                "double-float on 128 FP32 lanes per SM"),
+                "fp64_flops_per_launch": fl64, "df_flops_per_launch": fldf,
+                "fp64_pipe_frac": t64 / t, "fp32_pipe_frac": tdf / t,
+                "peak_fp64": pk64, "peak_fp32_tinstr": pk32, "peak_probe": peak64, "avg_launch_ms": avg_ms,
+                "flop_model": ("per energy, FP64: (n^3 - n_o^3)/3 (real LDL^T over the closed channels) + "
+                               "4 n_o^2 r (refinement residual of Z's solutions); double-float: n_o^3/3 (inertia "
+                               "LDL^T of S'') + (4/3)n_o^3 + 16 n_o^2 r (complex LDL^T of Z, its unit right-hand "
+                               "sides and the correction solves); RM_FLAG_LU energies add the LU path in FP64 "
+                               "(2/3)n^3 + 2n^2 n_o + (4/3)n_o^3 + 8 n_o^2 r, RM_FLAG_FP64 ones S'' in FP64, "
+                               "dipole waves Z in FP64")}
+    elif dom in flops_per_step:
         total_fl = flops_per_step[dom] * args.steps
         n_l = kern[dom]["launches"]
         avg_ms = kern[dom]["ms_total"] / n_l
