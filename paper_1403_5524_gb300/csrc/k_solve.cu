@@ -127,8 +127,11 @@ struct Ops<dfl> {
   __device__ static dfl one() { return dfl{1.0f, 0.0f}; }
   __device__ static double mag(dfl x) { return fabs(df_to(x)); }
   __device__ static dfl inv(dfl x) {
-    const float r = __fdiv_rn(1.0f, x.hi);
-    float e = __fmaf_rn(-x.hi, r, 1.0f);  // exact residual of the FP32 reciprocal
+    // approximate FP32 reciprocal (about 2^-23), then one correction with the residual, exact in
+    // its FP32 part: about 2^-46 relative, as for a correctly rounded first guess
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x.hi));
+    float e = __fmaf_rn(-x.hi, r, 1.0f);
     e = __fmaf_rn(-x.lo, r, e);
     return df_quick(r, __fmul_rn(r, e));
   }
@@ -149,8 +152,9 @@ struct Ops<dfl> {
     return df_quick(s, __fadd_rn(err, __fsub_rn(acc.lo, pe)));
   }
   __device__ static dfl fma_acc(dfl acc, dfl a, dfl b) { return fms(acc, dfl{-a.hi, -a.lo}, b); }
-  __device__ static void put(double* d, dfl x) { d[0] = x.hi; d[1] = x.lo; }
-  __device__ static dfl get(const double* d) { return dfl{(float)d[0], (float)d[1]}; }
+  // kept bitwise in the first 8 bytes of the 16-byte slot (no FP64 conversions on the FP32 path)
+  __device__ static void put(double* d, dfl x) { *reinterpret_cast<dfl*>(d) = x; }
+  __device__ static dfl get(const double* d) { return *reinterpret_cast<const dfl*>(d); }
 };
 
 // Complex double-float: real and imaginary parts as double-floats (16 bytes, the size of a complex
@@ -185,9 +189,9 @@ struct Ops<cdf> {
   __device__ static cdf fma_acc(cdf acc, cdf a, cdf b) {
     return cdf{D::fms(D::fma_acc(acc.re, a.re, b.re), a.im, b.im), D::fma_acc(D::fma_acc(acc.im, a.re, b.im), a.im, b.re)};
   }
-  // a double holds hi + lo exactly (|lo| <= ulp(hi) / 2 leaves at most 48 significant bits)
-  __device__ static void put(double* d, cdf x) { d[0] = df_to(x.re); d[1] = df_to(x.im); }
-  __device__ static cdf get(const double* d) { return cdf{df_from(d[0]), df_from(d[1])}; }
+  // kept bitwise in the 16-byte slot (no FP64 conversions on the FP32 path)
+  __device__ static void put(double* d, cdf x) { *reinterpret_cast<cdf*>(d) = x; }
+  __device__ static cdf get(const double* d) { return *reinterpret_cast<const cdf*>(d); }
 };
 
 // Panel width: 16 columns for the real LU, 8 for the complex one, so that a
