@@ -98,6 +98,8 @@ typedef enum {
                                 zero pivot) and the matching system was solved in FP64 instead;
                                 RM_SOLVE_FP64 (rm_run / rm_xsec): the double-float LDL^T of S'' that gives
                                 the sign of det S_oo failed its growth or pivot check and S'' was
+                                factored in FP64 instead, or (split precisions) the refinement of the
+                                double-float solution of Z made a correction above 1e-7 and Z was
                                 factored in FP64 instead (same results) */
 #define RM_FLAG_LU 64u       /* rm_run / rm_xsec with solve_prec = RM_SOLVE_FP64: the outgoing-wave
                                 factorisation failed its growth or pivot check and the energy was solved
@@ -121,6 +123,9 @@ typedef enum {
    whose real elimination shows large growth or a tiny pivot goes through LU, RM_FLAG_LU);
    the sign of det S_oo comes from the inertia of S'' = V S_oo V (V = diag(c' / |h'|)), factored
    in double-float on the FP32 pipe, or in FP64 where that fails its checks (RM_FLAG_FP64);
+   with split precisions Z itself is factored in double-float (FP32 hi + lo pairs, about 48 bits)
+   and its solutions refined once against an FP64 residual (FP64 again where the correction
+   exceeds 1e-7 of the solution, RM_FLAG_FP64; FP64 plans and dipole waves factor Z in FP64);
    dipole waves' photoionisation amplitudes come from one more right-hand side of Z.
    FP64_LU: the LU path for every energy.  MIXED: LU in FP32, then iterative refinement
    with residuals r = -B - M Y in double-float (FP32 hi + lo, error-free products and sums, about

@@ -3,7 +3,9 @@
 // Two forms.  Cross sections, eigenphase sums and photoionisation (rm_run,
 // rm_xsec) come from the outgoing-wave form (sym_xsec below): the closed
 // channels eliminated by a real LDL^T, one complex symmetric LDL^T of
-// Z = G - diag(h / (a h')) on the open ones, no K.  The K-matrix (rm_kmatrix),
+// Z = G - diag(h / (a h')) on the open ones, no K.  With split-precision plans
+// the LDL^T of Z runs in double-float on the FP32 pipe, its solutions refined
+// once against an FP64 residual (z_ldl_refined).  The K-matrix (rm_kmatrix),
 // the mixed-precision option, and energies whose real eliminations fail their
 // checks take the LU form described next.
 //
@@ -106,8 +108,9 @@ struct Ops<cplx> {
 
 // Double-float: a value hi + lo of two FP32 numbers (about 48 bits), with error-free products
 // (FMA) and sums (Knuth's TwoSum) on the FP32 pipe, which GB300 runs about 64 times faster than
-// its FP64 pipe.  Used for the one factorisation whose results only decide signs: the inertia
-// LDL^T of S'' (sym_xsec).  Same size as a double, so it factors in place of the FP64 matrix.
+// its FP64 pipe.  Used for the inertia LDL^T of S'' (whose results only decide a sign) and, in
+// complex pairs (cdf), for the LDL^T of Z (sym_xsec).  Same size as a double, so it factors in
+// place of the FP64 matrix.
 struct dfl {
   float hi, lo;
 };
@@ -1003,6 +1006,7 @@ struct SolveArgs {
   double e0;        // initial bound-state energy (Ry)
   int mixed;        // 1: matching solve in FP32 + double-float iterative refinement
   int lu_only;      // 1: no outgoing-wave path; every energy through LU
+  int z_df;         // 1 (split-precision plans): Z factored in double-float and refined in FP64
   int64_t mix_off;  // doubles from a slot's start to its mixed-precision area
   const double* asym;
   int64_t ld_asym;  // stride between lam, s, sp, c blocks
@@ -1474,10 +1478,11 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
   const bool ok = ok_c && (growth_s <= SYM_GROWTH_MAX_INERTIA) && (piv_s >= SYM_PIVOT_MIN);
   if (!ok) return false;  // uniform: the values come from block reductions
   // ------------------------------------- complex LDL^T of Z, x = Z^-1 e_sel
-  // In double-float with one FP64 refinement step (z_ldl_refined; G: the S'' block, free once
-  // its inertia is counted); FP64 for dipole waves and where the refinement's correction is large.
+  // Split-precision plans: in double-float with one FP64 refinement step (z_ldl_refined; G: the
+  // S'' block, free once its inertia is counted); FP64 for FP64 plans, for dipole waves and where
+  // the refinement's correction is large.
   bool z_done = false;
-  if (!photo) {
+  if (!photo && g.z_df) {
     z_done = z_ldl_refined(C, no, r, g.ldC, As, ld, g.sel, panel_b, tile_b, tmp_b, tri_b, red);
     if (!z_done) {
       // Z again from its FP64 copy in G, with the unit right-hand sides
@@ -1935,6 +1940,7 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   g.e0 = w.e0;
   g.mixed = p.solve_mixed;
   g.lu_only = p.solve_lu;
+  g.z_df = is_split_like(p.prec) ? 1 : 0;
   g.mix_off = solve_mix_offset(p.n_max, p.n_sel + 1);
   g.asym = asym;
   g.ld_asym = ld_chunk;
@@ -1975,6 +1981,7 @@ cudaError_t group_setup_solve(Plan& p) {
     a.e0 = w.e0;
     a.mixed = p.solve_mixed;
     a.lu_only = p.solve_lu;
+    a.z_df = is_split_like(p.prec) ? 1 : 0;
     a.mix_off = solve_mix_offset(p.n_max, p.n_sel + 1);
     a.asym = G.asym[g];
     a.ld_asym = (int64_t)G.chunk * w.n;
