@@ -1006,7 +1006,8 @@ struct SolveArgs {
   double e0;        // initial bound-state energy (Ry)
   int mixed;        // 1: matching solve in FP32 + double-float iterative refinement
   int lu_only;      // 1: no outgoing-wave path; every energy through LU
-  int z_df;         // 1 (split-precision plans): Z factored in double-float and refined in FP64
+  int z_df;         // 1 (split-precision plans): Z factored in double-float and refined in FP64;
+                    // 2: as 1, but every energy takes the FP64 fallback (test hook)
   int64_t mix_off;  // doubles from a slot's start to its mixed-precision area
   const double* asym;
   int64_t ld_asym;  // stride between lam, s, sp, c blocks
@@ -1240,7 +1241,7 @@ constexpr double Z_DF_CORR_MAX = 1e-7;  // refined double-float Z solve: largest
 // forms Z again from G.
 __device__ bool z_ldl_refined(cplx* C, int no, int r, int ldC, double* G, int ld, const int32_t* sel,
                               unsigned char* panel_b, unsigned char* tile_b, unsigned char* tmp_b,
-                              unsigned char* tri_b, Red& red) {
+                              unsigned char* tri_b, Red& red, bool force_fp64) {
   using O = Ops<cdf>;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int mc = no + r;
@@ -1337,7 +1338,7 @@ __device__ bool z_ldl_refined(cplx* C, int no, int r, int ldC, double* G, int ld
     xmax = block_max(xmax, red);
     if (!(dmax <= Z_DF_CORR_MAX * xmax)) good = false;
   }
-  if (!good) return false;
+  if (!good || force_fp64) return false;
   // the pivots, in FP64, on the diagonal
   for (int i = t; i < no; i += NT) {
     const cdf d = Cd[(int64_t)i * ldC + i];
@@ -1483,7 +1484,7 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
   // the refinement's correction is large.
   bool z_done = false;
   if (!photo && g.z_df) {
-    z_done = z_ldl_refined(C, no, r, g.ldC, As, ld, g.sel, panel_b, tile_b, tmp_b, tri_b, red);
+    z_done = z_ldl_refined(C, no, r, g.ldC, As, ld, g.sel, panel_b, tile_b, tmp_b, tri_b, red, g.z_df == 2);
     if (!z_done) {
       // Z again from its FP64 copy in G, with the unit right-hand sides
       for (int64_t idx = t; idx < (int64_t)no * mc; idx += NT) {
@@ -1940,7 +1941,7 @@ cudaError_t launch_solve(const Plan& p, const WaveDev& w, int64_t e0, int ne, co
   g.e0 = w.e0;
   g.mixed = p.solve_mixed;
   g.lu_only = p.solve_lu;
-  g.z_df = is_split_like(p.prec) ? 1 : 0;
+  g.z_df = is_split_like(p.prec) ? (p.z_force_fp64 ? 2 : 1) : 0;
   g.mix_off = solve_mix_offset(p.n_max, p.n_sel + 1);
   g.asym = asym;
   g.ld_asym = ld_chunk;
@@ -1981,7 +1982,7 @@ cudaError_t group_setup_solve(Plan& p) {
     a.e0 = w.e0;
     a.mixed = p.solve_mixed;
     a.lu_only = p.solve_lu;
-    a.z_df = is_split_like(p.prec) ? 1 : 0;
+    a.z_df = is_split_like(p.prec) ? (p.z_force_fp64 ? 2 : 1) : 0;
     a.mix_off = solve_mix_offset(p.n_max, p.n_sel + 1);
     a.asym = G.asym[g];
     a.ld_asym = (int64_t)G.chunk * w.n;

@@ -675,6 +675,7 @@ rm_status_t rm_plan_create(rm_plan_t* out, const rm_wave* waves, int32_t n_waves
     p->slices = o.slices ? o.slices : (o.prec == RM_PREC_SPLIT_FP16 ? 13 : RM_DEFAULT_SLICES);
     p->grp.tc_pair = o.mma_pair >= 0;
     p->fault_wait = env_ll("RM_FAULT_WAIT_CYCLES");
+    p->z_force_fp64 = env_ll("RM_TEST_Z_FP64") == 1 ? 1 : 0;
     p->n_sel = n_sel;
     std::memcpy(p->sel, sel, sizeof(sel));
     p->sm_count = prop.multiProcessorCount;

@@ -200,6 +200,9 @@ struct Plan {
   // test hooks, read from the environment at plan creation (host-side fault injection):
   // RM_FAULT_WAIT_CYCLES shortens every mbarrier wait of unclustered tensor-core launches
   long long fault_wait = 0;
+  // RM_TEST_Z_FP64 = 1 makes every double-float solve of Z (split modes) take its FP64 fallback,
+  // as if its refinement correction had been too large, so that a test can run that path
+  int z_force_fp64 = 0;
 };
 
 // ---------------------------------------------------------------------------

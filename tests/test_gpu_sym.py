@@ -268,3 +268,29 @@ def test_s2_fp64_retry_energies(rm):
     keep = np.array([t for t in range(pick.size) if not ref["flags"][t] & orc.FLAG_ILLCOND], dtype=np.int64)
     assert keep.size
     close({k: v[pick[keep]] for k, v in a.items()}, {k: v[keep] for k, v in as_ref(ref).items()}, tol=1e-8)
+
+
+def test_z_double_float_against_its_fp64_fallback(rm, monkeypatch):
+    # split plans factor Z in double-float and refine its solutions once against an FP64 residual;
+    # where the correction is large the energy takes Z again in FP64 (RM_FLAG_FP64).  The test hook
+    # RM_TEST_Z_FP64=1 (read at plan creation) sends every energy down that fallback, so both paths
+    # run on the same R: they must agree at the FP64 tolerances (and the double-float one with the
+    # LU path and the oracle), on a block of the n_ch = 64 mesh (1..64 open channels, two initial
+    # channels) and on the n_ch = 256 mesh's first energies
+    for wl in (synth.config(2), synth.config(3)):
+        wl = synth.Workload(wl.name, wl.waves, wl.energies[7000:7240:2].copy(), delta=wl.delta)
+        sel = (0, 1)
+        a = run(rm, wl, "fp64", sel=sel, prec="split_bf16")
+        monkeypatch.setenv("RM_TEST_Z_FP64", "1")
+        f = run(rm, wl, "fp64", sel=sel, prec="split_bf16")
+        monkeypatch.delenv("RM_TEST_Z_FP64")
+        sym = (a["flags"] & (FLAG_LU | orc.FLAG_NO_OPEN)) == 0
+        assert np.all(f["flags"][sym] & FLAG_FP64), "the hook did not reach the fallback"
+        assert np.array_equal(a["n_open"], f["n_open"])
+        close(a, f, idx=np.flatnonzero(sym))
+        b = run(rm, wl, "fp64_lu", sel=sel, prec="split_bf16")  # the same R, solved by LU in FP64
+        close(a, b, idx=np.flatnonzero(sym & ((b["flags"] & orc.FLAG_ILLCOND) == 0)))
+        pick = np.array([3, 40, 77, 119])
+        ref = orc.sweep(wl.waves[0], wl.energies, sel=sel, energy_idx=pick, keep_R=False, keep_K=False)
+        keep = np.array([t for t in range(pick.size) if not ref["flags"][t] & orc.FLAG_ILLCOND], dtype=np.int64)
+        close({k: v[pick[keep]] for k, v in a.items()}, {k: v[keep] for k, v in as_ref(ref).items()}, tol=1e-8)
