@@ -123,6 +123,25 @@ __device__ __forceinline__ dfl df_from(double v) {
   return dfl{h, __double2float_rn(v - (double)h)};
 }
 __device__ __forceinline__ double df_to(dfl x) { return (double)x.hi + (double)x.lo; }
+// As df_from, with integer and FP32 operations only (GB300's FP64 pipe, which also runs the
+// double <-> float conversions, is 1/64 of the FP32 rate): hi takes v's sign, exponent and top 24
+// significand bits, lo the remaining 29 bits (rounded to FP32), then one FastTwoSum rounds hi to
+// nearest.  Values whose parts would leave FP32's normal range (zero, |v| < 2^-74, |v| >= 2^128,
+// non-finite) take df_from.
+__device__ __forceinline__ dfl df_from_fast(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);  // biased exponent
+  if (ex < 949 || ex > 1150) return df_from(v);
+  const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sgn | ((unsigned int)(ex - 896) << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu));
+  // the low 29 significand bits r = r1 2^23 + r0 as FP32 (exact parts, one rounding in the sum),
+  // scaled by 2^(ex - 1075)
+  const unsigned int r0 = (unsigned int)(b & 0x7FFFFFu), r1 = (unsigned int)((b >> 23) & 0x3Fu);
+  const float f0 = __fsub_rn(__uint_as_float(0x4B000000u | r0), 8388608.0f);
+  const float f1 = __fsub_rn(__uint_as_float(0x4B000000u | r1), 8388608.0f);
+  const float mag = __fmul_rn(__fmaf_rn(f1, 8388608.0f, f0), __uint_as_float((unsigned int)(ex - 948) << 23));
+  return df_quick(hi, sgn ? -mag : mag);
+}
 
 template <>
 struct Ops<dfl> {
@@ -1216,6 +1235,33 @@ __device__ void ldl_check(const double* A, int n, int nf, int ld, Red& red, doub
   rmin = -block_max(-rm, red);
 }
 
+// ldl_check on double-float factors, from their high parts in FP32: the tests' thresholds (1e4, 1e-8)
+// sit orders of magnitude away from FP32 rounding, and a non-finite sum fails them (the caller then
+// factors in FP64), so no FP64 work is needed on the double-float path
+__device__ void ldl_check_df(const dfl* A, int n, int nf, int ld, Red& red, double& gmax, double& rmin) {
+  const int lane = threadIdx.x & 31;
+  float gm = 0.0f, rm = INFINITY;
+  for (int p = threadIdx.x >> 5; p < n; p += NWARP) {
+    const int kend = min(p, nf);
+    float acc = 0.0f;
+    for (int k = lane; k < kend; k += 32) {
+      const float l = A[(int64_t)p * ld + k].hi;
+      acc = __fmaf_rn(__fmul_rn(l, l), fabsf(A[(int64_t)k * ld + k].hi), acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (p < nf) {
+      const float d = fabsf(A[(int64_t)p * ld + p].hi);
+      acc = __fadd_rn(acc, d);
+      const float q = __fdiv_rn(d, acc);
+      rm = (q == q) ? fminf(rm, q) : 0.0f;
+    }
+    gm = (acc == acc) ? fmaxf(gm, acc) : INFINITY;
+  }
+  gmax = block_max((double)gm, red);
+  rmin = -block_max(-(double)rm, red);
+}
+
 // Photoionisation (a wave with a dipole row y): the boundary derivatives of the
 // incoming-wave solutions are V = -(1/a) conj(Zhat)^-1 [diag(1/h'^*); 0], Zhat
 // the full-channel form of Z, so M^-_m = sqrt(2) a (V^T y)_m
@@ -1260,7 +1306,7 @@ __device__ bool z_ldl_refined(cplx* C, int no, int r, int ldC, double* G, int ld
     const int i = (int)(idx / mc), j = (int)(idx % mc);
     if (j < no && j > i) continue;
     const cplx v = C[(int64_t)i * ldC + j];
-    Cd[(int64_t)i * ldC + j] = cdf{df_from(v.re), df_from(v.im)};
+    Cd[(int64_t)i * ldC + j] = cdf{df_from_fast(v.re), df_from_fast(v.im)};
   }
   __syncthreads();
   LUStat st;
@@ -1455,16 +1501,20 @@ __device__ bool sym_xsec(const SolveArgs& g, int e, int no, uint8_t fl, unsigned
   // then turned back into FP64 for the tests and the sign count
   dfl* Ad = reinterpret_cast<dfl*>(As);
   for (int p = t >> 5; p < no; p += NWARP)
-    for (int q = lane; q <= p; q += 32) Ad[(int64_t)p * ld + q] = df_from(As[(int64_t)p * ld + q]);
+    for (int q = lane; q <= p; q += 32) Ad[(int64_t)p * ld + q] = df_from_fast(As[(int64_t)p * ld + q]);
   __syncthreads();
   ldl_solve<dfl>(Ad, no, no, ld, reinterpret_cast<dfl*>(panel_b), reinterpret_cast<dfl*>(tile_b),
                  reinterpret_cast<dfl*>(tmp_b), reinterpret_cast<dfl*>(tri_b), st);
-  for (int p = t >> 5; p < no; p += NWARP)
-    for (int q = lane; q <= p; q += 32) As[(int64_t)p * ld + q] = df_to(Ad[(int64_t)p * ld + q]);
   __syncthreads();
-  ldl_check(As, no, no, ld, red, growth_s, piv_s);
+  // the growth and pivot tests and the sign count on the factors' high parts, in FP32
+  ldl_check_df(Ad, no, no, ld, red, growth_s, piv_s);
   growth_s /= sm;
-  double negs = negatives();
+  double negs;
+  {
+    int neg = 0;
+    for (int p = t; p < no; p += NT) neg += (Ad[(int64_t)p * ld + p].hi < 0.0f) ? 1 : 0;
+    negs = block_sum((double)neg, red);
+  }
   const bool ok_c = (growth_c <= SYM_GROWTH_MAX) && (piv_c >= SYM_PIVOT_MIN);
   if (ok_c && !(growth_s <= SYM_GROWTH_MAX_INERTIA_DF && piv_s >= SYM_PIVOT_MIN)) {
     // the double-float factorisation is not trusted for this S'': form it again and factor in FP64
