@@ -35,7 +35,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # nominal GB300 FP64 (dense), one GPU; the measured 
 # 1000-energy launch (the solve; the tensor-core pole sum with its default 15 slice products, as
 # 2-SM and as one-SM MMAs); scaled to a launch by its energies.  A kernel changed since its capture
 # has no entry (traffic null), and so has the pole sum with another product set.
-DRAM_BYTES_PER_ENERGY_N256 = {"solve": 1.2454e7, "polesum_split_pair": 1.721e6}
+DRAM_BYTES_PER_ENERGY_N256 = {"solve": 1.2250e7, "polesum_split_pair": 1.721e6}
 PRODUCT_SETS = (3, 6, 10, 13, 15)
 # FP32 instructions per flop of the solve's double-float arithmetic: a double-float multiply-subtract
 # (an error-free product by FMA, TwoSum, renormalisation) is 15 FP32 instructions for 2 flops
